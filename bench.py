@@ -1,0 +1,336 @@
+"""Benchmark of the sparse COO tensor contraction on GB300.
+
+One step = one full contraction (Y grouping, X survey, product count, expansion and
+accumulation, compaction to COO) of one synthetic workload held in HBM. Default workload:
+two order-4 256^4 COO tensors with 5e6 uniform entries each, X modes (2,3) paired with Y
+modes (0,1) (about 3.8e8 products, 3.65e8 output entries).
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle instead, on a
+bounded sample of the same workload. Under torchrun each rank runs an independent
+replica on its own GPU (the contraction needs no exchange); value = all ranks' products
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "plain_large": lambda seed: W.plain_large(seed=seed),
+    "imbalanced": lambda seed: W.imbalanced(seed=seed),
+    "imbalanced_both": lambda seed: W.imbalanced(seed=seed, both_zipf=True),
+    "plain_small": lambda seed: W.plain_small(seed=seed),
+}
+SEEDS = {"plain_large": W.SEED_BASE + 2, "imbalanced": W.SEED_BASE + 3, "imbalanced_both": W.SEED_BASE + 3,
+         "plain_small": W.SEED_BASE + 1}
+DESCRIPTIONS = {
+    "plain_large": "X,Y order-4 256^4 COO, 5e6 uniform nnz each, X modes (2,3) x Y modes (0,1), FP64",
+    "imbalanced": "X 4096x512x512 2e7 nnz, Y 512x512x64 2e4 nnz with Zipf(1.2) contract keys, X (1,2) x Y (0,1)",
+    "imbalanced_both": "as imbalanced, X contract keys also Zipf(1.2)",
+    "plain_small": "X,Y order-3 64^3 COO, 5e3 distinct nnz each, X mode 2 x Y mode 0",
+}
+# Rows of X (first coordinate < bound) that make the oracle's bounded CPU sample.
+CPU_SAMPLE_X0 = {"plain_large": 7, "imbalanced": 4096, "imbalanced_both": 64, "plain_small": 64}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def alg_bytes(p, nz, oz):
+    """Bytes the contraction must move: read both inputs once, write the output once."""
+    return (4 * p.X.order + 8) * p.X.nnz + (4 * p.Y.order + 8) * p.Y.nnz + (4 * oz + 8) * nz
+
+
+def cpu_sample(p, workload):
+    bound = CPU_SAMPLE_X0[workload]
+    sel = p.X.coords[:, 0] < bound
+    return W.Problem(p.X.take(sel), p.Y, p.cx, p.cy, p.out_order), \
+        f"X entries with first coordinate < {bound} ({int(sel.sum())} of {p.X.nnz}), all of Y"
+
+
+def run_oracle_sample(p, workload):
+    import oracle
+
+    sp, desc = cpu_sample(p, workload)
+    t0 = time.perf_counter()
+    r = oracle.contract(sp.X, sp.Y, sp.cx, sp.cy, sp.out_order)
+    dt = time.perf_counter() - t0
+    return r.products, dt, desc
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    p = WORKLOADS[args.workload](SEEDS[args.workload])
+    for _ in range(args.warmup):
+        run_oracle_sample(p, args.workload)
+    prods, times, desc = 0, [], ""
+    for _ in range(args.steps):
+        pr, dt, desc = run_oracle_sample(p, args.workload)
+        prods += pr
+        times.append(dt)
+    total = sum(times)
+    value = prods / total
+    line = {
+        "impl": "reference", "metric": "products/s", "value": value, "unit": "products/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {DESCRIPTIONS[args.workload]}", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "products/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain_large", choices=sorted(WORKLOADS))
+    ap.add_argument("--strategy", type=int, default=0, help="0 auto, 1 global table, 2 grouped")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+
+    import paper_2410_10094_gb300 as stc
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stc.load()
+    ctx = stc.default_context(dev)
+
+    seed = SEEDS[args.workload] + 1000 * rank
+    p = WORKLOADS[args.workload](seed)
+    X = (p.X.shape, torch.from_numpy(p.X.coords).cuda(), torch.from_numpy(p.X.vals).cuda())
+    Y = (p.Y.shape, torch.from_numpy(p.Y.coords).cuda(), torch.from_numpy(p.Y.vals).cuda())
+    stream = torch.cuda.current_stream()
+
+    def step(record=False):
+        return stc.contract(X, Y, p.cx, p.cy, p.out_order, strategy=args.strategy, record_times=record,
+                            stream=stream, ctx=ctx)
+
+    for _ in range(args.warmup):
+        r = step()
+        nz, oz, P, launches = r.nnz, r.order, r.stats.products, r.stats.launches
+        del r
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- timed region: K device-resident steps
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage = np.zeros(8)
+    with ClockSampler(dev) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step(record=True)
+            stage[: len(r.stats.stage_ms)] += np.asarray(r.stats.stage_ms)
+            del r
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        pt = torch.tensor([float(P)], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(pt)
+        total_products = float(pt.item())
+    else:
+        total_products = float(P)
+    value = total_products * args.steps / (ms / 1e3)
+
+    # ---- e2e: the public API call with host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hx = [torch.from_numpy(p.X.coords).pin_memory(), torch.from_numpy(p.X.vals).pin_memory()]
+        hy = [torch.from_numpy(p.Y.coords).pin_memory(), torch.from_numpy(p.Y.vals).pin_memory()]
+        hc = torch.empty((nz, oz), dtype=torch.int32).pin_memory()
+        hv = torch.empty((nz,), dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in hx + hy)
+        d2h = hc.numel() * 4 + hv.numel() * 8
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            Xd = (p.X.shape, hx[0].to("cuda", non_blocking=True), hx[1].to("cuda", non_blocking=True))
+            Yd = (p.Y.shape, hy[0].to("cuda", non_blocking=True), hy[1].to("cuda", non_blocking=True))
+            r = stc.contract(Xd, Yd, p.cx, p.cy, p.out_order, strategy=args.strategy, stream=stream, ctx=ctx)
+            hc[: r.nnz].copy_(r.coords, non_blocking=True)
+            hv[: r.nnz].copy_(r.vals, non_blocking=True)
+            torch.cuda.synchronize()
+            del r, Xd, Yd
+        dt = time.perf_counter() - t0
+        barrier()
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": total_products * args.e2e_steps / dt, "unit": "products/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "ms_per_step": 1e3 * dt / args.e2e_steps}
+        del hc, hv
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel from the library's per-stage CUDA events
+    hbm, peak_kind = peaks()
+    stage_names = ["group_y", "survey_x", "group_x", "plan", "accumulate", "compact"]
+    per_step = stage / args.steps
+    dom = int(np.argmax(per_step[:6]))
+    bytes_in = (4 * p.X.order + 8) * p.X.nnz + (4 * p.Y.order + 8) * p.Y.nnz
+    kernel_bytes = {
+        0: (4 * p.Y.order + 8) * p.Y.nnz + 16 * p.Y.nnz,            # read Y, write grouped Y
+        1: (4 * p.X.order + 8) * p.X.nnz,                            # read X once
+        4: 12 * p.X.nnz + 16 * p.Y.nnz + 16 * nz,                    # survivors + Y runs in, distinct outputs out
+        5: (4 * oz + 8) * nz,                                        # write the COO output
+    }.get(dom, bytes_in)
+    dom_ms = per_step[dom]
+    achieved = kernel_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
+    step_ms = ms / args.steps
+    roofline = {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": None, "peak_kind": peak_kind,
+                "kernel_ms": dom_ms, "alg_bytes": kernel_bytes}
+    step_alg = alg_bytes(p, nz, oz)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        prods, dt, desc = run_oracle_sample(p, args.workload)
+        cpu = {"value": prods / dt, "unit": "products/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": dt}
+
+    line = {
+        "metric": "products/s", "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {DESCRIPTIONS[args.workload]}", "seed": seed,
+                   "products_per_step": P, "nnz_out": nz, "parallelism": f"replicas x{world}",
+                   "l2": "inputs 240 MB and output 8.8 GB exceed the 129 MB L2; no flush" if args.workload ==
+                   "plain_large" else "see DESIGN.md", "strategy": args.strategy},
+        "step_hbm": {"alg_bytes": step_alg, "gbs": step_alg / (step_ms / 1e3) / 1e9,
+                     "frac": step_alg / (step_ms / 1e3) / 1e9 / hbm},
+        "stage_ms": {n: float(per_step[i]) for i, n in enumerate(stage_names)},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches) * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

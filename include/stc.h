@@ -1,0 +1,155 @@
+/*
+ * stc.h -- C ABI of a GB300 (sm_103a) sparse COO tensor contraction library.
+ *
+ * The operation is the sparse tensor contraction of Swift (arXiv 2410.10094):
+ *
+ *     Z = X (x)_{cy}^{cx} Y,    z[fX, fY] = sum_c x[fX, c] * y[c, fY]     (Eq. 1, Eq. 2)
+ *
+ * X and Y are COO lists (Section 2.1.2); X mode cx[i] is paired with Y mode cy[i] and the
+ * two must have equal lengths (Section 2.1.3). The output's modes are X's free modes in
+ * ascending order followed by Y's free modes in ascending order (Eq. 4, Fig. 2), unless an
+ * explicit output order permutes them.
+ *
+ * Conventions for every entry point:
+ *   - Mode numbers are 0-based. Coordinates are int32, 0 <= coord < mode length.
+ *   - "device" pointers are CUDA global memory on the context's device; "host" pointers
+ *     are ordinary CPU memory read during the call only.
+ *   - Work is enqueued on the stream argument (a cudaStream_t; NULL = legacy default
+ *     stream). A call returns after its device work is complete unless stated otherwise.
+ *   - Inputs stay owned by the caller and must stay valid until the call returns.
+ *     Results are owned by the library and released with stc_result_free().
+ *   - Every entry point returns a stc_status; nothing throws across the ABI. On failure a
+ *     message for the calling thread is available from stc_last_error().
+ *   - Floating point is FP64 (IEEE binary64): products are rounded before they are added
+ *     (no fused multiply-add), sums are accumulated in binary64 in an unspecified order.
+ */
+#ifndef STC_H
+#define STC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum stc_status {
+  STC_OK = 0,
+  STC_ERR_INVALID_ARG = 1,        /* null pointer, bad order, bad mode list, bad permutation */
+  STC_ERR_SHAPE_MISMATCH = 2,     /* paired modes have different lengths (Section 2.1.3) */
+  STC_ERR_KEY_OVERFLOW = 3,       /* a key space (product of mode lengths) needs > 64 bits */
+  STC_ERR_OUT_OF_MEMORY = 4,      /* device allocation failed or the context budget is exceeded */
+  STC_ERR_TABLE_FULL = 5,         /* an accumulation table overflowed (internal; never expected) */
+  STC_ERR_TIMEOUT = 6,            /* a bounded wait gave up */
+  STC_ERR_CUDA = 7,               /* a CUDA runtime call failed; see stc_last_error() */
+  STC_ERR_COORD_OUT_OF_RANGE = 8, /* an input coordinate is negative or >= its mode length */
+  STC_ERR_UNSUPPORTED = 9         /* valid input outside what this build implements */
+} stc_status;
+
+#define STC_MAX_ORDER 8            /* modes per input tensor */
+#define STC_MAX_NNZ 2147483647LL   /* entries per input tensor (int32 positions) */
+
+typedef struct stc_ctx stc_ctx;
+typedef struct stc_result stc_result;
+
+/* A COO tensor (Section 2.1.2): nnz (coordinate, value) pairs. Repeated coordinates are
+ * allowed and are additive. */
+typedef struct stc_coo {
+  int32_t order;          /* number of modes, 0..STC_MAX_ORDER */
+  const int64_t* shape;   /* host, [order], each >= 1 */
+  int64_t nnz;            /* 0..STC_MAX_NNZ */
+  const int32_t* coords;  /* device, [nnz][order] row-major; may be NULL when nnz == 0 */
+  const double* vals;     /* device, [nnz]; may be NULL when nnz == 0 */
+} stc_coo;
+
+/* Accumulation strategy. AUTO picks from the key spaces: one global table when the output
+ * key space is small (the whole table stays in L2), otherwise per-X-free-group tables in
+ * shared memory (Section 4.3). */
+enum { STC_STRATEGY_AUTO = 0, STC_STRATEGY_GLOBAL = 1, STC_STRATEGY_GROUPED = 2 };
+
+typedef struct stc_opts {
+  int32_t strategy;       /* STC_STRATEGY_*; 0 = AUTO */
+  int32_t record_times;   /* nonzero: time each stage with CUDA events (stc_result_stats) */
+  double load_factor;     /* global-table load factor in (0, 0.9]; 0 = default 0.5 */
+} stc_opts;
+
+/* Per-call statistics of a finished contraction. */
+typedef struct stc_stats {
+  uint64_t products;      /* P = number of (x, y) pairs with equal contract coordinates */
+  uint64_t survivors;     /* X entries whose contract key has at least one Y entry */
+  uint64_t out_capacity;  /* output entries allocated (an upper bound on nnz) */
+  uint64_t table_slots;   /* global-table slots (GLOBAL) or overflow-table slots (GROUPED) */
+  uint64_t groups;        /* non-empty X free groups (GROUPED) */
+  int32_t strategy;       /* STC_STRATEGY_GLOBAL or STC_STRATEGY_GROUPED */
+  int32_t nstages;        /* valid entries of stage_ms when record_times was set */
+  uint32_t launches;      /* CUDA kernels this call launched (memsets and copies not counted) */
+  uint32_t reserved_;
+  float stage_ms[8];      /* 0 group Y, 1 survey X, 2 group X, 3 plan, 4 accumulate, 5 compact/write */
+} stc_stats;
+
+/* Human-readable name of a status code (static storage). */
+const char* stc_status_string(stc_status s);
+
+/* Last error message of the calling thread ("" if none). Valid until the thread's next call. */
+const char* stc_last_error(void);
+
+/* Create a context on CUDA device `device`. `mem_budget_bytes` caps the device memory the
+ * context may hold at once for scratch and results (0 = no cap beyond the device's). The
+ * context owns a stream-ordered memory pool; freed blocks are kept for reuse. */
+stc_status stc_create(stc_ctx** ctx, int device, size_t mem_budget_bytes);
+
+/* Destroy a context. All results created from it must have been freed. */
+stc_status stc_destroy(stc_ctx* ctx);
+
+/* Contract X and Y (Eq. 2). Arguments:
+ *   X, Y        input tensors (device coordinate and value arrays, host shapes)
+ *   ncontract   number of paired modes m, 0 <= m <= min(X.order, Y.order); m = 0 is the
+ *               outer product, m = order of both gives an order-0 (scalar) output
+ *   cx, cy      host, [m]; X mode cx[i] pairs with Y mode cy[i]; the lists order the
+ *               contract key (first listed mode most significant, Section 2.3.1)
+ *   out_order   host, [orderZ] or NULL; output mode q holds entry out_order[q] of the
+ *               concatenation (X free modes ascending, Y free modes ascending)
+ *   opts        host or NULL (defaults)
+ *   stream      cudaStream_t the work is enqueued on
+ *   out         receives the result
+ * Output: every coordinate that received at least one product, once, with the sum of its
+ * products (a structural nonzero is kept even if it sums to 0.0), in unspecified order.
+ * Errors: INVALID_ARG, SHAPE_MISMATCH, KEY_OVERFLOW (output key space > 2^64 - 2),
+ * COORD_OUT_OF_RANGE (checked on the device), OUT_OF_MEMORY, UNSUPPORTED, CUDA. */
+stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t ncontract,
+                        const int32_t* cx, const int32_t* cy, const int32_t* out_order,
+                        const stc_opts* opts, void* stream, stc_result** out);
+
+/* The exact product count of the contraction (Section 4.3: each X entry meets exactly
+ * count_Y[its contract key] Y entries) and the device bytes a stc_contract of the same
+ * inputs would hold at its peak (scratch + result). Used to admit work under a budget. */
+stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t ncontract,
+                     const int32_t* cx, const int32_t* cy, void* stream, uint64_t* products,
+                     uint64_t* bytes_bound);
+
+/* LN keys of the listed modes of every entry of T (Section 2.3.1, Fig. 3): the coordinates
+ * of modes[0..nmodes) read as digits of one mixed-radix number, modes[0] most significant,
+ * each digit's radix its mode length. keys_out: device, [T.nnz]. */
+stc_status stc_linearize(stc_ctx* ctx, const stc_coo* T, int32_t nmodes, const int32_t* modes,
+                         uint64_t* keys_out, void* stream);
+
+/* Group n keys in [0, k) with a counting sort (Section 4.1.1, Fig. 5): count, exclusive
+ * scan, scatter. offsets_out: device, [k+1], offsets_out[v] = first slot of key v and
+ * offsets_out[k] = n. perm_out: device, [n], perm_out[s] = index of the key placed in
+ * slot s; the order inside one key's run is unspecified. keys: device, [n]. Requires
+ * n <= STC_MAX_NNZ and k <= 2^26. */
+stc_status stc_group_keys(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t k,
+                          uint32_t* offsets_out, uint32_t* perm_out, void* stream);
+
+/* Result accessors. Coordinates are device int32 [nnz][order] row-major, values device
+ * double [nnz]; both stay valid until stc_result_free(). shape is host, [order]. */
+stc_status stc_result_info(const stc_result* r, int64_t* nnz, int32_t* order, const int64_t** shape);
+stc_status stc_result_data(const stc_result* r, const int32_t** coords, const double** vals);
+stc_status stc_result_stats(const stc_result* r, stc_stats* stats);
+stc_status stc_result_free(stc_result* r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STC_H */

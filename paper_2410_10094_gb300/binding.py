@@ -1,0 +1,321 @@
+"""ctypes binding of ``libstc.so`` (include/stc.h). Argument marshalling only: every step of
+the contraction runs in the library's CUDA kernels. PyTorch supplies device memory and
+streams; there is no CPU path, and a missing library raises instead of falling back."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+from .build import LIB as LIB_PATH
+
+STC_OK = 0
+STATUS_NAMES = {
+    0: "STC_OK", 1: "STC_ERR_INVALID_ARG", 2: "STC_ERR_SHAPE_MISMATCH", 3: "STC_ERR_KEY_OVERFLOW",
+    4: "STC_ERR_OUT_OF_MEMORY", 5: "STC_ERR_TABLE_FULL", 6: "STC_ERR_TIMEOUT", 7: "STC_ERR_CUDA",
+    8: "STC_ERR_COORD_OUT_OF_RANGE", 9: "STC_ERR_UNSUPPORTED",
+}
+STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_GROUPED = 0, 1, 2
+STC_MAX_ORDER = 8
+
+
+class StcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class stc_coo(C.Structure):
+    _fields_ = [("order", C.c_int32), ("shape", C.POINTER(C.c_int64)), ("nnz", C.c_int64),
+                ("coords", C.c_void_p), ("vals", C.c_void_p)]
+
+
+class stc_opts(C.Structure):
+    _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double)]
+
+
+class stc_stats(C.Structure):
+    _fields_ = [("products", C.c_uint64), ("survivors", C.c_uint64), ("out_capacity", C.c_uint64),
+                ("table_slots", C.c_uint64), ("groups", C.c_uint64), ("strategy", C.c_int32),
+                ("nstages", C.c_int32), ("launches", C.c_uint32), ("reserved_", C.c_uint32),
+                ("stage_ms", C.c_float * 8)]
+
+
+EXPORTS = {
+    "stc_status_string": ([C.c_int], C.c_char_p),
+    "stc_last_error": ([], C.c_char_p),
+    "stc_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_size_t], C.c_int),
+    "stc_destroy": ([C.c_void_p], C.c_int),
+    "stc_contract": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
+                      C.c_void_p, C.POINTER(stc_opts), C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "stc_count": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
+                   C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
+    "stc_linearize": ([C.c_void_p, C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "stc_group_keys": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p],
+                       C.c_int),
+    "stc_result_info": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                         C.POINTER(C.POINTER(C.c_int64))], C.c_int),
+    "stc_result_data": ([C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)], C.c_int),
+    "stc_result_stats": ([C.c_void_p, C.POINTER(stc_stats)], C.c_int),
+    "stc_result_free": ([C.c_void_p], C.c_int),
+}
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load(path: Optional[str] = None):
+    """Load libstc.so (built by ``paper_2410_10094_gb300.build``); raises if it is missing."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise ImportError(f"{p} is not built; run `python -m paper_2410_10094_gb300.build` "
+                                  "(there is no CPU fallback)")
+            L = C.CDLL(p)
+            for name, (args, res) in EXPORTS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+        return _lib
+
+
+def check(status: int):
+    if status != STC_OK:
+        msg = load().stc_last_error().decode(errors="replace")
+        raise StcError(status, msg)
+
+
+# ---------------------------------------------------------------- thin wrappers, same names
+
+def stc_status_string(s: int) -> str:
+    return load().stc_status_string(s).decode()
+
+
+def stc_create(device: int = 0, mem_budget_bytes: int = 0) -> int:
+    h = C.c_void_p()
+    check(load().stc_create(C.byref(h), device, mem_budget_bytes))
+    return h.value
+
+
+def stc_destroy(ctx: int):
+    check(load().stc_destroy(C.c_void_p(ctx)))
+
+
+def _mode_array(v: Sequence[int]):
+    n = len(v)
+    arr = (C.c_int32 * max(n, 1))(*[int(x) for x in v])
+    return arr
+
+
+class _CooArg:
+    """Keeps the ctypes views of one input alive for the duration of a call."""
+
+    def __init__(self, shape, coords, vals):
+        import torch
+
+        self.shape_arr = (C.c_int64 * max(len(shape), 1))(*[int(s) for s in shape])
+        order = len(shape)
+        if coords is not None and coords.numel():
+            if coords.device.type != "cuda" or coords.dtype != torch.int32 or not coords.is_contiguous():
+                raise ValueError("coords must be a contiguous CUDA int32 tensor of shape [nnz, order]")
+        if vals is not None and vals.numel():
+            if vals.device.type != "cuda" or vals.dtype != torch.float64 or not vals.is_contiguous():
+                raise ValueError("vals must be a contiguous CUDA float64 tensor of shape [nnz]")
+        nnz = int(vals.shape[0]) if vals is not None else 0
+        if coords is not None and coords.dim() == 2 and (coords.shape[0] != nnz or coords.shape[1] != order):
+            raise ValueError("coords must have shape [nnz, order]")
+        self.coo = stc_coo(order, C.cast(self.shape_arr, C.POINTER(C.c_int64)), nnz,
+                           C.c_void_p(coords.data_ptr() if coords is not None and coords.numel() else 0),
+                           C.c_void_p(vals.data_ptr() if vals is not None and vals.numel() else 0))
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def stc_contract(ctx: int, X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, opts: stc_opts = None,
+                 stream=None) -> int:
+    """Calls stc_contract; X and Y are (shape, coords, vals) with CUDA tensors. Returns the
+    stc_result handle (free with stc_result_free)."""
+    xa, ya = _CooArg(*X), _CooArg(*Y)
+    if len(cx) != len(cy):
+        raise ValueError("cx and cy must have the same length")
+    acx, acy = _mode_array(cx), _mode_array(cy)
+    oo = _mode_array(out_order) if out_order is not None else None
+    r = C.c_void_p()
+    check(load().stc_contract(C.c_void_p(ctx), C.byref(xa.coo), C.byref(ya.coo), len(cx), acx, acy, oo,
+                              C.byref(opts) if opts is not None else None, C.c_void_p(_stream_handle(stream)),
+                              C.byref(r)))
+    return r.value
+
+
+def stc_count(ctx: int, X, Y, cx, cy, stream=None):
+    xa, ya = _CooArg(*X), _CooArg(*Y)
+    acx, acy = _mode_array(cx), _mode_array(cy)
+    P, B = C.c_uint64(), C.c_uint64()
+    check(load().stc_count(C.c_void_p(ctx), C.byref(xa.coo), C.byref(ya.coo), len(cx), acx, acy,
+                           C.c_void_p(_stream_handle(stream)), C.byref(P), C.byref(B)))
+    return int(P.value), int(B.value)
+
+
+def stc_linearize(ctx: int, T, modes: Sequence[int], keys_out, stream=None):
+    ta = _CooArg(*T)
+    am = _mode_array(modes)
+    check(load().stc_linearize(C.c_void_p(ctx), C.byref(ta.coo), len(modes), am,
+                               C.c_void_p(keys_out.data_ptr() if keys_out.numel() else 0),
+                               C.c_void_p(_stream_handle(stream))))
+
+
+def stc_group_keys(ctx: int, keys, k: int, offsets_out, perm_out, stream=None):
+    n = int(keys.numel())
+    check(load().stc_group_keys(C.c_void_p(ctx), C.c_void_p(keys.data_ptr() if n else 0), n, int(k),
+                                C.c_void_p(offsets_out.data_ptr()), C.c_void_p(perm_out.data_ptr() if n else 0),
+                                C.c_void_p(_stream_handle(stream))))
+
+
+def stc_result_info(r: int):
+    nnz, order = C.c_int64(), C.c_int32()
+    shape = C.POINTER(C.c_int64)()
+    check(load().stc_result_info(C.c_void_p(r), C.byref(nnz), C.byref(order), C.byref(shape)))
+    return int(nnz.value), int(order.value), tuple(shape[i] for i in range(order.value))
+
+
+def stc_result_data(r: int):
+    co, va = C.c_void_p(), C.c_void_p()
+    check(load().stc_result_data(C.c_void_p(r), C.byref(co), C.byref(va)))
+    return co.value or 0, va.value or 0
+
+
+def stc_result_stats(r: int) -> stc_stats:
+    st = stc_stats()
+    check(load().stc_result_stats(C.c_void_p(r), C.byref(st)))
+    return st
+
+
+def stc_result_free(r: int):
+    check(load().stc_result_free(C.c_void_p(r)))
+
+
+# ---------------------------------------------------------------- convenience layer
+
+class _DeviceArray:
+    """Exposes library-owned device memory through __cuda_array_interface__; keeps the
+    owning result alive while any tensor views it."""
+
+    def __init__(self, owner, ptr: int, shape, typestr: str):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class Context:
+    """An stc_ctx on one device (its memory pool lives as long as the context)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self.device = device
+        self.handle = stc_create(device, mem_budget_bytes)
+
+    def close(self):
+        if self.handle:
+            stc_destroy(self.handle)
+            self.handle = 0
+
+
+_default_ctx = {}
+
+
+def default_context(device: Optional[int] = None) -> Context:
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else device
+    if dev not in _default_ctx:
+        _default_ctx[dev] = Context(dev)
+    return _default_ctx[dev]
+
+
+@dataclass
+class Stats:
+    products: int
+    survivors: int
+    out_capacity: int
+    table_slots: int
+    groups: int
+    strategy: int
+    launches: int
+    stage_ms: tuple
+
+
+class Result:
+    """A finished contraction. ``coords`` (int32 [nnz, order]) and ``vals`` (float64 [nnz])
+    are zero-copy CUDA tensors over the library's memory; they keep it alive."""
+
+    def __init__(self, handle: int):
+        import torch
+
+        self.handle = handle
+        self.nnz, self.order, self.shape = stc_result_info(handle)
+        cp, vp = stc_result_data(handle)
+        st = stc_result_stats(handle)
+        self.stats = Stats(st.products, st.survivors, st.out_capacity, st.table_slots, st.groups, st.strategy,
+                           st.launches, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))))
+        if self.nnz and self.order:
+            self.coords = torch.as_tensor(_DeviceArray(self, cp, (self.nnz, self.order), "<i4"), device="cuda")
+        else:
+            self.coords = torch.empty((self.nnz, self.order), dtype=torch.int32, device="cuda")
+        if self.nnz:
+            self.vals = torch.as_tensor(_DeviceArray(self, vp, (self.nnz,), "<f8"), device="cuda")
+        else:
+            self.vals = torch.empty((0,), dtype=torch.float64, device="cuda")
+
+    def __del__(self):
+        h = getattr(self, "handle", 0)
+        if h and _lib is not None:
+            stc_result_free(h)
+            self.handle = 0
+
+
+def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, strategy: int = STRATEGY_AUTO,
+             load_factor: float = 0.0, record_times: bool = False, stream=None, ctx: Context = None) -> Result:
+    """Z = X (x) Y (Eq. 2) on the GPU. X and Y are (shape, coords, vals) with coords a CUDA
+    int32 [nnz, order] tensor and vals a CUDA float64 [nnz] tensor."""
+    ctx = ctx or default_context()
+    o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor))
+    return Result(stc_contract(ctx.handle, X, Y, cx, cy, out_order, o, stream))
+
+
+def count(X, Y, cx, cy, *, stream=None, ctx: Context = None):
+    """(P, peak device bytes) of the contraction: the exact product count of Section 4.3."""
+    ctx = ctx or default_context()
+    return stc_count(ctx.handle, X, Y, cx, cy, stream)
+
+
+def linearize(T, modes, *, stream=None, ctx: Context = None):
+    """LN keys (Fig. 3) of the listed modes of each entry of T, as a CUDA int64 tensor
+    holding the unsigned 64-bit keys."""
+    import torch
+
+    ctx = ctx or default_context()
+    n = int(T[2].shape[0]) if T[2] is not None else 0
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    stc_linearize(ctx.handle, T, modes, out, stream)
+    return out
+
+
+def group_keys(keys, k: int, *, stream=None, ctx: Context = None):
+    """Counting-sort grouping (Fig. 5) of keys in [0, k): returns (offsets[k+1], perm[n])."""
+    import torch
+
+    ctx = ctx or default_context()
+    off = torch.empty(int(k) + 1, dtype=torch.int32, device="cuda")
+    perm = torch.empty(int(keys.numel()), dtype=torch.int32, device="cuda")
+    stc_group_keys(ctx.handle, keys, k, off, perm, stream)
+    return off, perm

@@ -1,0 +1,644 @@
+// The C ABI (include/stc.h): argument checks, the key plan, stream-ordered memory, and the
+// order of the stages of one contraction.
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+using namespace stc;
+
+struct stc_ctx {
+  int device = 0;
+  size_t budget = 0;  // 0 = no cap
+  cudaMemPool_t pool = nullptr;
+  std::atomic<size_t> held{0};
+  std::atomic<int64_t> live_results{0};
+  int sms = 0;
+};
+
+struct stc_result {
+  stc_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  int64_t nnz = 0;
+  int32_t order = 0;
+  std::vector<int64_t> shape;
+  int32_t* coords = nullptr;
+  double* vals = nullptr;
+  size_t bytes = 0;
+  stc_stats stats{};
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+stc_status fail(stc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define STC_CUDA(expr)                                                                          \
+  do {                                                                                          \
+    const cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(STC_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define STC_TRY(expr)                    \
+  do {                                   \
+    const stc_status s_ = (expr);        \
+    if (s_ != STC_OK) return s_;         \
+  } while (0)
+
+// Makes the context's device current for the duration of a call, then restores the caller's.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && (prev == dev || cudaSetDevice(dev) == cudaSuccess)) ok = true;
+  }
+  ~DeviceGuard() {
+    if (ok && prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Stream-ordered scratch from the context's pool. Everything still held when the arena
+// dies is returned to the pool in stream order; `keep` hands a block to a result instead.
+struct Arena {
+  stc_ctx* ctx;
+  cudaStream_t s;
+  struct Block { void* p; size_t bytes; };
+  std::vector<Block> blocks;
+  Arena(stc_ctx* c, cudaStream_t st) : ctx(c), s(st) {}
+  ~Arena() {
+    for (auto& b : blocks) {
+      cudaFreeAsync(b.p, s);
+      ctx->held -= b.bytes;
+    }
+  }
+  template <typename T>
+  stc_status alloc(T** out, size_t count) {
+    *out = nullptr;
+    const size_t bytes = count * sizeof(T);
+    if (bytes == 0) return STC_OK;
+    const size_t after = ctx->held.fetch_add(bytes) + bytes;
+    if (ctx->budget && after > ctx->budget) {
+      ctx->held -= bytes;
+      return fail(STC_ERR_OUT_OF_MEMORY, "request of %zu bytes exceeds the context budget (%zu of %zu held)", bytes,
+                  after - bytes, ctx->budget);
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, ctx->pool, s);
+    if (e != cudaSuccess) {
+      ctx->held -= bytes;
+      cudaGetLastError();
+      return fail(STC_ERR_OUT_OF_MEMORY, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    blocks.push_back({p, bytes});
+    *out = static_cast<T*>(p);
+    return STC_OK;
+  }
+  size_t keep(void* p) {
+    for (size_t i = 0; i < blocks.size(); i++)
+      if (blocks[i].p == p) {
+        const size_t b = blocks[i].bytes;
+        blocks.erase(blocks.begin() + i);
+        return b;
+      }
+    return 0;
+  }
+};
+
+bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
+
+uint64_t pow2_at_least(uint64_t v) {
+  uint64_t c = 1;
+  while (c < v) c <<= 1;
+  return c;
+}
+
+uint32_t log2_u64(uint64_t v) {
+  uint32_t r = 0;
+  while (v > 1) v >>= 1, r++;
+  return r;
+}
+
+// The key plan of a contraction (Section 2.3.1 LN keys; the output mode order of Eq. 4).
+struct Plan {
+  KeyPlan kx{}, ky{};
+  OutPlan op{};
+  uint64_t K = 1, FX = 1, FY = 1, F = 1;
+  int32_t oz = 0;
+  std::vector<int64_t> zshape;
+};
+
+stc_status check_coo(const stc_coo* t, const char* name) {
+  if (!t) return fail(STC_ERR_INVALID_ARG, "%s is NULL", name);
+  if (t->order < 0 || t->order > STC_MAX_ORDER)
+    return fail(STC_ERR_INVALID_ARG, "%s.order = %d outside 0..%d", name, t->order, STC_MAX_ORDER);
+  if (t->order > 0 && !t->shape) return fail(STC_ERR_INVALID_ARG, "%s.shape is NULL", name);
+  for (int j = 0; j < t->order; j++)
+    if (t->shape[j] < 1 || t->shape[j] > (int64_t)1 << 31)
+      return fail(STC_ERR_INVALID_ARG, "%s.shape[%d] = %lld outside 1..2^31", name, j, (long long)t->shape[j]);
+  if (t->nnz < 0 || t->nnz > STC_MAX_NNZ)
+    return fail(STC_ERR_INVALID_ARG, "%s.nnz = %lld outside 0..%lld", name, (long long)t->nnz, STC_MAX_NNZ);
+  if (t->nnz > 0 && (!t->vals || (t->order > 0 && !t->coords)))
+    return fail(STC_ERR_INVALID_ARG, "%s has nnz > 0 but NULL coords or vals", name);
+  return STC_OK;
+}
+
+stc_status make_plan(const stc_coo* X, const stc_coo* Y, int32_t m, const int32_t* cx, const int32_t* cy,
+                     const int32_t* out_order, Plan& pl) {
+  STC_TRY(check_coo(X, "X"));
+  STC_TRY(check_coo(Y, "Y"));
+  if (m < 0 || m > X->order || m > Y->order)
+    return fail(STC_ERR_INVALID_ARG, "ncontract = %d outside 0..min(%d, %d)", m, X->order, Y->order);
+  if (m > 0 && (!cx || !cy)) return fail(STC_ERR_INVALID_ARG, "cx or cy is NULL");
+  bool xc[STC_MAX_ORDER] = {}, yc[STC_MAX_ORDER] = {};
+  for (int i = 0; i < m; i++) {
+    if (cx[i] < 0 || cx[i] >= X->order || cy[i] < 0 || cy[i] >= Y->order)
+      return fail(STC_ERR_INVALID_ARG, "contract pair %d = (%d, %d) out of range", i, cx[i], cy[i]);
+    if (xc[cx[i]] || yc[cy[i]]) return fail(STC_ERR_INVALID_ARG, "a mode is listed twice in cx or cy");
+    xc[cx[i]] = yc[cy[i]] = true;
+  }
+  for (int i = 0; i < m; i++)
+    if (X->shape[cx[i]] != Y->shape[cy[i]])
+      return fail(STC_ERR_SHAPE_MISMATCH, "X mode %d has length %lld but Y mode %d has length %lld", cx[i],
+                  (long long)X->shape[cx[i]], cy[i], (long long)Y->shape[cy[i]]);
+
+  pl.kx = KeyPlan{};
+  pl.ky = KeyPlan{};
+  pl.kx.order = X->order;
+  pl.ky.order = Y->order;
+  for (int j = 0; j < X->order; j++) pl.kx.size[j] = X->shape[j];
+  for (int j = 0; j < Y->order; j++) pl.ky.size[j] = Y->shape[j];
+
+  // Contract key: row-major over the contract list, first listed pair most significant.
+  unsigned __int128 acc = 1;
+  for (int i = m - 1; i >= 0; i--) {
+    pl.kx.cstride[cx[i]] = (uint64_t)acc;
+    pl.ky.cstride[cy[i]] = (uint64_t)acc;
+    acc *= (unsigned __int128)X->shape[cx[i]];
+    if (acc > (unsigned __int128)UINT64_MAX) return fail(STC_ERR_KEY_OVERFLOW, "contract key space exceeds 2^64");
+  }
+  pl.K = (uint64_t)acc;
+
+  // Free keys: row-major over the free modes in ascending order.
+  std::vector<int> xf, yf;
+  for (int j = 0; j < X->order; j++)
+    if (!xc[j]) xf.push_back(j);
+  for (int j = 0; j < Y->order; j++)
+    if (!yc[j]) yf.push_back(j);
+  acc = 1;
+  for (int a = (int)xf.size() - 1; a >= 0; a--) {
+    pl.kx.fstride[xf[a]] = (uint64_t)acc;
+    acc *= (unsigned __int128)X->shape[xf[a]];
+    if (acc > (unsigned __int128)UINT64_MAX) return fail(STC_ERR_KEY_OVERFLOW, "X free key space exceeds 2^64");
+  }
+  pl.FX = (uint64_t)acc;
+  acc = 1;
+  for (int b = (int)yf.size() - 1; b >= 0; b--) {
+    pl.ky.fstride[yf[b]] = (uint64_t)acc;
+    acc *= (unsigned __int128)Y->shape[yf[b]];
+    if (acc > (unsigned __int128)UINT64_MAX) return fail(STC_ERR_KEY_OVERFLOW, "Y free key space exceeds 2^64");
+  }
+  pl.FY = (uint64_t)acc;
+  const unsigned __int128 F = (unsigned __int128)pl.FX * pl.FY;
+  // The all-ones key marks empty table slots, so the largest usable key is 2^64 - 2.
+  if (F > (unsigned __int128)(UINT64_MAX - 1)) return fail(STC_ERR_KEY_OVERFLOW, "output key space exceeds 2^64 - 1");
+  pl.F = (uint64_t)F;
+
+  // Output: the concatenation (X free, Y free) is row-major in zkey = fX * FY + fY.
+  pl.oz = (int32_t)(xf.size() + yf.size());
+  std::vector<uint64_t> csize(pl.oz), cstr(pl.oz);
+  for (size_t a = 0; a < xf.size(); a++) csize[a] = (uint64_t)X->shape[xf[a]];
+  for (size_t b = 0; b < yf.size(); b++) csize[xf.size() + b] = (uint64_t)Y->shape[yf[b]];
+  uint64_t st = 1;
+  for (int t = pl.oz - 1; t >= 0; t--) {
+    cstr[t] = st;
+    st *= csize[t];
+  }
+  if (out_order) {
+    std::vector<int> seen(pl.oz, 0);
+    for (int q = 0; q < pl.oz; q++) {
+      if (out_order[q] < 0 || out_order[q] >= pl.oz || seen[out_order[q]])
+        return fail(STC_ERR_INVALID_ARG, "out_order is not a permutation of 0..%d", pl.oz - 1);
+      seen[out_order[q]] = 1;
+    }
+  }
+  pl.op = OutPlan{};
+  pl.op.order = pl.oz;
+  pl.op.pow2 = 1;
+  pl.zshape.assign(pl.oz, 0);
+  for (int q = 0; q < pl.oz; q++) {
+    const int t = out_order ? out_order[q] : q;
+    pl.op.div[q] = cstr[t];
+    pl.op.mod[q] = csize[t];
+    pl.zshape[q] = (int64_t)csize[t];
+    if (!is_pow2(csize[t])) pl.op.pow2 = 0;
+  }
+  for (int q = 0; q < pl.oz; q++) pl.op.shift[q] = pl.op.pow2 ? log2_u64(pl.op.div[q]) : 0;
+  return STC_OK;
+}
+
+stc_status status_word(uint32_t st) {
+  if (st & kStatCoordRange) return fail(STC_ERR_COORD_OUT_OF_RANGE, "an input coordinate is outside its mode");
+  if (st & kStatTableFull) return fail(STC_ERR_TABLE_FULL, "an accumulation table overflowed");
+  if (st & kStatOutOverflow) return fail(STC_ERR_TABLE_FULL, "output capacity exceeded");
+  if (st & kStatTimeout) return fail(STC_ERR_TIMEOUT, "a bounded wait gave up");
+  return STC_OK;
+}
+
+// Small device counters of one call, in one allocation so one memset clears them.
+struct Counters {
+  u64 P;           // products
+  u64 nz;          // output entries written
+  unsigned ns;     // survivors
+  uint32_t status; // kStat* bits
+};
+
+// Per-stage CUDA events when timing is requested.
+struct StageTimer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<cudaEvent_t> ev;
+  int stage_of[16] = {};
+  void start(bool enable, cudaStream_t st) {
+    on = enable;
+    s = st;
+    if (on) mark(-1);
+  }
+  void mark(int stage) {
+    if (!on) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      on = false;
+      return;
+    }
+    cudaEventRecord(e, s);
+    if (ev.size() > 16) {
+      cudaEventDestroy(e);
+      return;
+    }
+    if (stage >= 0 && stage < 8 && !ev.empty()) stage_of[ev.size() - 1] = stage;
+    ev.push_back(e);
+  }
+  void collect(stc_stats& stats) {
+    if (!on) return;
+    for (size_t i = 1; i < ev.size(); i++) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+      const int st = stage_of[i - 1];
+      stats.stage_ms[st] += ms;
+      stats.nstages = std::max(stats.nstages, st + 1);
+    }
+  }
+  ~StageTimer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+// The device state shared by the counting pass and the contraction: Y grouped by contract
+// key, and X surveyed against it.
+struct Prepared {
+  uint32_t* yoff = nullptr;  // [K + 1]
+  u64* yfk = nullptr;        // [nY], Y free keys in contract-key order
+  double* yv = nullptr;      // [nY]
+  Survivors sv{};
+  Counters* ctr = nullptr;
+  uint32_t* gcnt = nullptr;  // [FX] survivors per X free key (GROUPED only)
+  u64* gbound = nullptr;     // [FX] sum of run lengths per X free key (GROUPED only)
+};
+
+stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, const Plan& pl, bool groups,
+                   cudaStream_t s, StageTimer& tm, Prepared& pr) {
+  if (pl.K > kMaxDirectBins)
+    return fail(STC_ERR_UNSUPPORTED, "contract key space %llu exceeds %llu bins", (unsigned long long)pl.K,
+                (unsigned long long)kMaxDirectBins);
+  const int64_t nX = X->nnz, nY = Y->nnz;
+  STC_TRY(ar.alloc(&pr.ctr, 1));
+  STC_CUDA(cudaMemsetAsync(pr.ctr, 0, sizeof(Counters), s));
+  uint32_t* status = &pr.ctr->status;
+
+  // Y: count per contract key, exclusive scan, scatter (Section 4.1.1 counting sort).
+  uint32_t *ycnt = nullptr, *ycur = nullptr, *scr = nullptr;
+  STC_TRY(ar.alloc(&ycnt, pl.K));
+  STC_TRY(ar.alloc(&pr.yoff, pl.K + 1));
+  STC_TRY(ar.alloc(&ycur, pl.K));
+  STC_TRY(ar.alloc(&scr, (size_t)scan_scratch_elems((int64_t)pl.K)));
+  STC_TRY(ar.alloc(&pr.yfk, (size_t)nY));
+  STC_TRY(ar.alloc(&pr.yv, (size_t)nY));
+  STC_CUDA(cudaMemsetAsync(ycnt, 0, pl.K * sizeof(uint32_t), s));
+  STC_CUDA(launch_y_count(Y->coords, nY, pl.ky, ycnt, status, ctx->sms, s));
+  STC_CUDA(scan_u32(ycnt, pr.yoff, (int64_t)pl.K, scr, s));
+  STC_CUDA(cudaMemcpyAsync(ycur, pr.yoff, pl.K * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  STC_CUDA(launch_y_scatter(Y->coords, Y->vals, nY, pl.ky, ycur, pr.yfk, pr.yv, ctx->sms, s));
+  tm.mark(0);
+
+  // X: find each entry's Y run; keep the entries that have one (Section 4.3 counts).
+  STC_TRY(ar.alloc(&pr.sv.fk, (size_t)nX));
+  STC_TRY(ar.alloc(&pr.sv.ystart, (size_t)nX));
+  STC_TRY(ar.alloc(&pr.sv.w, (size_t)nX));
+  STC_TRY(ar.alloc(&pr.sv.v, (size_t)nX));
+  pr.sv.count = &pr.ctr->ns;
+  if (groups) {
+    STC_TRY(ar.alloc(&pr.gcnt, pl.FX));
+    STC_TRY(ar.alloc(&pr.gbound, pl.FX));
+    STC_CUDA(cudaMemsetAsync(pr.gcnt, 0, pl.FX * sizeof(uint32_t), s));
+    STC_CUDA(cudaMemsetAsync(pr.gbound, 0, pl.FX * sizeof(u64), s));
+  }
+  STC_CUDA(launch_x_survey(X->coords, X->vals, nX, pl.kx, pr.yoff, pr.sv, &pr.ctr->P, pr.gcnt, pr.gbound, status,
+                           ctx->sms, s));
+  tm.mark(1);
+  return STC_OK;
+}
+
+stc_status read_counters(const Prepared& pr, cudaStream_t s, Counters& h) {
+  STC_CUDA(cudaMemcpyAsync(&h, pr.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaStreamSynchronize(s));
+  return status_word(h.status);
+}
+
+// Peak device bytes of the GLOBAL strategy for these counts.
+uint64_t global_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t ns, uint64_t P, double alpha) {
+  const uint64_t target = std::min<uint64_t>(P, pl.F);
+  const uint64_t cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)((double)target / alpha) + 1));
+  const uint64_t out_cap = std::min(target, cap);
+  uint64_t b = sizeof(Counters) + pl.K * 4 * 3 + (uint64_t)scan_scratch_elems((int64_t)pl.K) * 4;
+  b += (uint64_t)nY * 16 + (uint64_t)nX * 24;
+  b += (ns + 1) * 8 + (uint64_t)scan_scratch_elems((int64_t)ns) * 8;
+  b += cap * 16 + out_cap * (4ull * pl.oz + 8);
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stc_status_string(stc_status s) {
+  switch (s) {
+    case STC_OK: return "ok";
+    case STC_ERR_INVALID_ARG: return "invalid argument";
+    case STC_ERR_SHAPE_MISMATCH: return "paired modes have different lengths";
+    case STC_ERR_KEY_OVERFLOW: return "key space exceeds 64 bits";
+    case STC_ERR_OUT_OF_MEMORY: return "out of device memory or over budget";
+    case STC_ERR_TABLE_FULL: return "accumulation table full";
+    case STC_ERR_TIMEOUT: return "timeout";
+    case STC_ERR_CUDA: return "CUDA error";
+    case STC_ERR_COORD_OUT_OF_RANGE: return "coordinate out of range";
+    case STC_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* stc_last_error(void) { return g_last_error.c_str(); }
+
+stc_status stc_create(stc_ctx** out, int device, size_t mem_budget_bytes) {
+  if (!out) return fail(STC_ERR_INVALID_ARG, "ctx is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  STC_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(STC_ERR_INVALID_ARG, "device %d of %d", device, ndev);
+  DeviceGuard g(device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", device);
+  stc_ctx* c = new stc_ctx;
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (e == cudaSuccess) e = cudaMemPoolCreate(&c->pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t keep_all = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep_all);
+  }
+  if (e != cudaSuccess) {
+    if (c->pool) cudaMemPoolDestroy(c->pool);
+    delete c;
+    return fail(STC_ERR_CUDA, "context set-up failed: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return STC_OK;
+}
+
+stc_status stc_destroy(stc_ctx* ctx) {
+  if (!ctx) return fail(STC_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->live_results.load() != 0)
+    return fail(STC_ERR_INVALID_ARG, "%lld results of this context are still alive",
+                (long long)ctx->live_results.load());
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  cudaMemPoolDestroy(ctx->pool);
+  delete ctx;
+  return STC_OK;
+}
+
+stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m, const int32_t* cx,
+                        const int32_t* cy, const int32_t* out_order, const stc_opts* opts, void* stream,
+                        stc_result** out) {
+  if (!ctx || !out) return fail(STC_ERR_INVALID_ARG, "ctx or out is NULL");
+  *out = nullptr;
+  Plan pl;
+  STC_TRY(make_plan(X, Y, m, cx, cy, out_order, pl));
+  const stc_opts o = opts ? *opts : stc_opts{};
+  const double alpha = (o.load_factor > 0.0) ? o.load_factor : 0.5;
+  if (!(alpha > 0.0 && alpha <= 0.9)) return fail(STC_ERR_INVALID_ARG, "load_factor %g outside (0, 0.9]", alpha);
+  if (o.strategy < 0 || o.strategy > STC_STRATEGY_GROUPED)
+    return fail(STC_ERR_INVALID_ARG, "unknown strategy %d", o.strategy);
+  if (o.strategy == STC_STRATEGY_GROUPED) return fail(STC_ERR_UNSUPPORTED, "grouped strategy not built yet");
+
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(ctx, s);
+  StageTimer tm;
+  tm.start(o.record_times != 0, s);
+  take_launches();
+
+  Prepared pr;
+  STC_TRY(prepare(ctx, ar, X, Y, pl, false, s, tm, pr));
+  Counters h{};
+  STC_TRY(read_counters(pr, s, h));
+  tm.mark(3);
+
+  stc_result* r = new stc_result;
+  r->ctx = ctx;
+  r->stream = s;
+  r->order = pl.oz;
+  r->shape = pl.zshape;
+  r->stats.products = h.P;
+  r->stats.survivors = h.ns;
+  r->stats.strategy = STC_STRATEGY_GLOBAL;
+
+  if (h.P > 0) {
+    const uint64_t target = std::min<uint64_t>(h.P, pl.F);
+    const uint64_t cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)((double)target / alpha) + 1));
+    const uint64_t out_cap = std::min(target, cap);
+    GlobalTable t{};
+    u64* wpre = nullptr;
+    u64* wscr = nullptr;
+    stc_status st = STC_OK;
+    auto run = [&]() -> stc_status {
+      STC_TRY(ar.alloc(&t.keys, cap));
+      STC_TRY(ar.alloc(&t.vals, cap));
+      t.mask = cap - 1;
+      STC_TRY(ar.alloc(&wpre, (size_t)h.ns + 1));
+      STC_TRY(ar.alloc(&wscr, (size_t)scan_scratch_elems((int64_t)h.ns)));
+      STC_TRY(ar.alloc(&r->coords, out_cap * (size_t)pl.oz));
+      STC_TRY(ar.alloc(&r->vals, out_cap));
+      STC_CUDA(cudaMemsetAsync(t.keys, 0xff, cap * sizeof(u64), s));
+      STC_CUDA(cudaMemsetAsync(t.vals, 0, cap * sizeof(double), s));
+      STC_CUDA(scan_u32_u64(pr.sv.w, wpre, (int64_t)h.ns, wscr, s));
+      tm.mark(3);
+      STC_CUDA(launch_expand_global(wpre, (int64_t)h.ns, h.P, pr.sv, pr.yfk, pr.yv, pl.FY, t, &pr.ctr->status,
+                                    ctx->sms, s));
+      tm.mark(4);
+      STC_CUDA(launch_compact_global(t, pl.op, r->coords, r->vals, out_cap, &pr.ctr->nz, &pr.ctr->status, ctx->sms,
+                                     s));
+      tm.mark(5);
+      Counters h2{};
+      STC_TRY(read_counters(pr, s, h2));
+      r->nnz = (int64_t)h2.nz;
+      return STC_OK;
+    };
+    st = run();
+    if (st != STC_OK) {
+      delete r;  // its blocks are still owned by the arena and are released with it
+      return st;
+    }
+    r->bytes = ar.keep(r->coords) + ar.keep(r->vals);
+    r->stats.out_capacity = out_cap;
+    r->stats.table_slots = cap;
+  }
+  tm.collect(r->stats);
+  r->stats.launches = take_launches();
+  ctx->live_results++;
+  *out = r;
+  return STC_OK;
+}
+
+stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m, const int32_t* cx,
+                     const int32_t* cy, void* stream, uint64_t* products, uint64_t* bytes_bound) {
+  if (!ctx) return fail(STC_ERR_INVALID_ARG, "ctx is NULL");
+  Plan pl;
+  STC_TRY(make_plan(X, Y, m, cx, cy, nullptr, pl));
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(ctx, s);
+  StageTimer tm;
+  Prepared pr;
+  STC_TRY(prepare(ctx, ar, X, Y, pl, false, s, tm, pr));
+  Counters h{};
+  STC_TRY(read_counters(pr, s, h));
+  if (products) *products = h.P;
+  if (bytes_bound) *bytes_bound = global_bytes(pl, X->nnz, Y->nnz, h.ns, h.P, 0.5);
+  return STC_OK;
+}
+
+stc_status stc_linearize(stc_ctx* ctx, const stc_coo* T, int32_t nmodes, const int32_t* modes, uint64_t* keys_out,
+                         void* stream) {
+  if (!ctx) return fail(STC_ERR_INVALID_ARG, "ctx is NULL");
+  STC_TRY(check_coo(T, "T"));
+  if (nmodes < 0 || nmodes > T->order || (nmodes > 0 && !modes))
+    return fail(STC_ERR_INVALID_ARG, "bad mode list");
+  if (T->nnz > 0 && !keys_out) return fail(STC_ERR_INVALID_ARG, "keys_out is NULL");
+  KeyPlan p{};
+  p.order = T->order;
+  for (int j = 0; j < T->order; j++) p.size[j] = T->shape[j];
+  bool seen[STC_MAX_ORDER] = {};
+  unsigned __int128 acc = 1;
+  for (int i = nmodes - 1; i >= 0; i--) {
+    if (modes[i] < 0 || modes[i] >= T->order || seen[modes[i]]) return fail(STC_ERR_INVALID_ARG, "bad mode list");
+    seen[modes[i]] = true;
+    p.cstride[modes[i]] = (uint64_t)acc;
+    acc *= (unsigned __int128)T->shape[modes[i]];
+    if (acc > (unsigned __int128)UINT64_MAX) return fail(STC_ERR_KEY_OVERFLOW, "key space exceeds 2^64");
+  }
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(ctx, s);
+  uint32_t* status = nullptr;
+  STC_TRY(ar.alloc(&status, 1));
+  STC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  STC_CUDA(launch_linearize(T->coords, T->nnz, p, reinterpret_cast<u64*>(keys_out), status, ctx->sms, s));
+  uint32_t h = 0;
+  STC_CUDA(cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaStreamSynchronize(s));
+  return status_word(h);
+}
+
+stc_status stc_group_keys(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t k, uint32_t* offsets_out,
+                          uint32_t* perm_out, void* stream) {
+  if (!ctx) return fail(STC_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0 || n > STC_MAX_NNZ) return fail(STC_ERR_INVALID_ARG, "n = %lld out of range", (long long)n);
+  if (k > kMaxDirectBins) return fail(STC_ERR_UNSUPPORTED, "k = %llu exceeds 2^26", (unsigned long long)k);
+  if (!offsets_out || (n > 0 && (!keys || !perm_out))) return fail(STC_ERR_INVALID_ARG, "NULL pointer");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(ctx, s);
+  uint32_t *cnt = nullptr, *cur = nullptr, *scr = nullptr, *status = nullptr;
+  STC_TRY(ar.alloc(&status, 1));
+  STC_TRY(ar.alloc(&cnt, k));
+  STC_TRY(ar.alloc(&cur, k));
+  STC_TRY(ar.alloc(&scr, (size_t)scan_scratch_elems((int64_t)k)));
+  STC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  if (k) STC_CUDA(cudaMemsetAsync(cnt, 0, k * sizeof(uint32_t), s));
+  const u64* kk = reinterpret_cast<const u64*>(keys);
+  STC_CUDA(launch_key_count(kk, n, k, cnt, status, ctx->sms, s));
+  STC_CUDA(scan_u32(cnt, offsets_out, (int64_t)k, scr, s));
+  if (k) STC_CUDA(cudaMemcpyAsync(cur, offsets_out, k * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  STC_CUDA(launch_key_scatter(kk, n, k, cur, perm_out, ctx->sms, s));
+  uint32_t h = 0;
+  STC_CUDA(cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaStreamSynchronize(s));
+  return status_word(h);
+}
+
+stc_status stc_result_info(const stc_result* r, int64_t* nnz, int32_t* order, const int64_t** shape) {
+  if (!r) return fail(STC_ERR_INVALID_ARG, "result is NULL");
+  if (nnz) *nnz = r->nnz;
+  if (order) *order = r->order;
+  if (shape) *shape = r->shape.empty() ? nullptr : r->shape.data();
+  return STC_OK;
+}
+
+stc_status stc_result_data(const stc_result* r, const int32_t** coords, const double** vals) {
+  if (!r) return fail(STC_ERR_INVALID_ARG, "result is NULL");
+  if (coords) *coords = r->coords;
+  if (vals) *vals = r->vals;
+  return STC_OK;
+}
+
+stc_status stc_result_stats(const stc_result* r, stc_stats* stats) {
+  if (!r || !stats) return fail(STC_ERR_INVALID_ARG, "NULL argument");
+  *stats = r->stats;
+  return STC_OK;
+}
+
+stc_status stc_result_free(stc_result* r) {
+  if (!r) return STC_OK;
+  DeviceGuard g(r->ctx->device);
+  if (r->coords) cudaFreeAsync(r->coords, r->stream);
+  if (r->vals) cudaFreeAsync(r->vals, r->stream);
+  r->ctx->held -= r->bytes;
+  r->ctx->live_results--;
+  delete r;
+  return STC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Internal definitions shared by the library's CUDA translation units: key plans, status
+// bits, hashing, warp helpers. Nothing here is part of the public ABI (include/stc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "stc.h"
+
+namespace stc {
+
+constexpr int kMaxOrder = STC_MAX_ORDER;
+constexpr int kMaxOutOrder = 2 * STC_MAX_ORDER;
+constexpr uint64_t kEmpty64 = ~0ull;       // empty slot of a 64-bit-key table
+constexpr uint32_t kEmpty32 = ~0u;         // empty slot of a 32-bit-key table
+constexpr uint64_t kMaxDirectBins = 1ull << 26;  // largest key space grouped by direct counting
+
+// Bits a kernel raises in the device status word; the host maps them to stc_status.
+enum : uint32_t {
+  kStatCoordRange = 1u,   // an input coordinate was out of range (entry skipped)
+  kStatTableFull = 2u,    // a probe sequence ran through the whole table
+  kStatOutOverflow = 4u,  // an output position past the allocated capacity (entry dropped)
+  kStatTimeout = 8u,      // a bounded wait gave up
+};
+
+// How one input tensor's coordinates map to its two keys (Section 2.3.1, the LN key):
+// ckey = sum_j coord[j] * cstride[j] (contract modes, in the order of the contract list),
+// fkey = sum_j coord[j] * fstride[j] (free modes, ascending). A mode has a nonzero stride
+// in exactly one of the two. size[] bounds-checks each coordinate.
+struct KeyPlan {
+  int32_t order;
+  int32_t pad_;
+  int64_t size[kMaxOrder];
+  uint64_t cstride[kMaxOrder];
+  uint64_t fstride[kMaxOrder];
+};
+
+// How an output key zkey = fX * F_Y + fY decodes into output coordinates. Output mode q is
+// (zkey / div[q]) % mod[q]; when every length is a power of two, (zkey >> shift[q]) & (mod[q]-1).
+struct OutPlan {
+  int32_t order;
+  int32_t pow2;
+  uint64_t div[kMaxOutOrder];
+  uint64_t mod[kMaxOutOrder];
+  uint32_t shift[kMaxOutOrder];
+};
+
+// MurmurHash3's 64-bit finaliser (fmix64, Austin Appleby, public domain): a bijective
+// mixer, so distinct keys never share a home slot pattern by construction of the key.
+__device__ __forceinline__ uint64_t mix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// MurmurHash3's 32-bit finaliser (fmix32).
+__device__ __forceinline__ uint32_t mix32(uint32_t k) {
+  k ^= k >> 16;
+  k *= 0x85ebca6bu;
+  k ^= k >> 13;
+  k *= 0xc2b2ae35u;
+  k ^= k >> 16;
+  return k;
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Reads coordinate row i of a [n][ORDER] int32 array and forms its contract and free
+// keys. Returns false if any coordinate is outside its mode.
+template <int ORDER, bool VEC>
+__device__ __forceinline__ bool row_keys(const int32_t* __restrict__ coords, int64_t i,
+                                         const KeyPlan& p, uint64_t& ck, uint64_t& fk) {
+  int32_t c[ORDER > 0 ? ORDER : 1];
+  if constexpr (ORDER == 4 && VEC) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(coords) + i);
+    c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+  } else if constexpr (ORDER == 2 && VEC) {
+    const int2 v = __ldg(reinterpret_cast<const int2*>(coords) + i);
+    c[0] = v.x; c[1] = v.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < ORDER; j++) c[j] = __ldg(coords + i * ORDER + j);
+  }
+  bool ok = true;
+  ck = 0;
+  fk = 0;
+#pragma unroll
+  for (int j = 0; j < ORDER; j++) {
+    ok &= (c[j] >= 0) & ((int64_t)c[j] < p.size[j]);
+    ck += (uint64_t)(uint32_t)c[j] * p.cstride[j];
+    fk += (uint64_t)(uint32_t)c[j] * p.fstride[j];
+  }
+  return ok;
+}
+
+// Output coordinate q of an output key.
+__device__ __forceinline__ int32_t out_coord(uint64_t zkey, const OutPlan& op, int q) {
+  if (op.pow2) return (int32_t)((zkey >> op.shift[q]) & (op.mod[q] - 1));
+  if (zkey <= 0xffffffffull && op.div[q] <= 0xffffffffull)
+    return (int32_t)(((uint32_t)zkey / (uint32_t)op.div[q]) % (uint32_t)op.mod[q]);
+  return (int32_t)((zkey / op.div[q]) % op.mod[q]);
+}
+
+// Writes the output coordinates of zkey to dst[0..order).
+__device__ __forceinline__ void store_coords(uint64_t zkey, const OutPlan& op, int32_t* __restrict__ dst) {
+  if (op.order == 4 && op.pow2 && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+    int4 v;
+    v.x = (int32_t)((zkey >> op.shift[0]) & (op.mod[0] - 1));
+    v.y = (int32_t)((zkey >> op.shift[1]) & (op.mod[1] - 1));
+    v.z = (int32_t)((zkey >> op.shift[2]) & (op.mod[2] - 1));
+    v.w = (int32_t)((zkey >> op.shift[3]) & (op.mod[3] - 1));
+    *reinterpret_cast<int4*>(dst) = v;
+    return;
+  }
+#pragma unroll 1
+  for (int q = 0; q < op.order; q++) dst[q] = out_coord(zkey, op, q);
+}
+
+// Warp-aggregated reservation of `pred ? 1 : 0` slots from a global counter. All 32 lanes
+// must call it together. Returns this lane's position (meaningful only where pred).
+template <typename T>
+__device__ __forceinline__ T warp_reserve(bool pred, T* counter) {
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  T base = 0;
+  if (mask) {
+    const int leader = __ffs(mask) - 1;
+    if ((int)lane_id() == leader) base = atomicAdd(counter, (T)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+  }
+  return base + (T)__popc(mask & lanemask_lt());
+}
+
+}  // namespace stc

@@ -1,0 +1,71 @@
+// Host-side launchers of the library's kernels. Internal; the public ABI is include/stc.h.
+#pragma once
+
+#include "common.cuh"
+
+namespace stc {
+
+using u64 = unsigned long long;
+
+// Kernels launched by the calling thread since the last take_launches() (for the stats).
+void note_launch(unsigned n = 1);
+unsigned take_launches();
+
+// ------------------------------------------------------------------ scans (scan.cu)
+// Exclusive prefix sums: out[0] = 0, out[i] = in[0] + ... + in[i-1], out[n] = total.
+// `scratch` holds scan_scratch_elems(n) elements of the output type.
+int64_t scan_scratch_elems(int64_t n);
+cudaError_t scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* scratch, cudaStream_t s);
+cudaError_t scan_u32_u64(const uint32_t* in, u64* out, int64_t n, u64* scratch, cudaStream_t s);
+cudaError_t scan_u64(const u64* in, u64* out, int64_t n, u64* scratch, cudaStream_t s);
+
+// ------------------------------------------------------------------ preparation (prep.cu)
+// Contract key of every entry (the LN key of the contract modes): keys[i] = ckey(i).
+cudaError_t launch_linearize(const int32_t* coords, int64_t n, const KeyPlan& p, u64* keys,
+                             uint32_t* status, int sms, cudaStream_t s);
+
+// Counting sort of arbitrary keys in [0, k): count, then scatter through a cursor copy of
+// the offsets. perm[pos] = input index.
+cudaError_t launch_key_count(const u64* keys, int64_t n, u64 k, uint32_t* cnt, uint32_t* status,
+                             int sms, cudaStream_t s);
+cudaError_t launch_key_scatter(const u64* keys, int64_t n, u64 k, uint32_t* cursor, uint32_t* perm,
+                               int sms, cudaStream_t s);
+
+// Group Y by contract key (Section 4.2): histogram of ckey, then (after a scan) a scatter
+// of each entry's free key and value into its key's run.
+cudaError_t launch_y_count(const int32_t* coords, int64_t n, const KeyPlan& p, uint32_t* cnt,
+                           uint32_t* status, int sms, cudaStream_t s);
+cudaError_t launch_y_scatter(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
+                             uint32_t* cursor, u64* yfk, double* yv, int sms, cudaStream_t s);
+
+// X entries whose contract key has a non-empty Y run ("survivors"), compacted, with the
+// run they will read and the total product count P (Section 4.3).
+struct Survivors {
+  u64* fk;          // X free key
+  uint32_t* ystart; // first slot of the matching Y run
+  uint32_t* w;      // run length = products this entry makes
+  double* v;        // X value
+  unsigned* count;  // number of survivors (device counter)
+};
+// With gcnt/gbound non-null, also counts survivors per X free key and sums their run
+// lengths per X free key (the per-group bound of Section 4.3).
+cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
+                            const uint32_t* yoff, Survivors sv, u64* P, uint32_t* gcnt, u64* gbound,
+                            uint32_t* status, int sms, cudaStream_t s);
+
+// ------------------------------------------------------------------ one global table (global.cu)
+struct GlobalTable {
+  u64* keys;    // [cap], kEmpty64 when free
+  double* vals; // [cap]
+  u64 mask;     // cap - 1, cap a power of two
+};
+// Expansion with a merge-path split over the survivors' product prefix `wpre` (ns+1
+// entries, wpre[ns] = P): every CTA takes an equal share of the P products.
+cudaError_t launch_expand_global(const u64* wpre, int64_t ns, u64 P, Survivors sv, const u64* yfk,
+                                 const double* yv, u64 FY, GlobalTable t, uint32_t* status, int sms,
+                                 cudaStream_t s);
+// Occupied slots -> COO output (coordinates decoded from the key).
+cudaError_t launch_compact_global(GlobalTable t, const OutPlan& op, int32_t* coords, double* vals,
+                                  u64 out_cap, u64* nz, uint32_t* status, int sms, cudaStream_t s);
+
+}  // namespace stc

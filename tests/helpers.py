@@ -70,7 +70,7 @@ def dense_contract(p: Problem, kind: str = "vals") -> np.ndarray:
 def canonical(coords: np.ndarray, *cols: np.ndarray):
     """Sort rows of ``coords`` lexicographically and apply the same order to ``cols``."""
     coords = np.asarray(coords)
-    if coords.ndim != 2 or coords.shape[1] == 0 or coords.shape[0] == 0:
+    if coords.ndim != 2 or coords.shape[1] == 0 or coords.shape[0] <= 1:
         return (coords,) + tuple(np.asarray(c) for c in cols)
     order = np.lexsort(coords.T[::-1])
     return (coords[order],) + tuple(np.asarray(c)[order] for c in cols)

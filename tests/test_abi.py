@@ -1,0 +1,81 @@
+"""CPU-side checks of the boundary: the library builds for sm_103a, loads, and exports every
+function include/stc.h declares; the Python binding declares the same set; the oracle
+library exports what its wrapper uses. No compute call is made (no GPU here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "stc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(stc_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2410_10094_gb300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    fns = header_functions()
+    for name in ["stc_create", "stc_destroy", "stc_contract", "stc_count", "stc_linearize", "stc_group_keys",
+                 "stc_result_info", "stc_result_data", "stc_result_stats", "stc_result_free",
+                 "stc_status_string", "stc_last_error"]:
+        assert name in fns
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (stc_[a-z_0-9]+)$", out, flags=re.M))
+    missing = [f for f in header_functions() if f not in exported]
+    assert not missing, f"declared in stc.h but not exported: {missing}"
+    lib = ctypes.CDLL(libpath)
+    for f in header_functions():
+        assert getattr(lib, f) is not None
+
+
+def test_binding_wraps_every_declared_symbol():
+    from paper_2410_10094_gb300 import binding
+
+    assert sorted(binding.EXPORTS) == header_functions()
+
+
+def test_library_is_built_for_sm_103a(libpath):
+    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_status_strings_without_gpu(libpath):
+    from paper_2410_10094_gb300 import binding
+
+    binding.load(libpath)
+    assert binding.stc_status_string(0) == "ok"
+    assert "coordinate" in binding.stc_status_string(8)
+
+
+def test_oracle_exports():
+    import oracle
+
+    lib = ctypes.CDLL(oracle.build())
+    for f in ["oracle_contract", "oracle_ln_key", "oracle_counting_sort", "oracle_first_seen_ids",
+              "oracle_group_bounds", "oracle_table_slots"]:
+        assert getattr(lib, f) is not None
+
+
+def test_library_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_2410_10094_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "stc_oracle" not in txt, f

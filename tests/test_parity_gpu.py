@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle on the same
+seeded inputs. Coordinates and nnz must match bit-exactly, values within
+1e-12 * sum|x*y| per output (bit-exactly where at most two products meet)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import assert_matches_oracle, gpu_contract, result_host, to_dev
+from helpers import REL_TOL
+
+pytestmark = pytest.mark.gpu
+
+STRATEGIES = [1]  # GLOBAL; GROUPED joins once built
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_10094_gb300 import build
+
+    build.build()
+    import paper_2410_10094_gb300 as stc
+
+    stc.load()
+    return stc
+
+
+def check(p, **kw):
+    ref = oracle.contract(p.X, p.Y, p.cx, p.cy, p.out_order)
+    res = gpu_contract(p, **kw)
+    c, v = result_host(res)
+    assert_matches_oracle(c, v, ref)
+    assert res.stats.products == ref.products
+    assert res.shape == ref.shape
+    return res, ref
+
+
+# ------------------------------------------------------------------ small and random cases
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_plain_small_workload(strategy):
+    """64^3 tensors with 5,000 distinct entries each, X mode 2 with Y mode 0 (full parity)."""
+    res, ref = check(W.plain_small(), strategy=strategy)
+    assert ref.nnz > 300_000
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+@pytest.mark.parametrize("seed", range(40))
+def test_random_cases(seed, strategy):
+    rng = W.rng_for(5000 + seed)
+    p = W.random_case(rng, max_order=5, max_size=6, max_nnz=120)
+    check(p, strategy=strategy)
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_several_tiles_ragged_non_pow2(strategy):
+    """Non-power-of-two mode lengths (division decode path) and a product count that spans
+    many 2048-product tiles with a ragged last tile."""
+    rng = W.rng_for(6001)
+    X = W.uniform_coo(rng, (37, 53, 29), 60_000)
+    Y = W.uniform_coo(rng, (29, 41, 7), 9_000)
+    res, ref = check(W.Problem(X, Y, (2,), (0,)), strategy=strategy)
+    assert ref.products % 2048 != 0 and ref.products > 20 * 2048
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_heavy_duplicates(strategy):
+    """Few cells, many repeated coordinates: many products per output (summation order matters)."""
+    rng = W.rng_for(6002)
+    X = W.uniform_coo(rng, (4, 6, 5), 20_000)
+    Y = W.uniform_coo(rng, (5, 3), 5_000)
+    res, ref = check(W.Problem(X, Y, (2,), (0,)), strategy=strategy)
+    assert ref.cnt.max() > 1000
+
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_out_order_and_two_mode_pairing(strategy):
+    rng = W.rng_for(6003)
+    X = W.uniform_coo(rng, (9, 16, 8, 4), 8_000)
+    Y = W.uniform_coo(rng, (4, 12, 16), 3_000)
+    check(W.Problem(X, Y, (3, 1), (0, 2), out_order=(2, 0, 1)), strategy=strategy)
+
+
+def test_empty_and_degenerate():
+    rng = W.rng_for(6004)
+    A = W.uniform_coo(rng, (5, 6), 0)
+    B = W.uniform_coo(rng, (6, 7), 50)
+    for p in [W.Problem(A, B, (1,), (0,)), W.Problem(B, W.uniform_coo(rng, (7, 3), 0), (1,), (0,))]:
+        res = gpu_contract(p)
+        assert res.nnz == 0 and res.stats.products == 0
+    # no common contract key at all
+    X = W.COO((4, 8), [[0, 1], [1, 1]], [1.0, 2.0])
+    Y = W.COO((8, 3), [[2, 0], [3, 1]], [1.0, 2.0])
+    assert gpu_contract(W.Problem(X, Y, (1,), (0,))).nnz == 0
+    # outer product (no paired modes)
+    check(W.Problem(W.uniform_coo(rng, (3, 5), 9), W.uniform_coo(rng, (4,), 3), (), ()))
+    # full contraction: order-0 output
+    X = W.uniform_coo(rng, (6, 7), 30)
+    Y = W.uniform_coo(rng, (7, 6), 30)
+    res, ref = check(W.Problem(X, Y, (0, 1), (1, 0)))
+    assert res.order == 0 and res.nnz == ref.nnz
+    # cancellation keeps the structural zero
+    X = W.COO((1, 2), [[0, 0], [0, 1]], [1.0, 1.0])
+    Y = W.COO((2, 1), [[0, 0], [1, 0]], [1.0, -1.0])
+    res, ref = check(W.Problem(X, Y, (1,), (0,)))
+    assert res.nnz == 1 and float(res.vals[0]) == 0.0
+
+
+def test_wide_keys_non_pow2():
+    """Output keys above 2^32 with non-power-of-two lengths (64-bit division decode)."""
+    rng = W.rng_for(6005)
+    X = W.uniform_coo(rng, (1_000_003, 7, 999_983), 3_000)
+    Y = W.uniform_coo(rng, (7, 65_537), 500)
+    check(W.Problem(X, Y, (1,), (0,)))
+
+
+def test_errors():
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(6006)
+    X = W.uniform_coo(rng, (5, 6), 10)
+    Y = W.uniform_coo(rng, (7, 3), 10)
+    with pytest.raises(stc.StcError) as e:
+        stc.contract(to_dev(X), to_dev(Y), (1,), (0,))
+    assert e.value.status == 2
+    bad = W.COO((5, 6), [[0, 6]], [1.0])
+    Y2 = W.uniform_coo(rng, (6, 3), 10)
+    with pytest.raises(stc.StcError) as e:
+        stc.contract(to_dev(bad), to_dev(Y2), (1,), (0,))
+    assert e.value.status == 8
+    big = W.COO((2 ** 31, 2 ** 31, 4), [[0, 0, 0]], [1.0])
+    Yb = W.COO((4, 2 ** 31), [[0, 0]], [1.0])
+    with pytest.raises(stc.StcError) as e:
+        stc.contract(to_dev(big), to_dev(Yb), (2,), (0,))
+    assert e.value.status == 3
+    with pytest.raises(stc.StcError) as e:
+        stc.contract(to_dev(X), to_dev(W.uniform_coo(rng, (6, 3), 5)), (1,), (0,), out_order=(0, 0))
+    assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ step-level entry points
+
+def test_linearize_matches_oracle_ln_key():
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(6007)
+    T = W.uniform_coo(rng, (7, 300, 11, 5000), 40_000)
+    for modes in [(0,), (2, 1), (3, 0, 2), (0, 1, 2, 3), (1, 3)]:
+        got = stc.linearize(to_dev(T), modes).cpu().numpy().view(np.uint64)
+        ref = oracle.ln_key(T.shape, T.coords, modes)
+        np.testing.assert_array_equal(got, ref)
+    g = __import__("helpers").golden("ln_key_fig3.json")
+    Tg = W.COO(tuple(g["shape"]), g["coords"], [1.0])
+    assert stc.linearize(to_dev(Tg), g["modes"]).cpu().tolist() == g["expect"]
+
+
+def test_group_keys_matches_oracle_counting_sort():
+    import torch
+
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(6008)
+    for n, k in [(0, 5), (1, 1), (5000, 7), (300_000, 65_536), (100_000, 1_000_003)]:
+        keys = rng.integers(0, k, n).astype(np.uint64)
+        off, perm = stc.group_keys(torch.from_numpy(keys.view(np.int64)).cuda(), k)
+        off = off.cpu().numpy().astype(np.int64)
+        perm = perm.cpu().numpy().astype(np.int64)
+        ref_off, ref_perm = oracle.counting_sort(keys, k)
+        np.testing.assert_array_equal(off, ref_off)
+        np.testing.assert_array_equal(np.sort(perm), np.arange(n))
+        np.testing.assert_array_equal(keys[perm], keys[ref_perm])
+        # the same members in every run (order inside a run is unspecified)
+        for v in np.unique(keys)[:50]:
+            a, b = ref_off[v], ref_off[v + 1]
+            assert sorted(perm[a:b]) == sorted(ref_perm[a:b])
+    g = __import__("helpers").golden("counting_sort_fig5.json")
+    off, _ = stc.group_keys(torch.tensor(g["keys"], dtype=torch.int64).cuda(), g["k"])
+    assert off.cpu().tolist() == g["expect_offsets"]
+
+
+def test_count_matches_oracle_products():
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(6009)
+    X = W.uniform_coo(rng, (40, 30, 20), 50_000)
+    Y = W.uniform_coo(rng, (20, 30, 9), 20_000)
+    P, nbytes = stc.count(to_dev(X), to_dev(Y), (2, 1), (0, 1))
+    assert P == oracle.group_bounds(X, Y, (2, 1), (0, 1)).total
+    assert nbytes > 0
+    g = __import__("helpers").golden("group_bound_sec43.json")
+    Xg = W.COO(tuple(g["X"]["shape"]), g["X"]["coords"], g["X"]["vals"])
+    Yg = W.COO(tuple(g["Y"]["shape"]), g["Y"]["coords"], g["Y"]["vals"])
+    P, _ = stc.count(to_dev(Xg), to_dev(Yg), g["cx"], g["cy"])
+    assert P == g["expect_bound"]
+
+
+# ------------------------------------------------------------------ benchmark-sized workloads
+
+@pytest.mark.parametrize("strategy", STRATEGIES)
+def test_imbalanced_zipf_full(strategy):
+    """X 4096x512x512 with 2e7 entries, Y 512x512x64 with 2e4 Zipf(1.2) contract keys:
+    full parity against the oracle."""
+    p = W.imbalanced()
+    check(p, strategy=strategy)
+
+
+def test_plain_large_sampled_rows():
+    """256^4 tensors with 5e6 entries each, X modes (2,3) with Y modes (0,1), in the launch
+    configuration the benchmark times: 48 sampled output rows (X free tuples) against the
+    oracle row by row, plus full-size properties (P exact, nnz <= P, unique coordinates,
+    the global checksum's closed form)."""
+    import torch
+
+    p = W.plain_large()
+    res = gpu_contract(p)
+    ref_groups = oracle.group_bounds(p.X, p.Y, p.cx, p.cy)
+    assert res.stats.products == ref_groups.total
+    assert res.nnz <= ref_groups.total
+    rng = W.rng_for(6010)
+    rows = p.X.coords[rng.integers(0, p.X.nnz, 48)][:, :2].astype(np.int64)
+    row_keys = np.unique(rows[:, 0] * 256 + rows[:, 1])
+    xkey = p.X.coords[:, 0].astype(np.int64) * 256 + p.X.coords[:, 1]
+    ref = oracle.contract(p.X.take(np.isin(xkey, row_keys)), p.Y, p.cx, p.cy)
+    zc = res.coords
+    zkey = zc[:, 0].to(torch.int64) * 256 + zc[:, 1].to(torch.int64)
+    sel = torch.isin(zkey, torch.from_numpy(row_keys).cuda())
+    assert_matches_oracle(zc[sel].cpu().numpy(), res.vals[sel].cpu().numpy(), ref)
+    # every output coordinate appears once
+    full = ((zc[:, 0].to(torch.int64) * 256 + zc[:, 1]) * 256 + zc[:, 2]) * 256 + zc[:, 3]
+    assert torch.unique(full).numel() == res.nnz
+    # closed form of the checksum: sum_Z z = sum_c (sum_{x: c_x=c} x) (sum_{y: c_y=c} y)
+    cxk = p.X.coords[:, 2].astype(np.int64) * 256 + p.X.coords[:, 3]
+    cyk = p.Y.coords[:, 0].astype(np.int64) * 256 + p.Y.coords[:, 1]
+    sx = np.bincount(cxk, weights=p.X.vals, minlength=65536)
+    sy = np.bincount(cyk, weights=p.Y.vals, minlength=65536)
+    ax = np.bincount(cxk, weights=np.abs(p.X.vals), minlength=65536)
+    ay = np.bincount(cyk, weights=np.abs(p.Y.vals), minlength=65536)
+    total = float(res.vals.sum())
+    assert abs(total - float(sx @ sy)) <= REL_TOL * float(ax @ ay) * 10
