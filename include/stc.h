@@ -71,6 +71,9 @@ typedef struct stc_opts {
   int32_t strategy;       /* STC_STRATEGY_*; 0 = AUTO */
   int32_t record_times;   /* nonzero: time each stage with CUDA events (stc_result_stats) */
   double load_factor;     /* global-table load factor in (0, 0.9]; 0 = default 0.5 */
+  double group_load_factor; /* largest load of a per-group shared-memory table, in (0, 0.9];
+                               0 = default 0.5. A group of bound t goes to the smallest table
+                               class with t <= group_load_factor * slots. */
 } stc_opts;
 
 /* Per-call statistics of a finished contraction. */
@@ -119,6 +122,10 @@ stc_status stc_destroy(stc_ctx* ctx);
 stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t ncontract,
                         const int32_t* cx, const int32_t* cy, const int32_t* out_order,
                         const stc_opts* opts, void* stream, stc_result** out);
+
+/* Device bytes the context holds now (scratch of calls in flight + live results) and the
+ * number of live results. held_bytes and live_results may be NULL. */
+stc_status stc_ctx_stats(const stc_ctx* ctx, uint64_t* held_bytes, int64_t* live_results);
 
 /* The exact product count of the contraction (Section 4.3: each X entry meets exactly
  * count_Y[its contract key] Y entries) and the device bytes a stc_contract of the same

@@ -33,7 +33,8 @@ class stc_coo(C.Structure):
 
 
 class stc_opts(C.Structure):
-    _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double)]
+    _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double),
+                ("group_load_factor", C.c_double)]
 
 
 class stc_stats(C.Structure):
@@ -48,6 +49,7 @@ EXPORTS = {
     "stc_last_error": ([], C.c_char_p),
     "stc_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_size_t], C.c_int),
     "stc_destroy": ([C.c_void_p], C.c_int),
+    "stc_ctx_stats": ([C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int64)], C.c_int),
     "stc_contract": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
                       C.c_void_p, C.POINTER(stc_opts), C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
     "stc_count": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
@@ -104,6 +106,13 @@ def stc_create(device: int = 0, mem_budget_bytes: int = 0) -> int:
 
 def stc_destroy(ctx: int):
     check(load().stc_destroy(C.c_void_p(ctx)))
+
+
+def stc_ctx_stats(ctx: int):
+    """(device bytes held, live results) of a context."""
+    held, live = C.c_uint64(), C.c_int64()
+    check(load().stc_ctx_stats(C.c_void_p(ctx), C.byref(held), C.byref(live)))
+    return int(held.value), int(live.value)
 
 
 def _mode_array(v: Sequence[int]):
@@ -207,11 +216,24 @@ def stc_result_free(r: int):
 
 # ---------------------------------------------------------------- convenience layer
 
+class _Handle:
+    """Owns one stc_result; frees it when the last Result or tensor view lets go."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        h = getattr(self, "handle", 0)
+        if h and _lib is not None:
+            stc_result_free(h)
+            self.handle = 0
+
+
 class _DeviceArray:
     """Exposes library-owned device memory through __cuda_array_interface__; keeps the
-    owning result alive while any tensor views it."""
+    owning handle alive while any tensor views it."""
 
-    def __init__(self, owner, ptr: int, shape, typestr: str):
+    def __init__(self, owner: _Handle, ptr: int, shape, typestr: str):
         self._owner = owner
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
                                          "version": 3, "strides": None}
@@ -261,6 +283,7 @@ class Result:
     def __init__(self, handle: int):
         import torch
 
+        self._h = _Handle(handle)
         self.handle = handle
         self.nnz, self.order, self.shape = stc_result_info(handle)
         cp, vp = stc_result_data(handle)
@@ -268,27 +291,23 @@ class Result:
         self.stats = Stats(st.products, st.survivors, st.out_capacity, st.table_slots, st.groups, st.strategy,
                            st.launches, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))))
         if self.nnz and self.order:
-            self.coords = torch.as_tensor(_DeviceArray(self, cp, (self.nnz, self.order), "<i4"), device="cuda")
+            self.coords = torch.as_tensor(_DeviceArray(self._h, cp, (self.nnz, self.order), "<i4"), device="cuda")
         else:
             self.coords = torch.empty((self.nnz, self.order), dtype=torch.int32, device="cuda")
         if self.nnz:
-            self.vals = torch.as_tensor(_DeviceArray(self, vp, (self.nnz,), "<f8"), device="cuda")
+            self.vals = torch.as_tensor(_DeviceArray(self._h, vp, (self.nnz,), "<f8"), device="cuda")
         else:
             self.vals = torch.empty((0,), dtype=torch.float64, device="cuda")
 
-    def __del__(self):
-        h = getattr(self, "handle", 0)
-        if h and _lib is not None:
-            stc_result_free(h)
-            self.handle = 0
 
 
 def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, strategy: int = STRATEGY_AUTO,
-             load_factor: float = 0.0, record_times: bool = False, stream=None, ctx: Context = None) -> Result:
+             load_factor: float = 0.0, group_load_factor: float = 0.0, record_times: bool = False, stream=None,
+             ctx: Context = None) -> Result:
     """Z = X (x) Y (Eq. 2) on the GPU. X and Y are (shape, coords, vals) with coords a CUDA
     int32 [nnz, order] tensor and vals a CUDA float64 [nnz] tensor."""
     ctx = ctx or default_context()
-    o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor))
+    o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor), float(group_load_factor))
     return Result(stc_contract(ctx.handle, X, Y, cx, cy, out_order, o, stream))
 
 

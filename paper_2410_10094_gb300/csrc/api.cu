@@ -256,6 +256,7 @@ stc_status status_word(uint32_t st) {
   if (st & kStatTableFull) return fail(STC_ERR_TABLE_FULL, "an accumulation table overflowed");
   if (st & kStatOutOverflow) return fail(STC_ERR_TABLE_FULL, "output capacity exceeded");
   if (st & kStatTimeout) return fail(STC_ERR_TIMEOUT, "a bounded wait gave up");
+  if (st & kStatTooLarge) return fail(STC_ERR_UNSUPPORTED, "one X free group needs a table above 2^31 slots");
   return STC_OK;
 }
 
@@ -381,6 +382,119 @@ uint64_t global_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t ns, uint6
   return b;
 }
 
+
+// Counters of the grouping and binning passes, read back with the first host sync.
+struct GroupCounters {
+  uint32_t count[kMaxClasses + 1];
+  uint32_t pad_;
+  u64 huge_slots;
+  u64 out_cap;
+};
+
+// GROUPED strategy (Sections 4.1 and 4.3): survivors are counting-sorted by X free key,
+// each group is binned by its table size, and the class kernels accumulate one group per
+// CTA in shared memory and write its outputs directly.
+stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, const Plan& pl,
+                            const stc_opts& o, cudaStream_t s, StageTimer& tm, stc_result* r) {
+  const int64_t nX = X->nnz;
+  Prepared pr;
+  STC_TRY(prepare(ctx, ar, X, Y, pl, true, s, tm, pr));
+
+  const bool wide = pl.FY > 0xffffffffull;
+  const int ncls = wide ? kNumClasses64 : kNumClasses32;
+  const ClassShape* shapes = wide ? kClassShapes64 : kClassShapes32;
+  const double ga = (o.group_load_factor > 0.0) ? o.group_load_factor : 0.5;
+  const uint64_t maxg = std::min<uint64_t>(pl.FX, (uint64_t)std::max<int64_t>(nX, 1));
+
+  uint32_t *goff = nullptr, *gcur = nullptr, *scr = nullptr;
+  GroupedX gx{};
+  Bins b{};
+  GroupCounters* gc = nullptr;
+  STC_TRY(ar.alloc(&goff, pl.FX + 1));
+  STC_TRY(ar.alloc(&gcur, pl.FX));
+  STC_TRY(ar.alloc(&scr, (size_t)scan_scratch_elems((int64_t)pl.FX)));
+  STC_TRY(ar.alloc(&gx.ystart, (size_t)nX));
+  STC_TRY(ar.alloc(&gx.w, (size_t)nX));
+  STC_TRY(ar.alloc(&gx.v, (size_t)nX));
+  STC_TRY(ar.alloc(&gc, 1));
+  b.nclasses = ncls;
+  for (int c = 0; c < ncls; c++) {
+    b.tmax[c] = (u64)(ga * shapes[c].slots);
+    STC_TRY(ar.alloc(&b.list[c], maxg));
+  }
+  STC_TRY(ar.alloc(&b.huge_list, maxg));
+  STC_TRY(ar.alloc(&b.huge_off, maxg));
+  STC_TRY(ar.alloc(&b.huge_cap, maxg));
+  b.count = gc->count;
+  b.huge_slots = &gc->huge_slots;
+  b.out_cap = &gc->out_cap;
+  b.status = &pr.ctr->status;
+  STC_CUDA(cudaMemsetAsync(gc, 0, sizeof(GroupCounters), s));
+  STC_CUDA(scan_u32(pr.gcnt, goff, (int64_t)pl.FX, scr, s));
+  STC_CUDA(cudaMemcpyAsync(gcur, goff, pl.FX * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  STC_CUDA(launch_x_group_scatter(pr.sv, gcur, gx, nX, ctx->sms, s));
+  STC_CUDA(launch_bin_groups(pl.FX, pr.gcnt, pr.gbound, pl.FY, b, ctx->sms, s));
+  tm.mark(2);
+
+  Counters h{};
+  GroupCounters hg{};
+  STC_CUDA(cudaMemcpyAsync(&hg, gc, sizeof(GroupCounters), cudaMemcpyDeviceToHost, s));
+  STC_TRY(read_counters(pr, s, h));
+  tm.mark(3);
+  r->stats.products = h.P;
+  r->stats.survivors = h.ns;
+  uint64_t groups = 0;
+  for (int c = 0; c <= kMaxClasses; c++) groups += hg.count[c];
+  r->stats.groups = groups;
+  r->stats.table_slots = hg.huge_slots;
+  if (h.P == 0) return STC_OK;
+
+  const uint64_t out_cap = hg.out_cap;
+  HugeGroups hh{};
+  hh.count = hg.count[kMaxClasses];
+  hh.list = b.huge_list;
+  hh.off = b.huge_off;
+  hh.cap = b.huge_cap;
+  STC_TRY(ar.alloc(&r->coords, out_cap * (size_t)pl.oz));
+  STC_TRY(ar.alloc(&r->vals, out_cap));
+  if (hh.count) {
+    STC_TRY(ar.alloc(&hh.keys, hg.huge_slots));
+    STC_TRY(ar.alloc(&hh.vals, hg.huge_slots));
+    STC_CUDA(cudaMemsetAsync(hh.keys, 0xff, hg.huge_slots * sizeof(u64), s));
+    STC_CUDA(cudaMemsetAsync(hh.vals, 0, hg.huge_slots * sizeof(double), s));
+  }
+  GroupArgs a{};
+  a.goff = goff;
+  a.gx = gx;
+  a.yfk = pr.yfk;
+  a.yv = pr.yv;
+  a.FY = pl.FY;
+  a.op = pl.op;
+  a.coords = r->coords;
+  a.vals = r->vals;
+  a.out_cap = out_cap;
+  a.nz = &pr.ctr->nz;
+  a.status = &pr.ctr->status;
+  STC_CUDA(launch_group_classes(a, wide, b, hg.count, ctx->sms, s));
+  STC_CUDA(launch_group_huge(a, hh, ctx->sms, s));
+  tm.mark(4);
+  Counters h2{};
+  STC_TRY(read_counters(pr, s, h2));
+  r->nnz = (int64_t)h2.nz;
+  r->stats.out_capacity = out_cap;
+  r->bytes = ar.keep(r->coords) + ar.keep(r->vals);
+  return STC_OK;
+}
+
+// AUTO: one global table when the output key space is small (the table stays in L2),
+// per-group shared-memory tables when X's free keys can be counted directly.
+int pick_strategy(const Plan& pl, const stc_coo* X, int requested) {
+  if (requested != STC_STRATEGY_AUTO) return requested;
+  if (pl.F <= (1ull << 22)) return STC_STRATEGY_GLOBAL;
+  if (pl.FX <= kMaxDirectBins && pl.FX <= 16ull * (uint64_t)X->nnz + (1ull << 20)) return STC_STRATEGY_GROUPED;
+  return STC_STRATEGY_GLOBAL;
+}
+
 }  // namespace
 
 extern "C" {
@@ -457,7 +571,12 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
   if (!(alpha > 0.0 && alpha <= 0.9)) return fail(STC_ERR_INVALID_ARG, "load_factor %g outside (0, 0.9]", alpha);
   if (o.strategy < 0 || o.strategy > STC_STRATEGY_GROUPED)
     return fail(STC_ERR_INVALID_ARG, "unknown strategy %d", o.strategy);
-  if (o.strategy == STC_STRATEGY_GROUPED) return fail(STC_ERR_UNSUPPORTED, "grouped strategy not built yet");
+  if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
+    return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
+  const int strategy = pick_strategy(pl, X, o.strategy);
+  if (strategy == STC_STRATEGY_GROUPED && pl.FX > kMaxDirectBins)
+    return fail(STC_ERR_UNSUPPORTED, "X free key space %llu exceeds %llu bins", (unsigned long long)pl.FX,
+                (unsigned long long)kMaxDirectBins);
 
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
@@ -466,6 +585,25 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
   StageTimer tm;
   tm.start(o.record_times != 0, s);
   take_launches();
+
+  if (strategy == STC_STRATEGY_GROUPED) {
+    stc_result* r = new stc_result;
+    r->ctx = ctx;
+    r->stream = s;
+    r->order = pl.oz;
+    r->shape = pl.zshape;
+    r->stats.strategy = STC_STRATEGY_GROUPED;
+    const stc_status st = contract_grouped(ctx, ar, X, Y, pl, o, s, tm, r);
+    if (st != STC_OK) {
+      delete r;
+      return st;
+    }
+    tm.collect(r->stats);
+    r->stats.launches = take_launches();
+    ctx->live_results++;
+    *out = r;
+    return STC_OK;
+  }
 
   Prepared pr;
   STC_TRY(prepare(ctx, ar, X, Y, pl, false, s, tm, pr));
@@ -526,6 +664,13 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
   r->stats.launches = take_launches();
   ctx->live_results++;
   *out = r;
+  return STC_OK;
+}
+
+stc_status stc_ctx_stats(const stc_ctx* ctx, uint64_t* held_bytes, int64_t* live_results) {
+  if (!ctx) return fail(STC_ERR_INVALID_ARG, "ctx is NULL");
+  if (held_bytes) *held_bytes = ctx->held.load();
+  if (live_results) *live_results = ctx->live_results.load();
   return STC_OK;
 }
 

@@ -21,6 +21,7 @@ enum : uint32_t {
   kStatTableFull = 2u,    // a probe sequence ran through the whole table
   kStatOutOverflow = 4u,  // an output position past the allocated capacity (entry dropped)
   kStatTimeout = 8u,      // a bounded wait gave up
+  kStatTooLarge = 16u,    // one group's table would exceed 2^31 slots
 };
 
 // How one input tensor's coordinates map to its two keys (Section 2.3.1, the LN key):

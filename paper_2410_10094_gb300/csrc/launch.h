@@ -68,4 +68,68 @@ cudaError_t launch_expand_global(const u64* wpre, int64_t ns, u64 P, Survivors s
 cudaError_t launch_compact_global(GlobalTable t, const OutPlan& op, int32_t* coords, double* vals,
                                   u64 out_cap, u64* nz, uint32_t* status, int sms, cudaStream_t s);
 
+// ------------------------------------------------------------------ per-group tables (grouped.cu)
+constexpr int kMaxClasses = 5;
+
+struct ClassShape {
+  uint32_t slots;    // table slots in shared memory
+  uint32_t threads;  // threads per CTA
+};
+extern const ClassShape kClassShapes32[];  // 32-bit local keys (F_Y < 2^32)
+extern const ClassShape kClassShapes64[];  // 64-bit local keys
+extern const int kNumClasses32;
+extern const int kNumClasses64;
+
+// X survivors in group order: the entries of X free key g are [goff[g], goff[g+1]).
+struct GroupedX {
+  uint32_t* ystart;
+  uint32_t* w;
+  double* v;
+};
+
+// Output of the binning pass.
+struct Bins {
+  int nclasses;
+  u64 tmax[kMaxClasses];      // a group goes to the first class with t <= tmax
+  uint32_t* list[kMaxClasses];
+  uint32_t* count;            // [kMaxClasses + 1]; the last entry counts overflow groups
+  uint32_t* huge_list;        // overflow groups, their table offsets and capacities
+  u64* huge_off;
+  u64* huge_cap;
+  u64* huge_slots;            // total overflow-table slots
+  u64* out_cap;               // sum over groups of min(B_g, F_Y): bound on the output size
+  uint32_t* status;
+};
+
+struct GroupArgs {
+  const uint32_t* goff;
+  GroupedX gx;
+  const u64* yfk;
+  const double* yv;
+  u64 FY;
+  OutPlan op;
+  int32_t* coords;
+  double* vals;
+  u64 out_cap;
+  u64* nz;
+  uint32_t* status;
+};
+
+struct HugeGroups {
+  uint32_t count;
+  const uint32_t* list;
+  const u64* off;
+  const u64* cap;
+  u64* keys;
+  double* vals;
+};
+
+cudaError_t launch_x_group_scatter(Survivors sv, uint32_t* gcur, GroupedX gx, int64_t max_ns, int sms,
+                                   cudaStream_t s);
+cudaError_t launch_bin_groups(u64 FX, const uint32_t* gcnt, const u64* gbound, u64 FY, const Bins& b, int sms,
+                              cudaStream_t s);
+cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins& b, const uint32_t* counts,
+                                 int sms, cudaStream_t s);
+cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, int sms, cudaStream_t s);
+
 }  // namespace stc

@@ -11,7 +11,7 @@ from helpers import REL_TOL
 
 pytestmark = pytest.mark.gpu
 
-STRATEGIES = [1]  # GLOBAL; GROUPED joins once built
+STRATEGIES = [1, 2]  # one global table; per-X-free-group tables
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -84,13 +84,42 @@ def test_out_order_and_two_mode_pairing(strategy):
     check(W.Problem(X, Y, (3, 1), (0, 2), out_order=(2, 0, 1)), strategy=strategy)
 
 
+def test_grouped_overflow_groups():
+    """Groups whose bound exceeds every shared-memory class use the global overflow table."""
+    rng = W.rng_for(6011)
+    X = W.uniform_coo(rng, (3, 50), 3_000)
+    Y = W.uniform_coo(rng, (50, 100_000), 40_000)
+    res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2)
+    assert res.stats.table_slots > 0 and res.stats.strategy == 2
+
+
+def test_grouped_wide_local_keys():
+    """Y free key space above 2^32: per-group tables keyed on 64-bit local keys."""
+    rng = W.rng_for(6012)
+    X = W.uniform_coo(rng, (300, 7), 20_000)
+    Y = W.uniform_coo(rng, (7, 70_000, 70_000), 30_000)
+    res, ref = check(W.Problem(X, Y, (1,), (0,)))
+    assert res.stats.strategy == 2
+
+
+def test_grouped_load_factors_agree():
+    """The table class thresholds change only memory and speed, never the result."""
+    p = W.plain_small()
+    ref = oracle.contract(p.X, p.Y, p.cx, p.cy)
+    for ga in (0.25, 0.5, 0.75, 0.9):
+        res = gpu_contract(p, strategy=2, group_load_factor=ga)
+        c, v = result_host(res)
+        assert_matches_oracle(c, v, ref)
+
+
 def test_empty_and_degenerate():
     rng = W.rng_for(6004)
     A = W.uniform_coo(rng, (5, 6), 0)
     B = W.uniform_coo(rng, (6, 7), 50)
     for p in [W.Problem(A, B, (1,), (0,)), W.Problem(B, W.uniform_coo(rng, (7, 3), 0), (1,), (0,))]:
-        res = gpu_contract(p)
-        assert res.nnz == 0 and res.stats.products == 0
+        for strategy in STRATEGIES:
+            res = gpu_contract(p, strategy=strategy)
+            assert res.nnz == 0 and res.stats.products == 0
     # no common contract key at all
     X = W.COO((4, 8), [[0, 1], [1, 1]], [1.0, 2.0])
     Y = W.COO((8, 3), [[2, 0], [3, 1]], [1.0, 2.0])
@@ -115,6 +144,26 @@ def test_wide_keys_non_pow2():
     X = W.uniform_coo(rng, (1_000_003, 7, 999_983), 3_000)
     Y = W.uniform_coo(rng, (7, 65_537), 500)
     check(W.Problem(X, Y, (1,), (0,)))
+
+
+def test_results_are_released():
+    """Dropping a result (and the tensors viewing it) returns its memory to the context."""
+    import gc
+
+    import paper_2410_10094_gb300 as stc
+
+    ctx = stc.default_context()
+    p = W.plain_small()
+    held0, live0 = stc.stc_ctx_stats(ctx.handle)
+    for _ in range(3):
+        res = gpu_contract(p)
+        coords = res.coords
+        del res
+        assert stc.stc_ctx_stats(ctx.handle)[1] == live0 + 1  # the tensor keeps it alive
+        del coords
+        gc.collect()
+        held, live = stc.stc_ctx_stats(ctx.handle)
+        assert live == live0 and held == held0
 
 
 def test_errors():
