@@ -29,22 +29,33 @@ if ROOT not in sys.path:
 
 import workloads as W  # noqa: E402
 
+def plain_large_slice(seed):
+    """plain_large with X cut to its first 16 values of mode 0 (same per-group work, 1/16 of
+    the groups): a profiling-sized case of the same kernels."""
+    rng = W.rng_for(seed)
+    X = W.uniform_coo(rng, (16, 256, 256, 256), 312_500)
+    Y = W.uniform_coo(rng, (256,) * 4, 5_000_000)
+    return W.Problem(X, Y, (2, 3), (0, 1), name="plain_large_slice")
+
+
 WORKLOADS = {
     "plain_large": lambda seed: W.plain_large(seed=seed),
+    "plain_large_slice": plain_large_slice,
     "imbalanced": lambda seed: W.imbalanced(seed=seed),
     "imbalanced_both": lambda seed: W.imbalanced(seed=seed, both_zipf=True),
     "plain_small": lambda seed: W.plain_small(seed=seed),
 }
-SEEDS = {"plain_large": W.SEED_BASE + 2, "imbalanced": W.SEED_BASE + 3, "imbalanced_both": W.SEED_BASE + 3,
+SEEDS = {"plain_large": W.SEED_BASE + 2, "plain_large_slice": W.SEED_BASE + 2, "imbalanced": W.SEED_BASE + 3, "imbalanced_both": W.SEED_BASE + 3,
          "plain_small": W.SEED_BASE + 1}
 DESCRIPTIONS = {
+    "plain_large_slice": "X 16x256^3 3.125e5 nnz, Y 256^4 5e6 nnz, X modes (2,3) x Y modes (0,1) (profiling slice)",
     "plain_large": "X,Y order-4 256^4 COO, 5e6 uniform nnz each, X modes (2,3) x Y modes (0,1), FP64",
     "imbalanced": "X 4096x512x512 2e7 nnz, Y 512x512x64 2e4 nnz with Zipf(1.2) contract keys, X (1,2) x Y (0,1)",
     "imbalanced_both": "as imbalanced, X contract keys also Zipf(1.2)",
     "plain_small": "X,Y order-3 64^3 COO, 5e3 distinct nnz each, X mode 2 x Y mode 0",
 }
 # Rows of X (first coordinate < bound) that make the oracle's bounded CPU sample.
-CPU_SAMPLE_X0 = {"plain_large": 7, "imbalanced": 4096, "imbalanced_both": 64, "plain_small": 64}
+CPU_SAMPLE_X0 = {"plain_large": 7, "plain_large_slice": 1, "imbalanced": 4096, "imbalanced_both": 64, "plain_small": 64}
 
 
 def peaks():

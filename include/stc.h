@@ -148,6 +148,25 @@ stc_status stc_linearize(stc_ctx* ctx, const stc_coo* T, int32_t nmodes, const i
 stc_status stc_group_keys(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t k,
                           uint32_t* offsets_out, uint32_t* perm_out, void* stream);
 
+/* stc_group_keys without allocation. The paper has no counterpart: this entry point exists
+ * for callers that must not allocate device memory, for example a process whose device memory
+ * is already fully carved up by its own allocator, or a loop that forbids allocation after
+ * start-up. It performs the same counting sort as stc_group_keys, with the same arguments
+ * and results, but takes no context and calls no allocator: its scratch (key counts, a
+ * cursor copy, scan partials and a status word) is one fixed array of about 2 MB in device
+ * memory that every device loading this library holds until the process exits.
+ *   - Limit: k <= 262144 (2^18) and n <= STC_MAX_NNZ; a larger k returns
+ *     STC_ERR_INVALID_ARG with a message naming the limit.
+ *   - It runs on the caller's current device. The first call on a device looks up the
+ *     array's device address (set-up); make that first call before capturing any stream.
+ *   - All calls on a device share the one array. The call clears what must start at zero,
+ *     but calls whose work overlaps on the GPU (other streams, other host threads) race on
+ *     it: serialise them.
+ *   - Returns after its device work completes; reports STC_ERR_COORD_OUT_OF_RANGE for a
+ *     key >= k, as stc_group_keys does. */
+stc_status stc_group_keys_static(const uint64_t* keys, int64_t n, uint64_t k, uint32_t* offsets_out,
+                                 uint32_t* perm_out, void* stream);
+
 /* Result accessors. Coordinates are device int32 [nnz][order] row-major, values device
  * double [nnz]; both stay valid until stc_result_free(). shape is host, [order]. */
 stc_status stc_result_info(const stc_result* r, int64_t* nnz, int32_t* order, const int64_t** shape);

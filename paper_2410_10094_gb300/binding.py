@@ -57,6 +57,7 @@ EXPORTS = {
     "stc_linearize": ([C.c_void_p, C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "stc_group_keys": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p],
                        C.c_int),
+    "stc_group_keys_static": ([C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "stc_result_info": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                          C.POINTER(C.POINTER(C.c_int64))], C.c_int),
     "stc_result_data": ([C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)], C.c_int),
@@ -189,6 +190,16 @@ def stc_group_keys(ctx: int, keys, k: int, offsets_out, perm_out, stream=None):
     check(load().stc_group_keys(C.c_void_p(ctx), C.c_void_p(keys.data_ptr() if n else 0), n, int(k),
                                 C.c_void_p(offsets_out.data_ptr()), C.c_void_p(perm_out.data_ptr() if n else 0),
                                 C.c_void_p(_stream_handle(stream))))
+
+
+def stc_group_keys_static(keys, k: int, offsets_out, perm_out, stream=None):
+    """stc_group_keys without allocation (fixed device scratch; k <= 262144). Runs on the
+    current device; calls that overlap on the GPU race on the shared scratch."""
+    n = int(keys.numel())
+    check(load().stc_group_keys_static(C.c_void_p(keys.data_ptr() if n else 0), n, int(k),
+                                       C.c_void_p(offsets_out.data_ptr()),
+                                       C.c_void_p(perm_out.data_ptr() if n else 0),
+                                       C.c_void_p(_stream_handle(stream))))
 
 
 def stc_result_info(r: int):

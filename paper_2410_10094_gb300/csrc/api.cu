@@ -497,6 +497,11 @@ int pick_strategy(const Plan& pl, const stc_coo* X, int requested) {
 
 }  // namespace
 
+namespace stc {
+// Lets other translation units of the library set the calling thread's last error.
+stc_status report_error(stc_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace stc
+
 extern "C" {
 
 const char* stc_status_string(stc_status s) {
