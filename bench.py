@@ -191,6 +191,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_large", choices=sorted(WORKLOADS))
     ap.add_argument("--strategy", type=int, default=0, help="0 auto, 1 global table, 2 grouped")
+    ap.add_argument("--group-load-factor", type=float, default=0.0, help="0 = library default")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -224,7 +225,7 @@ def main(argv=None):
 
     def step(record=False):
         return stc.contract(X, Y, p.cx, p.cy, p.out_order, strategy=args.strategy, record_times=record,
-                            stream=stream, ctx=ctx)
+                            group_load_factor=args.group_load_factor, stream=stream, ctx=ctx)
 
     for _ in range(args.warmup):
         r = step()
@@ -277,7 +278,8 @@ def main(argv=None):
         for _ in range(args.e2e_steps):
             Xd = (p.X.shape, hx[0].to("cuda", non_blocking=True), hx[1].to("cuda", non_blocking=True))
             Yd = (p.Y.shape, hy[0].to("cuda", non_blocking=True), hy[1].to("cuda", non_blocking=True))
-            r = stc.contract(Xd, Yd, p.cx, p.cy, p.out_order, strategy=args.strategy, stream=stream, ctx=ctx)
+            r = stc.contract(Xd, Yd, p.cx, p.cy, p.out_order, strategy=args.strategy,
+                             group_load_factor=args.group_load_factor, stream=stream, ctx=ctx)
             hc[: r.nnz].copy_(r.coords, non_blocking=True)
             hv[: r.nnz].copy_(r.vals, non_blocking=True)
             torch.cuda.synchronize()
@@ -330,7 +332,8 @@ def main(argv=None):
         "config": {"workload": f"{args.workload}: {DESCRIPTIONS[args.workload]}", "seed": seed,
                    "products_per_step": P, "nnz_out": nz, "parallelism": f"replicas x{world}",
                    "l2": "inputs 240 MB and output 8.8 GB exceed the 129 MB L2; no flush" if args.workload ==
-                   "plain_large" else "see DESIGN.md", "strategy": args.strategy},
+                   "plain_large" else "see DESIGN.md", "strategy": args.strategy,
+                   "group_load_factor": args.group_load_factor},
         "step_hbm": {"alg_bytes": step_alg, "gbs": step_alg / (step_ms / 1e3) / 1e9,
                      "frac": step_alg / (step_ms / 1e3) / 1e9 / hbm},
         "stage_ms": {n: float(per_step[i]) for i, n in enumerate(stage_names)},

@@ -72,7 +72,7 @@ typedef struct stc_opts {
   int32_t record_times;   /* nonzero: time each stage with CUDA events (stc_result_stats) */
   double load_factor;     /* global-table load factor in (0, 0.9]; 0 = default 0.5 */
   double group_load_factor; /* largest load of a per-group shared-memory table, in (0, 0.9];
-                               0 = default 0.5. A group of bound t goes to the smallest table
+                               0 = default 0.75. A group of bound t goes to the smallest table
                                class with t <= group_load_factor * slots. */
 } stc_opts;
 

@@ -313,16 +313,22 @@ struct StageTimer {
 // key, and X surveyed against it.
 struct Prepared {
   uint32_t* yoff = nullptr;  // [K + 1]
-  u64* yfk = nullptr;        // [nY], Y free keys in contract-key order
+  void* yfk = nullptr;       // [nY], Y free keys in contract-key order (u32 when key32, else u64)
+  bool key32 = false;
   double* yv = nullptr;      // [nY]
   Survivors sv{};
   Counters* ctr = nullptr;
-  uint32_t* gcnt = nullptr;  // [FX] survivors per X free key (GROUPED only)
-  u64* gbound = nullptr;     // [FX] sum of run lengths per X free key (GROUPED only)
+  uint32_t* gcnt = nullptr;  // [FX] entries with a Y run per X free key (GROUPED only)
+  bool dense = false;        // GROUPED without a survivor list (X re-read by the scatter)
 };
 
-stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, const Plan& pl, bool groups,
+// How X is surveyed: a survivor list (GLOBAL), a survivor list plus per-group counts
+// (GROUPED, few X entries have a Y run), or per-group counts alone (GROUPED, most do).
+enum class Survey { kSurvivors, kSurvivorsGroups, kDenseGroups };
+
+stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, const Plan& pl, Survey mode,
                    cudaStream_t s, StageTimer& tm, Prepared& pr) {
+  const bool groups = mode != Survey::kSurvivors;
   if (pl.K > kMaxDirectBins)
     return fail(STC_ERR_UNSUPPORTED, "contract key space %llu exceeds %llu bins", (unsigned long long)pl.K,
                 (unsigned long long)kMaxDirectBins);
@@ -337,29 +343,41 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
   STC_TRY(ar.alloc(&pr.yoff, pl.K + 1));
   STC_TRY(ar.alloc(&ycur, pl.K));
   STC_TRY(ar.alloc(&scr, (size_t)scan_scratch_elems((int64_t)pl.K)));
-  STC_TRY(ar.alloc(&pr.yfk, (size_t)nY));
+  pr.key32 = groups && pl.FY <= 0xffffffffull;
+  if (pr.key32) {
+    uint32_t* k32 = nullptr;
+    STC_TRY(ar.alloc(&k32, (size_t)nY));
+    pr.yfk = k32;
+  } else {
+    u64* k64 = nullptr;
+    STC_TRY(ar.alloc(&k64, (size_t)nY));
+    pr.yfk = k64;
+  }
   STC_TRY(ar.alloc(&pr.yv, (size_t)nY));
   STC_CUDA(cudaMemsetAsync(ycnt, 0, pl.K * sizeof(uint32_t), s));
   STC_CUDA(launch_y_count(Y->coords, nY, pl.ky, ycnt, status, ctx->sms, s));
   STC_CUDA(scan_u32(ycnt, pr.yoff, (int64_t)pl.K, scr, s));
   STC_CUDA(cudaMemcpyAsync(ycur, pr.yoff, pl.K * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-  STC_CUDA(launch_y_scatter(Y->coords, Y->vals, nY, pl.ky, ycur, pr.yfk, pr.yv, ctx->sms, s));
+  STC_CUDA(launch_y_scatter(Y->coords, Y->vals, nY, pl.ky, ycur, pr.yfk, pr.key32, pr.yv, ctx->sms, s));
   tm.mark(0);
 
-  // X: find each entry's Y run; keep the entries that have one (Section 4.3 counts).
-  STC_TRY(ar.alloc(&pr.sv.fk, (size_t)nX));
-  STC_TRY(ar.alloc(&pr.sv.ystart, (size_t)nX));
-  STC_TRY(ar.alloc(&pr.sv.w, (size_t)nX));
-  STC_TRY(ar.alloc(&pr.sv.v, (size_t)nX));
+  // X: find each entry's Y run and count the products exactly (Section 4.3).
   pr.sv.count = &pr.ctr->ns;
   if (groups) {
     STC_TRY(ar.alloc(&pr.gcnt, pl.FX));
-    STC_TRY(ar.alloc(&pr.gbound, pl.FX));
     STC_CUDA(cudaMemsetAsync(pr.gcnt, 0, pl.FX * sizeof(uint32_t), s));
-    STC_CUDA(cudaMemsetAsync(pr.gbound, 0, pl.FX * sizeof(u64), s));
   }
-  STC_CUDA(launch_x_survey(X->coords, X->vals, nX, pl.kx, pr.yoff, pr.sv, &pr.ctr->P, pr.gcnt, pr.gbound, status,
-                           ctx->sms, s));
+  pr.dense = mode == Survey::kDenseGroups;
+  if (pr.dense) {
+    STC_CUDA(launch_x_count(X->coords, nX, pl.kx, pr.yoff, &pr.ctr->P, pr.gcnt, status, ctx->sms, s));
+  } else {
+    STC_TRY(ar.alloc(&pr.sv.fk, (size_t)nX));
+    STC_TRY(ar.alloc(&pr.sv.ystart, (size_t)nX));
+    STC_TRY(ar.alloc(&pr.sv.w, (size_t)nX));
+    STC_TRY(ar.alloc(&pr.sv.v, (size_t)nX));
+    STC_CUDA(launch_x_survey(X->coords, X->vals, nX, pl.kx, pr.yoff, pr.sv, &pr.ctr->P, pr.gcnt, status, ctx->sms,
+                             s));
+  }
   tm.mark(1);
   return STC_OK;
 }
@@ -383,6 +401,18 @@ uint64_t global_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t ns, uint6
 }
 
 
+// Peak device bytes of the GROUPED strategy: Y grouped, X grouped (and, at worst, a survivor
+// list), per-group arrays, and an output at its bound. Overflow-group tables are bounded by
+// twice the output bound.
+uint64_t grouped_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t P) {
+  const uint64_t out = std::min<uint64_t>(P, pl.F);
+  uint64_t b = sizeof(Counters) + pl.K * 4 * 3 + (uint64_t)scan_scratch_elems((int64_t)pl.K) * 4;
+  b += (uint64_t)nY * 16 + (uint64_t)nX * (24 + 16);
+  b += pl.FX * (4 * 3) + std::min<uint64_t>(pl.FX, (uint64_t)nX) * 4 * (kMaxClasses + 5);
+  b += out * (4ull * pl.oz + 8);
+  return b;
+}
+
 // Counters of the grouping and binning passes, read back with the first host sync.
 struct GroupCounters {
   uint32_t count[kMaxClasses + 1];
@@ -398,12 +428,15 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
                             const stc_opts& o, cudaStream_t s, StageTimer& tm, stc_result* r) {
   const int64_t nX = X->nnz;
   Prepared pr;
-  STC_TRY(prepare(ctx, ar, X, Y, pl, true, s, tm, pr));
+  // Dense when Y's runs cover the contract keys on average: then nearly every X entry has a
+  // run and a survivor list would only be written and read back.
+  const Survey mode = ((uint64_t)Y->nnz >= pl.K) ? Survey::kDenseGroups : Survey::kSurvivorsGroups;
+  STC_TRY(prepare(ctx, ar, X, Y, pl, mode, s, tm, pr));
 
   const bool wide = pl.FY > 0xffffffffull;
   const int ncls = wide ? kNumClasses64 : kNumClasses32;
   const ClassShape* shapes = wide ? kClassShapes64 : kClassShapes32;
-  const double ga = (o.group_load_factor > 0.0) ? o.group_load_factor : 0.5;
+  const double ga = (o.group_load_factor > 0.0) ? o.group_load_factor : 0.75;
   const uint64_t maxg = std::min<uint64_t>(pl.FX, (uint64_t)std::max<int64_t>(nX, 1));
 
   uint32_t *goff = nullptr, *gcur = nullptr, *scr = nullptr;
@@ -432,8 +465,13 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   STC_CUDA(cudaMemsetAsync(gc, 0, sizeof(GroupCounters), s));
   STC_CUDA(scan_u32(pr.gcnt, goff, (int64_t)pl.FX, scr, s));
   STC_CUDA(cudaMemcpyAsync(gcur, goff, pl.FX * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-  STC_CUDA(launch_x_group_scatter(pr.sv, gcur, gx, nX, ctx->sms, s));
-  STC_CUDA(launch_bin_groups(pl.FX, pr.gcnt, pr.gbound, pl.FY, b, ctx->sms, s));
+  if (pr.dense) {
+    STC_CUDA(launch_x_scatter_dense(X->coords, X->vals, nX, pl.kx, pr.yoff, gcur, gx, &pr.ctr->status, ctx->sms, s));
+    STC_CUDA(cudaMemcpyAsync(&pr.ctr->ns, goff + pl.FX, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  } else {
+    STC_CUDA(launch_x_group_scatter(pr.sv, gcur, gx, nX, ctx->sms, s));
+  }
+  STC_CUDA(launch_bin_groups(pl.FX, goff, gx.w, pl.FY, b, ctx->sms, s));
   tm.mark(2);
 
   Counters h{};
@@ -476,7 +514,7 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   a.nz = &pr.ctr->nz;
   a.status = &pr.ctr->status;
   STC_CUDA(launch_group_classes(a, wide, b, hg.count, ctx->sms, s));
-  STC_CUDA(launch_group_huge(a, hh, ctx->sms, s));
+  STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
   tm.mark(4);
   Counters h2{};
   STC_TRY(read_counters(pr, s, h2));
@@ -611,7 +649,7 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
   }
 
   Prepared pr;
-  STC_TRY(prepare(ctx, ar, X, Y, pl, false, s, tm, pr));
+  STC_TRY(prepare(ctx, ar, X, Y, pl, Survey::kSurvivors, s, tm, pr));
   Counters h{};
   STC_TRY(read_counters(pr, s, h));
   tm.mark(3);
@@ -645,7 +683,8 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
       STC_CUDA(cudaMemsetAsync(t.vals, 0, cap * sizeof(double), s));
       STC_CUDA(scan_u32_u64(pr.sv.w, wpre, (int64_t)h.ns, wscr, s));
       tm.mark(3);
-      STC_CUDA(launch_expand_global(wpre, (int64_t)h.ns, h.P, pr.sv, pr.yfk, pr.yv, pl.FY, t, &pr.ctr->status,
+      STC_CUDA(launch_expand_global(wpre, (int64_t)h.ns, h.P, pr.sv, static_cast<const u64*>(pr.yfk), pr.yv, pl.FY,
+                                    t, &pr.ctr->status,
                                     ctx->sms, s));
       tm.mark(4);
       STC_CUDA(launch_compact_global(t, pl.op, r->coords, r->vals, out_cap, &pr.ctr->nz, &pr.ctr->status, ctx->sms,
@@ -690,11 +729,15 @@ stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m
   Arena ar(ctx, s);
   StageTimer tm;
   Prepared pr;
-  STC_TRY(prepare(ctx, ar, X, Y, pl, false, s, tm, pr));
+  const int strategy = pick_strategy(pl, X, STC_STRATEGY_AUTO);
+  const bool dense = strategy == STC_STRATEGY_GROUPED && (uint64_t)Y->nnz >= pl.K;
+  STC_TRY(prepare(ctx, ar, X, Y, pl, dense ? Survey::kDenseGroups : Survey::kSurvivors, s, tm, pr));
   Counters h{};
   STC_TRY(read_counters(pr, s, h));
   if (products) *products = h.P;
-  if (bytes_bound) *bytes_bound = global_bytes(pl, X->nnz, Y->nnz, h.ns, h.P, 0.5);
+  if (bytes_bound)
+    *bytes_bound = strategy == STC_STRATEGY_GROUPED ? grouped_bytes(pl, X->nnz, Y->nnz, h.P)
+                                                    : global_bytes(pl, X->nnz, Y->nnz, h.ns, h.P, 0.5);
   return STC_OK;
 }
 

@@ -44,17 +44,23 @@ __global__ void __launch_bounds__(kThreads) x_group_scatter_kernel(Survivors sv,
   }
 }
 
-// One thread per X free key: non-empty groups go to the first class whose table holds
-// their bound t = min(B_g, F_Y); larger ones get a region of the overflow table.
-__global__ void __launch_bounds__(kThreads) bin_groups_kernel(u64 FX, const uint32_t* __restrict__ gcnt,
-                                                              const u64* __restrict__ gbound, u64 FY, Bins b) {
+// One warp per X free key g: the group's bound B_g (Section 4.3) is the sum of its entries'
+// run lengths, read from the grouped X. Non-empty groups go to the first class whose table
+// holds t = min(B_g, F_Y); larger ones get a region of the overflow table.
+__global__ void __launch_bounds__(kThreads) bin_groups_kernel(u64 FX, const uint32_t* __restrict__ goff,
+                                                              const uint32_t* __restrict__ gw, u64 FY, Bins b) {
   __shared__ u64 s_cap[kThreads / 32];
+  const unsigned lane = lane_id();
   u64 my_cap = 0;
-  for (int64_t base = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u); base < (int64_t)FX;
-       base += (int64_t)gridDim.x * kThreads) {
-    const int64_t g = base + lane_id();
-    if (g < (int64_t)FX && gcnt[g] != 0) {
-      const u64 bnd = gbound[g];
+  for (u64 g = (u64)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); g < FX;
+       g += (u64)gridDim.x * (kThreads / 32)) {
+    const uint32_t x0 = goff[g], x1 = goff[g + 1];
+    if (x0 == x1) continue;
+    u64 bnd = 0;
+    for (uint32_t i = x0 + lane; i < x1; i += 32) bnd += gw[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+    if (lane == 0) {
       const u64 t = bnd < FY ? bnd : FY;
       my_cap += t;
       int c = 0;
@@ -74,9 +80,7 @@ __global__ void __launch_bounds__(kThreads) bin_groups_kernel(u64 FX, const uint
       }
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_cap += __shfl_down_sync(0xffffffffu, my_cap, o);
-  if (lane_id() == 0) s_cap[threadIdx.x >> 5] = my_cap;
+  if (lane == 0) s_cap[threadIdx.x >> 5] = my_cap;
   __syncthreads();
   if (threadIdx.x == 0) {
     u64 t = 0;
@@ -122,8 +126,249 @@ __device__ __forceinline__ void chunk_scan(Chunk<THREADS>& c, u64 w, u64* warp_t
   c.pre[threadIdx.x] = warp_tot[warp] + x - w;
 }
 
-// Insert (key, v) into a linear-probing table of mask+1 slots: claim an empty slot with a
-// compare-and-swap, or find the key, then add v to the slot's value.
+// Loads the chunk of X entries [c0, c0 + n) of a group and scans their run lengths.
+template <int THREADS>
+__device__ __forceinline__ void load_chunk(const GroupArgs& a, Chunk<THREADS>& c, u64* warp_tot, uint32_t c0,
+                                           uint32_t n) {
+  u64 w = 0;
+  if (threadIdx.x < n) {
+    const uint32_t xi = c0 + threadIdx.x;
+    w = a.gx.w[xi];
+    c.ystart[threadIdx.x] = a.gx.ystart[xi];
+    c.v[threadIdx.x] = a.gx.v[xi];
+  }
+  chunk_scan<THREADS>(c, w, warp_tot);
+  __syncthreads();
+}
+
+template <typename YK>
+__device__ __forceinline__ u64 y_key(const void* yfk, u64 j) {
+  return (u64)__ldg(static_cast<const YK*>(yfk) + j);
+}
+
+// ---- shared-memory tables: buckets of 16 bytes (4 32-bit keys or 2 64-bit keys) probed
+// with one vector load; the first empty slot of the first bucket without the key is
+// claimed with a compare-and-swap (linear probing over buckets, Section 2.2.1).
+
+template <typename KT>
+struct Bucket;
+template <>
+struct Bucket<uint32_t> {
+  static constexpr int N = 4;
+  uint32_t k[4];
+};
+template <>
+struct Bucket<u64> {
+  static constexpr int N = 2;
+  u64 k[2];
+};
+
+// A fresh 16-byte read of bucket b (volatile: other threads claim slots concurrently).
+template <typename KT>
+__device__ __forceinline__ Bucket<KT> load_bucket(const KT* keys, uint32_t b) {
+  Bucket<KT> out;
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(keys + (16 / sizeof(KT)) * b);
+  if constexpr (sizeof(KT) == 4) {
+    asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(out.k[0]), "=r"(out.k[1]), "=r"(out.k[2]), "=r"(out.k[3])
+                 : "r"(addr)
+                 : "memory");
+  } else {
+    asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];" : "=l"(out.k[0]), "=l"(out.k[1]) : "r"(addr) : "memory");
+  }
+  return out;
+}
+
+// Returns the slot holding `key` after inserting it if absent, or -1 if the table is full.
+// *claimed tells whether this call took a new slot.
+template <typename KT, int SLOTS>
+__device__ __forceinline__ int bucket_claim(KT* keys, KT key, bool* claimed) {
+  constexpr int B = Bucket<KT>::N;
+  constexpr uint32_t NB = SLOTS / B;
+  uint32_t b = slot_hash(key) & (NB - 1);
+  *claimed = false;
+  for (uint32_t probe = 0; probe < NB;) {
+    const Bucket<KT> bk = load_bucket<KT>(keys, b);
+    int empty = -1;
+#pragma unroll
+    for (int i = B - 1; i >= 0; i--) {
+      if (bk.k[i] == key) return (int)(b * B + i);
+      if (bk.k[i] == empty_key<KT>()) empty = i;
+    }
+    if (empty < 0) {
+      b = (b + 1) & (NB - 1);
+      probe++;
+      continue;
+    }
+    const KT prev = atomicCAS(keys + b * B + empty, empty_key<KT>(), key);
+    if (prev == empty_key<KT>()) {
+      *claimed = true;
+      return (int)(b * B + empty);
+    }
+    if (prev == key) return (int)(b * B + empty);
+    // Another key took that slot: look at the same bucket again.
+  }
+  return -1;
+}
+
+// One group: every product of its X entries goes into the shared-memory table. The chunk's
+// product range is split evenly over the warps; a warp walks its share 32 products at a
+// time (consecutive lanes read consecutive slots of a Y run), advancing the owning X entry
+// with the chunk prefix instead of searching for it. The Y reads of D such steps are all
+// issued before any of their inserts, so each warp keeps D loads in flight.
+template <int SLOTS, int THREADS, typename KT, int D>
+__device__ __forceinline__ void expand_group_smem(const GroupArgs& a, Chunk<THREADS>& c, u64* warp_tot,
+                                                  uint32_t x0, uint32_t x1, KT* keys, double* vals,
+                                                  unsigned* claims) {
+  constexpr int NW = THREADS / 32;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  for (uint32_t c0 = x0; c0 < x1; c0 += THREADS) {
+    const uint32_t n = (x1 - c0 < (uint32_t)THREADS) ? x1 - c0 : (uint32_t)THREADS;
+    load_chunk<THREADS>(a, c, warp_tot, c0, n);
+    const u64 total = c.pre[n];
+    const u64 lo = total * warp / NW, hi = total * (warp + 1) / NW;
+    // Owner of product lo: the largest k with pre[k] <= lo.
+    uint32_t own = 0;
+    if (lo < hi) {
+      uint32_t l = 0, h = n - 1;
+      while (l < h) {
+        const uint32_t mid = (l + h + 1) >> 1;
+        if (c.pre[mid] <= lo) l = mid; else h = mid - 1;
+      }
+      own = l;
+    }
+    unsigned my_claims = 0;
+    for (u64 base = lo; base < hi; base += 32 * D) {
+      KT key[D];
+      double yv[D], xv[D];
+#pragma unroll
+      for (int u = 0; u < D; u++) {
+        const u64 p = base + (u64)u * 32 + lane;
+        uint32_t k = own;
+        key[u] = empty_key<KT>();
+        if (p < hi) {
+          while (c.pre[k + 1] <= p) k++;
+          const u64 j = (u64)c.ystart[k] + (p - c.pre[k]);
+          key[u] = (KT)y_key<KT>(a.yfk, j);
+          yv[u] = __ldg(a.yv + j);
+          xv[u] = c.v[k];
+        }
+        own = __shfl_sync(0xffffffffu, k, 31);
+      }
+#pragma unroll
+      for (int u = 0; u < D; u++) {
+        bool claimed = false;
+        if (key[u] != empty_key<KT>()) {
+          const int slot = bucket_claim<KT, SLOTS>(keys, key[u], &claimed);
+          if (slot >= 0) atomicAdd(vals + slot, __dmul_rn(xv[u], yv[u]));
+          else atomicOr(a.status, kStatTableFull);
+        }
+        my_claims += __popc(__ballot_sync(0xffffffffu, claimed));
+      }
+    }
+    if (lane == 0 && my_claims) atomicAdd(claims, my_claims);
+    __syncthreads();
+  }
+}
+
+// Writes the occupied slots as COO output (streaming stores: written once, not re-read)
+// and empties them. One atomic reserves the group's output range; inside it, warps take
+// positions from a shared-memory cursor in the order they find occupied slots.
+template <int SLOTS, int THREADS, typename KT>
+__device__ __forceinline__ void write_group_smem(const GroupArgs& a, u64 g, KT* keys, double* vals,
+                                                 unsigned* claims, unsigned* cursor, u64* gbase) {
+  constexpr int B = Bucket<KT>::N;
+  constexpr uint32_t NB = SLOTS / B;
+  const unsigned lane = lane_id();
+  if (threadIdx.x == 0) {
+    const unsigned n = *claims;
+    *gbase = n ? atomicAdd(a.nz, (u64)n) : 0;
+    *cursor = 0;
+  }
+  __syncthreads();
+  const u64 base = *gbase;
+  const u64 zrow = g * a.FY;
+  const int oz = a.op.order;
+  for (uint32_t b0 = (threadIdx.x & ~31u); b0 < NB; b0 += THREADS) {
+    const uint32_t b = b0 + lane;
+    Bucket<KT> bk;
+    unsigned live = 0;
+    if (b < NB) {
+      bk = load_bucket<KT>(keys, b);
+#pragma unroll
+      for (int i = 0; i < B; i++) live |= (bk.k[i] != empty_key<KT>()) ? (1u << i) : 0u;
+    }
+    const unsigned cnt = __popc(live);
+    unsigned pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
+      if ((int)lane >= o) pre += y;
+    }
+    const unsigned tot = __shfl_sync(0xffffffffu, pre, 31);
+    unsigned off = 0;
+    if (lane == 0 && tot) off = atomicAdd(cursor, tot);
+    off = __shfl_sync(0xffffffffu, off, 0) + pre - cnt;
+#pragma unroll
+    for (int i = 0; i < B; i++) {
+      if (live & (1u << i)) {
+        const uint32_t slot = b * B + i;
+        const u64 pos = base + off++;
+        const double v = vals[slot];
+        if (pos < a.out_cap) {
+          const u64 z = zrow + (u64)bk.k[i];
+          int32_t* dst = a.coords + pos * (u64)oz;
+          if (oz == 4 && a.op.pow2 && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+            int4 cv;
+            cv.x = (int32_t)((z >> a.op.shift[0]) & (a.op.mod[0] - 1));
+            cv.y = (int32_t)((z >> a.op.shift[1]) & (a.op.mod[1] - 1));
+            cv.z = (int32_t)((z >> a.op.shift[2]) & (a.op.mod[2] - 1));
+            cv.w = (int32_t)((z >> a.op.shift[3]) & (a.op.mod[3] - 1));
+            __stcs(reinterpret_cast<int4*>(dst), cv);
+          } else {
+            for (int q = 0; q < oz; q++) __stcs(dst + q, out_coord(z, a.op, q));
+          }
+          __stcs(a.vals + pos, v);
+        } else {
+          atomicOr(a.status, kStatOutOverflow);
+        }
+        keys[slot] = empty_key<KT>();
+        vals[slot] = 0.0;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *claims = 0;
+}
+
+// Persistent: CTA b takes groups b, b + grid, ... of its class list. The table is cleared
+// once; write_group_smem empties it again after each group.
+template <int SLOTS, int THREADS, typename KT>
+__global__ void __launch_bounds__(THREADS) group_smem_kernel(GroupArgs a, const uint32_t* __restrict__ list,
+                                                             uint32_t count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* vals = reinterpret_cast<double*>(smem);
+  KT* keys = reinterpret_cast<KT*>(vals + SLOTS);
+  Chunk<THREADS>& c = *reinterpret_cast<Chunk<THREADS>*>(smem + SLOTS * (sizeof(double) + sizeof(KT)));
+  __shared__ u64 warp_tot[THREADS / 32];
+  __shared__ unsigned claims, cursor;
+  __shared__ u64 gbase;
+  for (int i = threadIdx.x; i < SLOTS; i += THREADS) {
+    keys[i] = empty_key<KT>();
+    vals[i] = 0.0;
+  }
+  if (threadIdx.x == 0) claims = 0;
+  __syncthreads();
+  for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
+    const uint32_t g = list[k];
+    expand_group_smem<SLOTS, THREADS, KT, sizeof(KT) == 4 ? 8 : 4>(a, c, warp_tot, a.goff[g], a.goff[g + 1], keys,
+                                                                   vals, &claims);
+    write_group_smem<SLOTS, THREADS, KT>(a, g, keys, vals, &claims, &cursor, &gbase);
+  }
+}
+
+// ---- overflow groups: a table region in global memory, scalar linear probing.
+
 template <typename KT>
 __device__ __forceinline__ bool probe_add(KT* keys, double* vals, uint32_t mask, KT key, double v) {
   uint32_t h = slot_hash(key) & mask;
@@ -142,25 +387,14 @@ __device__ __forceinline__ bool probe_add(KT* keys, double* vals, uint32_t mask,
   return false;
 }
 
-// Expands every product of group g's X entries [x0, x1) into the table. Products of a chunk
-// of THREADS X entries are spread over the threads in order (consecutive threads read
-// consecutive slots of a Y run); the owning X entry of product p is found by binary search
-// in the chunk's prefix.
-template <int THREADS, typename KT>
-__device__ __forceinline__ void expand_group(const GroupArgs& a, Chunk<THREADS>& c, u64* warp_tot, uint32_t x0,
-                                             uint32_t x1, KT* keys, double* vals, uint32_t mask) {
+template <int THREADS, typename YK>
+__device__ __forceinline__ void expand_group_global(const GroupArgs& a, Chunk<THREADS>& c, u64* warp_tot,
+                                                    uint32_t x0, uint32_t x1, u64* keys, double* vals,
+                                                    uint32_t mask) {
   for (uint32_t c0 = x0; c0 < x1; c0 += THREADS) {
     const uint32_t n = (x1 - c0 < (uint32_t)THREADS) ? x1 - c0 : (uint32_t)THREADS;
-    const uint32_t xi = c0 + threadIdx.x;
-    u64 w = 0;
-    if (threadIdx.x < n) {
-      w = a.gx.w[xi];
-      c.ystart[threadIdx.x] = a.gx.ystart[xi];
-      c.v[threadIdx.x] = a.gx.v[xi];
-    }
-    chunk_scan<THREADS>(c, w, warp_tot);
-    __syncthreads();
-    const u64 total = c.pre[THREADS];
+    load_chunk<THREADS>(a, c, warp_tot, c0, n);
+    const u64 total = c.pre[n];
     for (u64 p = threadIdx.x; p < total; p += THREADS) {
       uint32_t lo = 0, hi = n - 1;
       while (lo < hi) {
@@ -168,27 +402,25 @@ __device__ __forceinline__ void expand_group(const GroupArgs& a, Chunk<THREADS>&
         if (c.pre[mid] <= p) lo = mid; else hi = mid - 1;
       }
       const u64 j = (u64)c.ystart[lo] + (p - c.pre[lo]);
-      const KT key = (KT)__ldg(a.yfk + j);
+      const u64 key = y_key<YK>(a.yfk, j);
       const double prod = __dmul_rn(c.v[lo], __ldg(a.yv + j));
-      if (!probe_add<KT>(keys, vals, mask, key, prod)) atomicOr(a.status, kStatTableFull);
+      if (!probe_add<u64>(keys, vals, mask, key, prod)) atomicOr(a.status, kStatTableFull);
     }
     __syncthreads();
   }
 }
 
-// Writes the occupied slots of group g's table as COO output and empties the table for
-// the next group. Each warp owns a contiguous slice of the table; one atomic per group
-// reserves the group's output range.
-template <int THREADS, typename KT>
-__device__ __forceinline__ void write_group(const GroupArgs& a, u64 g, KT* keys, double* vals, uint32_t slots,
-                                            uint32_t* warp_cnt, u64* warp_base) {
+template <int THREADS>
+__device__ __forceinline__ void write_group_global(const GroupArgs& a, u64 g, const u64* keys,
+                                                   const double* vals, uint32_t slots, uint32_t* warp_cnt,
+                                                   u64* warp_base) {
   constexpr int NW = THREADS / 32;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t per = (slots + NW - 1) / NW;
   const uint32_t s0 = warp * per;
   const uint32_t s1 = (s0 + per < slots) ? s0 + per : slots;
   uint32_t cnt = 0;
-  for (uint32_t i = s0 + lane; i < s1; i += 32) cnt += keys[i] != empty_key<KT>();
+  for (uint32_t i = s0 + lane; i < s1; i += 32) cnt += keys[i] != kEmpty64;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
   if (lane == 0) warp_cnt[warp] = cnt;
@@ -204,57 +436,29 @@ __device__ __forceinline__ void write_group(const GroupArgs& a, u64 g, KT* keys,
   }
   __syncthreads();
   u64 run = warp_base[warp];
-  const u64 gbase = g * a.FY;
+  const u64 zrow = g * a.FY;
   for (uint32_t i0 = s0; i0 < s1; i0 += 32) {
     const uint32_t i = i0 + lane;
-    KT k = empty_key<KT>();
-    if (i < s1) k = keys[i];
-    const bool live = k != empty_key<KT>();
+    const u64 k = (i < s1) ? keys[i] : kEmpty64;
+    const bool live = k != kEmpty64;
     const unsigned m = __ballot_sync(0xffffffffu, live);
     if (live) {
       const u64 pos = run + __popc(m & lanemask_lt());
       if (pos < a.out_cap) {
-        store_coords(gbase + (u64)k, a.op, a.coords + pos * (u64)a.op.order);
+        store_coords(zrow + k, a.op, a.coords + pos * (u64)a.op.order);
         a.vals[pos] = vals[i];
       } else {
         atomicOr(a.status, kStatOutOverflow);
       }
-      keys[i] = empty_key<KT>();
-      vals[i] = 0.0;
     }
     run += __popc(m);
   }
   __syncthreads();
 }
 
-// Persistent: CTA b takes groups b, b + grid, ... of its class list. The shared-memory
-// table is cleared once; write_group leaves it empty again after each group.
-template <int SLOTS, int THREADS, typename KT>
-__global__ void __launch_bounds__(THREADS) group_smem_kernel(GroupArgs a, const uint32_t* __restrict__ list,
-                                                             uint32_t count) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  double* vals = reinterpret_cast<double*>(smem);
-  KT* keys = reinterpret_cast<KT*>(vals + SLOTS);
-  Chunk<THREADS>& c = *reinterpret_cast<Chunk<THREADS>*>(smem + SLOTS * (sizeof(double) + sizeof(KT)));
-  __shared__ u64 warp_tot[THREADS / 32];
-  __shared__ uint32_t warp_cnt[THREADS / 32];
-  __shared__ u64 warp_base[THREADS / 32];
-  for (int i = threadIdx.x; i < SLOTS; i += THREADS) {
-    keys[i] = empty_key<KT>();
-    vals[i] = 0.0;
-  }
-  __syncthreads();
-  for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
-    const uint32_t g = list[k];
-    const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
-    expand_group<THREADS, KT>(a, c, warp_tot, x0, x1, keys, vals, SLOTS - 1);
-    write_group<THREADS, KT>(a, g, keys, vals, SLOTS, warp_cnt, warp_base);
-  }
-}
-
-// Groups whose table does not fit in shared memory: one CTA per group, the table a region
-// of a global array (cleared by the host before the launch).
-template <int THREADS>
+// One CTA per overflow group; the table is that group's region of a global array (the host
+// clears it before the launch).
+template <int THREADS, typename YK>
 __global__ void __launch_bounds__(THREADS) group_global_kernel(GroupArgs a, HugeGroups h) {
   __shared__ Chunk<THREADS> c;
   __shared__ u64 warp_tot[THREADS / 32];
@@ -265,9 +469,8 @@ __global__ void __launch_bounds__(THREADS) group_global_kernel(GroupArgs a, Huge
     u64* keys = h.keys + h.off[k];
     double* vals = h.vals + h.off[k];
     const uint32_t cap = (uint32_t)h.cap[k];
-    expand_group<THREADS, u64>(a, c, warp_tot, a.goff[g], a.goff[g + 1], keys, vals, cap - 1);
-    __threadfence_block();
-    write_group<THREADS, u64>(a, g, keys, vals, cap, warp_cnt, warp_base);
+    expand_group_global<THREADS, YK>(a, c, warp_tot, a.goff[g], a.goff[g + 1], keys, vals, cap - 1);
+    write_group_global<THREADS>(a, g, keys, vals, cap, warp_cnt, warp_base);
   }
 }
 
@@ -292,8 +495,8 @@ cudaError_t launch_class(const GroupArgs& a, const uint32_t* list, uint32_t coun
 
 // Table classes: slots and threads per CTA. The binning threshold of class c is
 // tmax[c] = floor(alpha_c * slots_c) (set by the host; default alpha 0.5).
-const ClassShape kClassShapes32[] = {{128, 64}, {1024, 128}, {4096, 256}, {8192, 512}, {16384, 1024}};
-const ClassShape kClassShapes64[] = {{128, 64}, {1024, 128}, {4096, 256}, {8192, 512}};
+const ClassShape kClassShapes32[] = {{256, 64}, {1024, 128}, {4096, 256}, {8192, 512}, {16384, 1024}};
+const ClassShape kClassShapes64[] = {{256, 64}, {1024, 128}, {4096, 256}, {8192, 512}};
 const int kNumClasses32 = 5;
 const int kNumClasses64 = 4;
 
@@ -305,10 +508,10 @@ cudaError_t launch_x_group_scatter(Survivors sv, uint32_t* gcur, GroupedX gx, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin_groups(u64 FX, const uint32_t* gcnt, const u64* gbound, u64 FY, const Bins& b, int sms,
+cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, u64 FY, const Bins& b, int sms,
                               cudaStream_t s) {
   if (FX == 0) return cudaSuccess;
-  bin_groups_kernel<<<grid_for((int64_t)FX, sms), kThreads, 0, s>>>(FX, gcnt, gbound, FY, b);
+  bin_groups_kernel<<<grid_for((int64_t)FX * 32, sms), kThreads, 0, s>>>(FX, goff, gw, FY, b);
   note_launch();
   return cudaGetLastError();
 }
@@ -317,13 +520,13 @@ cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins&
                                  int sms, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (!wide_keys) {
-    if ((e = launch_class<128, 64, uint32_t>(a, b.list[0], counts[0], sms, s))) return e;
+    if ((e = launch_class<256, 64, uint32_t>(a, b.list[0], counts[0], sms, s))) return e;
     if ((e = launch_class<1024, 128, uint32_t>(a, b.list[1], counts[1], sms, s))) return e;
     if ((e = launch_class<4096, 256, uint32_t>(a, b.list[2], counts[2], sms, s))) return e;
     if ((e = launch_class<8192, 512, uint32_t>(a, b.list[3], counts[3], sms, s))) return e;
     if ((e = launch_class<16384, 1024, uint32_t>(a, b.list[4], counts[4], sms, s))) return e;
   } else {
-    if ((e = launch_class<128, 64, u64>(a, b.list[0], counts[0], sms, s))) return e;
+    if ((e = launch_class<256, 64, u64>(a, b.list[0], counts[0], sms, s))) return e;
     if ((e = launch_class<1024, 128, u64>(a, b.list[1], counts[1], sms, s))) return e;
     if ((e = launch_class<4096, 256, u64>(a, b.list[2], counts[2], sms, s))) return e;
     if ((e = launch_class<8192, 512, u64>(a, b.list[3], counts[3], sms, s))) return e;
@@ -331,10 +534,13 @@ cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins&
   return cudaSuccess;
 }
 
-cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, int sms, cudaStream_t s) {
+cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s) {
   if (h.count == 0) return cudaSuccess;
   const uint32_t cap = (uint32_t)sms * 2;
-  group_global_kernel<512><<<h.count < cap ? h.count : cap, 512, 0, s>>>(a, h);
+  if (wide_keys)
+    group_global_kernel<512, u64><<<h.count < cap ? h.count : cap, 512, 0, s>>>(a, h);
+  else
+    group_global_kernel<512, uint32_t><<<h.count < cap ? h.count : cap, 512, 0, s>>>(a, h);
   note_launch();
   return cudaGetLastError();
 }

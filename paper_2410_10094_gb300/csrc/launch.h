@@ -35,8 +35,9 @@ cudaError_t launch_key_scatter(const u64* keys, int64_t n, u64 k, uint32_t* curs
 // of each entry's free key and value into its key's run.
 cudaError_t launch_y_count(const int32_t* coords, int64_t n, const KeyPlan& p, uint32_t* cnt,
                            uint32_t* status, int sms, cudaStream_t s);
+// yfk receives 32-bit free keys when key32 is set (F_Y < 2^32), 64-bit ones otherwise.
 cudaError_t launch_y_scatter(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
-                             uint32_t* cursor, u64* yfk, double* yv, int sms, cudaStream_t s);
+                             uint32_t* cursor, void* yfk, bool key32, double* yv, int sms, cudaStream_t s);
 
 // X entries whose contract key has a non-empty Y run ("survivors"), compacted, with the
 // run they will read and the total product count P (Section 4.3).
@@ -47,11 +48,20 @@ struct Survivors {
   double* v;        // X value
   unsigned* count;  // number of survivors (device counter)
 };
-// With gcnt/gbound non-null, also counts survivors per X free key and sums their run
-// lengths per X free key (the per-group bound of Section 4.3).
+// With gcnt non-null, also counts survivors per X free key.
 cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
-                            const uint32_t* yoff, Survivors sv, u64* P, uint32_t* gcnt, u64* gbound,
-                            uint32_t* status, int sms, cudaStream_t s);
+                            const uint32_t* yoff, Survivors sv, u64* P, uint32_t* gcnt, uint32_t* status, int sms,
+                            cudaStream_t s);
+
+// Dense X (Y runs exist for most contract keys): count entries with a run per X free key
+// and the products, then place them in group order straight from the input, without an
+// intermediate survivor list.
+struct GroupedX;
+cudaError_t launch_x_count(const int32_t* coords, int64_t n, const KeyPlan& p, const uint32_t* yoff, u64* P,
+                           uint32_t* gcnt, uint32_t* status, int sms, cudaStream_t s);
+cudaError_t launch_x_scatter_dense(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
+                                   const uint32_t* yoff, uint32_t* gcur, GroupedX gx, uint32_t* status, int sms,
+                                   cudaStream_t s);
 
 // ------------------------------------------------------------------ one global table (global.cu)
 struct GlobalTable {
@@ -104,7 +114,7 @@ struct Bins {
 struct GroupArgs {
   const uint32_t* goff;
   GroupedX gx;
-  const u64* yfk;
+  const void* yfk;  // Y free keys in contract-key order: uint32_t when F_Y < 2^32, else u64
   const double* yv;
   u64 FY;
   OutPlan op;
@@ -126,10 +136,10 @@ struct HugeGroups {
 
 cudaError_t launch_x_group_scatter(Survivors sv, uint32_t* gcur, GroupedX gx, int64_t max_ns, int sms,
                                    cudaStream_t s);
-cudaError_t launch_bin_groups(u64 FX, const uint32_t* gcnt, const u64* gbound, u64 FY, const Bins& b, int sms,
+cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, u64 FY, const Bins& b, int sms,
                               cudaStream_t s);
 cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins& b, const uint32_t* counts,
                                  int sms, cudaStream_t s);
-cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, int sms, cudaStream_t s);
+cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s);
 
 }  // namespace stc

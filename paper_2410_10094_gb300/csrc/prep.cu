@@ -57,31 +57,94 @@ __global__ void __launch_bounds__(kThreads) key_scatter_kernel(const u64* __rest
   }
 }
 
+// Row-streaming kernels take R rows per thread per step and issue all of their loads before
+// using any, so each thread keeps R coordinate rows (and their lookups) in flight.
+constexpr int kRows = 4;
+
 template <int ORDER, bool VEC>
 __global__ void __launch_bounds__(kThreads) y_count_kernel(const int32_t* __restrict__ coords, int64_t n, KeyPlan p,
                                                            uint32_t* __restrict__ cnt, uint32_t* status) {
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-    uint64_t ck, fk;
-    if (!row_keys<ORDER, VEC>(coords, i, p, ck, fk)) {
-      atomicOr(status, kStatCoordRange);
-      continue;
+  const int64_t step = (int64_t)gridDim.x * kThreads * kRows;
+  for (int64_t base = (int64_t)blockIdx.x * kThreads * kRows + threadIdx.x; base < n; base += step) {
+    uint64_t ck[kRows], fk[kRows];
+    bool ok[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      const int64_t i = base + (int64_t)r * kThreads;
+      ok[r] = i < n ? row_keys<ORDER, VEC>(coords, i, p, ck[r], fk[r]) : true;
+      if (i >= n) ck[r] = kEmpty64;
     }
-    atomicAdd(cnt + ck, 1u);
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      if (!ok[r]) atomicOr(status, kStatCoordRange);
+      else if (ck[r] != kEmpty64) atomicAdd(cnt + ck[r], 1u);
+    }
   }
 }
 
-template <int ORDER, bool VEC>
+template <int ORDER, bool VEC, typename YK>
 __global__ void __launch_bounds__(kThreads) y_scatter_kernel(const int32_t* __restrict__ coords,
                                                              const double* __restrict__ vals, int64_t n, KeyPlan p,
-                                                             uint32_t* __restrict__ cursor, u64* __restrict__ yfk,
+                                                             uint32_t* __restrict__ cursor, YK* __restrict__ yfk,
                                                              double* __restrict__ yv) {
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-    uint64_t ck, fk;
-    if (!row_keys<ORDER, VEC>(coords, i, p, ck, fk)) continue;
-    const uint32_t pos = atomicAdd(cursor + ck, 1u);
-    yfk[pos] = fk;
-    yv[pos] = __ldg(vals + i);
+  const int64_t step = (int64_t)gridDim.x * kThreads * kRows;
+  for (int64_t base = (int64_t)blockIdx.x * kThreads * kRows + threadIdx.x; base < n; base += step) {
+    uint64_t ck[kRows], fk[kRows];
+    bool ok[kRows];
+    double v[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      const int64_t i = base + (int64_t)r * kThreads;
+      ok[r] = false;
+      if (i < n) {
+        ok[r] = row_keys<ORDER, VEC>(coords, i, p, ck[r], fk[r]);
+        v[r] = __ldg(vals + i);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      if (!ok[r]) continue;
+      const uint32_t pos = atomicAdd(cursor + ck[r], 1u);
+      yfk[pos] = (YK)fk[r];
+      yv[pos] = v[r];
+    }
   }
+}
+
+// Warp-uniform loop over blocks of 32 * kRows consecutive rows; lane l takes rows
+// base + l + 32 r, so every load instruction of a warp reads consecutive rows.
+#define STC_WARP_ROWS(base, n)                                                                   \
+  for (int64_t base = ((int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * 32 * kRows; \
+       base < (n); base += (int64_t)gridDim.x * kThreads * kRows)
+
+// Looks up each row's Y run: lo = first slot, w = length (0 when the key has no run or the
+// row is invalid). Invalid coordinates raise kStatCoordRange.
+template <int ORDER, bool VEC>
+__device__ __forceinline__ void rows_runs(const int32_t* __restrict__ coords, int64_t base, int64_t n,
+                                          const KeyPlan& p, const uint32_t* __restrict__ yoff, uint64_t* fk,
+                                          uint32_t* lo, uint32_t* w, uint32_t* status) {
+  uint64_t ck[kRows];
+  bool ok[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; r++) {
+    const int64_t i = base + lane_id() + 32 * r;
+    ok[r] = false;
+    if (i < n) {
+      ok[r] = row_keys<ORDER, VEC>(coords, i, p, ck[r], fk[r]);
+      if (!ok[r]) atomicOr(status, kStatCoordRange);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRows; r++) {
+    lo[r] = 0;
+    w[r] = 0;
+    if (ok[r]) {
+      lo[r] = __ldg(yoff + ck[r]);
+      w[r] = __ldg(yoff + ck[r] + 1);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRows; r++) w[r] -= lo[r];
 }
 
 template <int ORDER, bool VEC, bool GROUPS>
@@ -89,32 +152,25 @@ __global__ void __launch_bounds__(kThreads) x_survey_kernel(const int32_t* __res
                                                             const double* __restrict__ vals, int64_t n, KeyPlan p,
                                                             const uint32_t* __restrict__ yoff, Survivors sv,
                                                             u64* __restrict__ P, uint32_t* __restrict__ gcnt,
-                                                            u64* __restrict__ gbound, uint32_t* status) {
+                                                            uint32_t* status) {
   __shared__ u64 warp_p[kThreads / 32];
   u64 my_p = 0;
-  STC_WARP_LOOP(i, n) {
-    bool live = false;
-    uint64_t ck = 0, fk = 0;
-    uint32_t lo = 0, w = 0;
-    if (i < n) {
-      if (!row_keys<ORDER, VEC>(coords, i, p, ck, fk)) {
-        atomicOr(status, kStatCoordRange);
-      } else {
-        lo = __ldg(yoff + ck);
-        w = __ldg(yoff + ck + 1) - lo;
-        live = w > 0;
-      }
-    }
-    const unsigned pos = warp_reserve<unsigned>(live, sv.count);
-    if (live) {
-      sv.fk[pos] = fk;
-      sv.ystart[pos] = lo;
-      sv.w[pos] = w;
-      sv.v[pos] = __ldg(vals + i);
-      my_p += w;
-      if (GROUPS) {
-        atomicAdd(gcnt + fk, 1u);
-        atomicAdd(gbound + fk, (u64)w);
+  STC_WARP_ROWS(base, n) {
+    uint64_t fk[kRows];
+    uint32_t lo[kRows], w[kRows];
+    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status);
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      const bool live = w[r] > 0;
+      const unsigned pos = warp_reserve<unsigned>(live, sv.count);
+      if (live) {
+        const int64_t i = base + lane_id() + 32 * r;
+        sv.fk[pos] = fk[r];
+        sv.ystart[pos] = lo[r];
+        sv.w[pos] = w[r];
+        sv.v[pos] = __ldg(vals + i);
+        my_p += w[r];
+        if (GROUPS) atomicAdd(gcnt + fk[r], 1u);
       }
     }
   }
@@ -124,8 +180,68 @@ __global__ void __launch_bounds__(kThreads) x_survey_kernel(const int32_t* __res
   __syncthreads();
   if (threadIdx.x == 0) {
     u64 t = 0;
-    for (int w = 0; w < kThreads / 32; w++) t += warp_p[w];
+    for (int k = 0; k < kThreads / 32; k++) t += warp_p[k];
     if (t) atomicAdd(P, t);
+  }
+}
+
+// Dense X (most entries have a Y run): count entries per X free key and the products,
+// without writing a survivor list.
+template <int ORDER, bool VEC>
+__global__ void __launch_bounds__(kThreads) x_count_kernel(const int32_t* __restrict__ coords, int64_t n, KeyPlan p,
+                                                           const uint32_t* __restrict__ yoff, u64* __restrict__ P,
+                                                           uint32_t* __restrict__ gcnt, uint32_t* status) {
+  __shared__ u64 warp_p[kThreads / 32];
+  u64 my_p = 0;
+  STC_WARP_ROWS(base, n) {
+    uint64_t fk[kRows];
+    uint32_t lo[kRows], w[kRows];
+    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status);
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      if (w[r] > 0) {
+        my_p += w[r];
+        atomicAdd(gcnt + fk[r], 1u);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_p += __shfl_down_sync(0xffffffffu, my_p, o);
+  if (lane_id() == 0) warp_p[threadIdx.x >> 5] = my_p;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 t = 0;
+    for (int k = 0; k < kThreads / 32; k++) t += warp_p[k];
+    if (t) atomicAdd(P, t);
+  }
+}
+
+// Dense X: read X again and place every entry with a Y run at its group's cursor.
+template <int ORDER, bool VEC>
+__global__ void __launch_bounds__(kThreads) x_scatter_dense_kernel(const int32_t* __restrict__ coords,
+                                                                   const double* __restrict__ vals, int64_t n,
+                                                                   KeyPlan p, const uint32_t* __restrict__ yoff,
+                                                                   uint32_t* __restrict__ gcur, GroupedX gx,
+                                                                   uint32_t* status) {
+  STC_WARP_ROWS(base, n) {
+    uint64_t fk[kRows];
+    uint32_t lo[kRows], w[kRows];
+    double v[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      const int64_t i = base + lane_id() + 32 * r;
+      if (i < n) v[r] = __ldg(vals + i);
+    }
+    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status);
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      if (w[r] > 0) {
+        const uint32_t pos = atomicAdd(gcur + fk[r], 1u);
+        gx.ystart[pos] = lo[r];
+        gx.w[pos] = w[r];
+        gx.v[pos] = v[r];
+      }
+    }
   }
 }
 
@@ -184,7 +300,7 @@ cudaError_t launch_key_scatter(const u64* keys, int64_t n, u64 k, uint32_t* curs
 cudaError_t launch_y_count(const int32_t* coords, int64_t n, const KeyPlan& p, uint32_t* cnt, uint32_t* status,
                            int sms, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const unsigned g = grid_for(n, sms);
+  const unsigned g = grid_for((n + kRows - 1) / kRows, sms);
   return dispatch_order(p.order, vec_ok(coords, p.order), [&]<int O, bool V>() {
     y_count_kernel<O, V><<<g, kThreads, 0, s>>>(coords, n, p, cnt, status);
     note_launch();
@@ -193,27 +309,54 @@ cudaError_t launch_y_count(const int32_t* coords, int64_t n, const KeyPlan& p, u
 }
 
 cudaError_t launch_y_scatter(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
-                             uint32_t* cursor, u64* yfk, double* yv, int sms, cudaStream_t s) {
+                             uint32_t* cursor, void* yfk, bool key32, double* yv, int sms, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const unsigned g = grid_for(n, sms);
+  const unsigned g = grid_for((n + kRows - 1) / kRows, sms);
   return dispatch_order(p.order, vec_ok(coords, p.order), [&]<int O, bool V>() {
-    y_scatter_kernel<O, V><<<g, kThreads, 0, s>>>(coords, vals, n, p, cursor, yfk, yv);
+    if (key32)
+      y_scatter_kernel<O, V, uint32_t>
+          <<<g, kThreads, 0, s>>>(coords, vals, n, p, cursor, static_cast<uint32_t*>(yfk), yv);
+    else
+      y_scatter_kernel<O, V, u64><<<g, kThreads, 0, s>>>(coords, vals, n, p, cursor, static_cast<u64*>(yfk), yv);
     note_launch();
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
-                            const uint32_t* yoff, Survivors sv, u64* P, uint32_t* gcnt, u64* gbound,
-                            uint32_t* status, int sms, cudaStream_t s) {
+                            const uint32_t* yoff, Survivors sv, u64* P, uint32_t* gcnt, uint32_t* status, int sms,
+                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const unsigned g = grid_for(n, sms);
+  const unsigned g = grid_for((n + kRows - 1) / kRows, sms);
   const bool groups = gcnt != nullptr;
   return dispatch_order(p.order, vec_ok(coords, p.order), [&]<int O, bool V>() {
     if (groups)
-      x_survey_kernel<O, V, true><<<g, kThreads, 0, s>>>(coords, vals, n, p, yoff, sv, P, gcnt, gbound, status);
+      x_survey_kernel<O, V, true><<<g, kThreads, 0, s>>>(coords, vals, n, p, yoff, sv, P, gcnt, status);
     else
-      x_survey_kernel<O, V, false><<<g, kThreads, 0, s>>>(coords, vals, n, p, yoff, sv, P, gcnt, gbound, status);
+      x_survey_kernel<O, V, false><<<g, kThreads, 0, s>>>(coords, vals, n, p, yoff, sv, P, gcnt, status);
+    note_launch();
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_x_count(const int32_t* coords, int64_t n, const KeyPlan& p, const uint32_t* yoff, u64* P,
+                           uint32_t* gcnt, uint32_t* status, int sms, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned g = grid_for((n + kRows - 1) / kRows, sms);
+  return dispatch_order(p.order, vec_ok(coords, p.order), [&]<int O, bool V>() {
+    x_count_kernel<O, V><<<g, kThreads, 0, s>>>(coords, n, p, yoff, P, gcnt, status);
+    note_launch();
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_x_scatter_dense(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
+                                   const uint32_t* yoff, uint32_t* gcur, GroupedX gx, uint32_t* status, int sms,
+                                   cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned g = grid_for((n + kRows - 1) / kRows, sms);
+  return dispatch_order(p.order, vec_ok(coords, p.order), [&]<int O, bool V>() {
+    x_scatter_dense_kernel<O, V><<<g, kThreads, 0, s>>>(coords, vals, n, p, yoff, gcur, gx, status);
     note_launch();
     return cudaGetLastError();
   });
