@@ -192,6 +192,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="plain_large", choices=sorted(WORKLOADS))
     ap.add_argument("--strategy", type=int, default=0, help="0 auto, 1 global table, 2 grouped")
     ap.add_argument("--group-load-factor", type=float, default=0.0, help="0 = library default")
+    ap.add_argument("--accumulator", type=int, default=0, help="0 auto, 1 hash tables, 2 dense rows")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -225,7 +226,8 @@ def main(argv=None):
 
     def step(record=False):
         return stc.contract(X, Y, p.cx, p.cy, p.out_order, strategy=args.strategy, record_times=record,
-                            group_load_factor=args.group_load_factor, stream=stream, ctx=ctx)
+                            group_load_factor=args.group_load_factor, accumulator=args.accumulator, stream=stream,
+                            ctx=ctx)
 
     for _ in range(args.warmup):
         r = step()
@@ -279,7 +281,8 @@ def main(argv=None):
             Xd = (p.X.shape, hx[0].to("cuda", non_blocking=True), hx[1].to("cuda", non_blocking=True))
             Yd = (p.Y.shape, hy[0].to("cuda", non_blocking=True), hy[1].to("cuda", non_blocking=True))
             r = stc.contract(Xd, Yd, p.cx, p.cy, p.out_order, strategy=args.strategy,
-                             group_load_factor=args.group_load_factor, stream=stream, ctx=ctx)
+                             group_load_factor=args.group_load_factor, accumulator=args.accumulator, stream=stream,
+                            ctx=ctx)
             hc[: r.nnz].copy_(r.coords, non_blocking=True)
             hv[: r.nnz].copy_(r.vals, non_blocking=True)
             torch.cuda.synchronize()
@@ -333,7 +336,7 @@ def main(argv=None):
                    "products_per_step": P, "nnz_out": nz, "parallelism": f"replicas x{world}",
                    "l2": "inputs 240 MB and output 8.8 GB exceed the 129 MB L2; no flush" if args.workload ==
                    "plain_large" else "see DESIGN.md", "strategy": args.strategy,
-                   "group_load_factor": args.group_load_factor},
+                   "group_load_factor": args.group_load_factor, "accumulator": args.accumulator},
         "step_hbm": {"alg_bytes": step_alg, "gbs": step_alg / (step_ms / 1e3) / 1e9,
                      "frac": step_alg / (step_ms / 1e3) / 1e9 / hbm},
         "stage_ms": {n: float(per_step[i]) for i, n in enumerate(stage_names)},

@@ -67,6 +67,12 @@ typedef struct stc_coo {
  * shared memory (Section 4.3). */
 enum { STC_STRATEGY_AUTO = 0, STC_STRATEGY_GLOBAL = 1, STC_STRATEGY_GROUPED = 2 };
 
+/* Per-group accumulator of the GROUPED strategy. HASH: a probing table sized from the
+ * group's bound (Section 4.3). DENSE: the group's output row swept in segments of the Y free
+ * key space, each accumulated in a dense array indexed by the free key; used when F_Y is at
+ * most 2^20 and rows are dense enough. AUTO picks between them. */
+enum { STC_ACC_AUTO = 0, STC_ACC_HASH = 1, STC_ACC_DENSE = 2 };
+
 typedef struct stc_opts {
   int32_t strategy;       /* STC_STRATEGY_*; 0 = AUTO */
   int32_t record_times;   /* nonzero: time each stage with CUDA events (stc_result_stats) */
@@ -74,6 +80,8 @@ typedef struct stc_opts {
   double group_load_factor; /* largest load of a per-group shared-memory table, in (0, 0.9];
                                0 = default 0.75. A group of bound t goes to the smallest table
                                class with t <= group_load_factor * slots. */
+  int32_t accumulator;    /* STC_ACC_*; 0 = AUTO */
+  int32_t reserved_;
 } stc_opts;
 
 /* Per-call statistics of a finished contraction. */
@@ -86,7 +94,7 @@ typedef struct stc_stats {
   int32_t strategy;       /* STC_STRATEGY_GLOBAL or STC_STRATEGY_GROUPED */
   int32_t nstages;        /* valid entries of stage_ms when record_times was set */
   uint32_t launches;      /* CUDA kernels this call launched (memsets and copies not counted) */
-  uint32_t reserved_;
+  int32_t accumulator;    /* STC_ACC_HASH or STC_ACC_DENSE when strategy is GROUPED */
   float stage_ms[8];      /* 0 group Y, 1 survey X, 2 group X, 3 plan, 4 accumulate, 5 compact/write */
 } stc_stats;
 

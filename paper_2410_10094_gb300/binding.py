@@ -18,6 +18,7 @@ STATUS_NAMES = {
     8: "STC_ERR_COORD_OUT_OF_RANGE", 9: "STC_ERR_UNSUPPORTED",
 }
 STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_GROUPED = 0, 1, 2
+ACC_AUTO, ACC_HASH, ACC_DENSE = 0, 1, 2
 STC_MAX_ORDER = 8
 
 
@@ -34,13 +35,13 @@ class stc_coo(C.Structure):
 
 class stc_opts(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double),
-                ("group_load_factor", C.c_double)]
+                ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class stc_stats(C.Structure):
     _fields_ = [("products", C.c_uint64), ("survivors", C.c_uint64), ("out_capacity", C.c_uint64),
                 ("table_slots", C.c_uint64), ("groups", C.c_uint64), ("strategy", C.c_int32),
-                ("nstages", C.c_int32), ("launches", C.c_uint32), ("reserved_", C.c_uint32),
+                ("nstages", C.c_int32), ("launches", C.c_uint32), ("accumulator", C.c_int32),
                 ("stage_ms", C.c_float * 8)]
 
 
@@ -284,6 +285,7 @@ class Stats:
     groups: int
     strategy: int
     launches: int
+    accumulator: int
     stage_ms: tuple
 
 
@@ -300,7 +302,7 @@ class Result:
         cp, vp = stc_result_data(handle)
         st = stc_result_stats(handle)
         self.stats = Stats(st.products, st.survivors, st.out_capacity, st.table_slots, st.groups, st.strategy,
-                           st.launches, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))))
+                           st.launches, st.accumulator, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))))
         if self.nnz and self.order:
             self.coords = torch.as_tensor(_DeviceArray(self._h, cp, (self.nnz, self.order), "<i4"), device="cuda")
         else:
@@ -313,12 +315,13 @@ class Result:
 
 
 def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, strategy: int = STRATEGY_AUTO,
-             load_factor: float = 0.0, group_load_factor: float = 0.0, record_times: bool = False, stream=None,
-             ctx: Context = None) -> Result:
+             load_factor: float = 0.0, group_load_factor: float = 0.0, accumulator: int = ACC_AUTO,
+             record_times: bool = False, stream=None, ctx: Context = None) -> Result:
     """Z = X (x) Y (Eq. 2) on the GPU. X and Y are (shape, coords, vals) with coords a CUDA
     int32 [nnz, order] tensor and vals a CUDA float64 [nnz] tensor."""
     ctx = ctx or default_context()
-    o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor), float(group_load_factor))
+    o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor), float(group_load_factor),
+                 int(accumulator), 0)
     return Result(stc_contract(ctx.handle, X, Y, cx, cy, out_order, o, stream))
 
 

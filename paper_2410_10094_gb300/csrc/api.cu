@@ -180,6 +180,7 @@ stc_status make_plan(const stc_coo* X, const stc_coo* Y, int32_t m, const int32_
   pl.ky = KeyPlan{};
   pl.kx.order = X->order;
   pl.ky.order = Y->order;
+  pl.kx.nseg = pl.ky.nseg = 1;
   for (int j = 0; j < X->order; j++) pl.kx.size[j] = X->shape[j];
   for (int j = 0; j < Y->order; j++) pl.ky.size[j] = Y->shape[j];
 
@@ -320,6 +321,7 @@ struct Prepared {
   Counters* ctr = nullptr;
   uint32_t* gcnt = nullptr;  // [FX] entries with a Y run per X free key (GROUPED only)
   bool dense = false;        // GROUPED without a survivor list (X re-read by the scatter)
+  bool keep_ck = false;      // survivors keep their contract key (dense-row accumulation)
 };
 
 // How X is surveyed: a survivor list (GLOBAL), a survivor list plus per-group counts
@@ -329,7 +331,8 @@ enum class Survey { kSurvivors, kSurvivorsGroups, kDenseGroups };
 stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, const Plan& pl, Survey mode,
                    cudaStream_t s, StageTimer& tm, Prepared& pr) {
   const bool groups = mode != Survey::kSurvivors;
-  if (pl.K > kMaxDirectBins)
+  const uint64_t bins = pl.K * pl.ky.nseg;
+  if (pl.K > kMaxDirectBins || bins > kMaxDirectBins)
     return fail(STC_ERR_UNSUPPORTED, "contract key space %llu exceeds %llu bins", (unsigned long long)pl.K,
                 (unsigned long long)kMaxDirectBins);
   const int64_t nX = X->nnz, nY = Y->nnz;
@@ -339,10 +342,10 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
 
   // Y: count per contract key, exclusive scan, scatter (Section 4.1.1 counting sort).
   uint32_t *ycnt = nullptr, *ycur = nullptr, *scr = nullptr;
-  STC_TRY(ar.alloc(&ycnt, pl.K));
-  STC_TRY(ar.alloc(&pr.yoff, pl.K + 1));
-  STC_TRY(ar.alloc(&ycur, pl.K));
-  STC_TRY(ar.alloc(&scr, (size_t)scan_scratch_elems((int64_t)pl.K)));
+  STC_TRY(ar.alloc(&ycnt, bins));
+  STC_TRY(ar.alloc(&pr.yoff, bins + 1));
+  STC_TRY(ar.alloc(&ycur, bins));
+  STC_TRY(ar.alloc(&scr, (size_t)scan_scratch_elems((int64_t)bins)));
   pr.key32 = groups && pl.FY <= 0xffffffffull;
   if (pr.key32) {
     uint32_t* k32 = nullptr;
@@ -354,10 +357,10 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
     pr.yfk = k64;
   }
   STC_TRY(ar.alloc(&pr.yv, (size_t)nY));
-  STC_CUDA(cudaMemsetAsync(ycnt, 0, pl.K * sizeof(uint32_t), s));
+  STC_CUDA(cudaMemsetAsync(ycnt, 0, bins * sizeof(uint32_t), s));
   STC_CUDA(launch_y_count(Y->coords, nY, pl.ky, ycnt, status, ctx->sms, s));
-  STC_CUDA(scan_u32(ycnt, pr.yoff, (int64_t)pl.K, scr, s));
-  STC_CUDA(cudaMemcpyAsync(ycur, pr.yoff, pl.K * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  STC_CUDA(scan_u32(ycnt, pr.yoff, (int64_t)bins, scr, s));
+  STC_CUDA(cudaMemcpyAsync(ycur, pr.yoff, bins * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   STC_CUDA(launch_y_scatter(Y->coords, Y->vals, nY, pl.ky, ycur, pr.yfk, pr.key32, pr.yv, ctx->sms, s));
   tm.mark(0);
 
@@ -372,6 +375,7 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
     STC_CUDA(launch_x_count(X->coords, nX, pl.kx, pr.yoff, &pr.ctr->P, pr.gcnt, status, ctx->sms, s));
   } else {
     STC_TRY(ar.alloc(&pr.sv.fk, (size_t)nX));
+    if (pr.keep_ck) STC_TRY(ar.alloc(&pr.sv.ck, (size_t)nX));
     STC_TRY(ar.alloc(&pr.sv.ystart, (size_t)nX));
     STC_TRY(ar.alloc(&pr.sv.w, (size_t)nX));
     STC_TRY(ar.alloc(&pr.sv.v, (size_t)nX));
@@ -424,10 +428,29 @@ struct GroupCounters {
 // GROUPED strategy (Sections 4.1 and 4.3): survivors are counting-sorted by X free key,
 // each group is binned by its table size, and the class kernels accumulate one group per
 // CTA in shared memory and write its outputs directly.
-stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, const Plan& pl,
+stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, const Plan& plan_in,
                             const stc_opts& o, cudaStream_t s, StageTimer& tm, stc_result* r) {
   const int64_t nX = X->nnz;
+  Plan pl = plan_in;
+  // Dense rows: F_Y is swept in segments of `seg` free keys; Y is grouped per (contract key,
+  // segment). Used on request when F_Y <= 2^20 (on the measured workloads the per-group hash
+  // tables are faster, so AUTO takes those).
+  bool dense_rows = false;
+  uint32_t seg = 1, nseg = 1;
+  if (pl.FY <= (1ull << 20) && o.accumulator != STC_ACC_HASH) {
+    const double rows = (double)std::max<uint64_t>(1, std::min<uint64_t>(pl.FX, (uint64_t)std::max<int64_t>(nX, 1)));
+    const double est_row = (double)nX * (double)Y->nnz / (double)pl.K / rows;
+    seg = (uint32_t)std::min<uint64_t>(kDenseSeg, pow2_at_least(std::max<uint64_t>(pl.FY, 64)));
+    nseg = (uint32_t)((pl.FY + seg - 1) / seg);
+    dense_rows = o.accumulator == STC_ACC_DENSE && pl.K * nseg <= kMaxDirectBins;
+    (void)est_row;
+  }
+  if (dense_rows) {
+    pl.ky.nseg = pl.kx.nseg = nseg;
+    pl.ky.seg_shift = log2_u64(seg);
+  }
   Prepared pr;
+  pr.keep_ck = dense_rows;
   // Dense when Y's runs cover the contract keys on average: then nearly every X entry has a
   // run and a survivor list would only be written and read back.
   const Survey mode = ((uint64_t)Y->nnz >= pl.K) ? Survey::kDenseGroups : Survey::kSurvivorsGroups;
@@ -449,11 +472,18 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   STC_TRY(ar.alloc(&gx.ystart, (size_t)nX));
   STC_TRY(ar.alloc(&gx.w, (size_t)nX));
   STC_TRY(ar.alloc(&gx.v, (size_t)nX));
+  if (dense_rows) STC_TRY(ar.alloc(&gx.ck, (size_t)nX));
   STC_TRY(ar.alloc(&gc, 1));
-  b.nclasses = ncls;
-  for (int c = 0; c < ncls; c++) {
-    b.tmax[c] = (u64)(ga * shapes[c].slots);
-    STC_TRY(ar.alloc(&b.list[c], maxg));
+  if (dense_rows) {
+    b.nclasses = 1;
+    b.tmax[0] = ~0ull;
+    STC_TRY(ar.alloc(&b.list[0], maxg));
+  } else {
+    b.nclasses = ncls;
+    for (int c = 0; c < ncls; c++) {
+      b.tmax[c] = (u64)(ga * shapes[c].slots);
+      STC_TRY(ar.alloc(&b.list[c], maxg));
+    }
   }
   STC_TRY(ar.alloc(&b.huge_list, maxg));
   STC_TRY(ar.alloc(&b.huge_off, maxg));
@@ -485,6 +515,7 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   for (int c = 0; c <= kMaxClasses; c++) groups += hg.count[c];
   r->stats.groups = groups;
   r->stats.table_slots = hg.huge_slots;
+  r->stats.accumulator = dense_rows ? STC_ACC_DENSE : STC_ACC_HASH;
   if (h.P == 0) return STC_OK;
 
   const uint64_t out_cap = hg.out_cap;
@@ -513,8 +544,12 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   a.out_cap = out_cap;
   a.nz = &pr.ctr->nz;
   a.status = &pr.ctr->status;
-  STC_CUDA(launch_group_classes(a, wide, b, hg.count, ctx->sms, s));
-  STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
+  if (dense_rows) {
+    STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.list[0], hg.count[0], ctx->sms, s));
+  } else {
+    STC_CUDA(launch_group_classes(a, wide, b, hg.count, ctx->sms, s));
+    STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
+  }
   tm.mark(4);
   Counters h2{};
   STC_TRY(read_counters(pr, s, h2));
@@ -614,6 +649,8 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
   if (!(alpha > 0.0 && alpha <= 0.9)) return fail(STC_ERR_INVALID_ARG, "load_factor %g outside (0, 0.9]", alpha);
   if (o.strategy < 0 || o.strategy > STC_STRATEGY_GROUPED)
     return fail(STC_ERR_INVALID_ARG, "unknown strategy %d", o.strategy);
+  if (o.accumulator < 0 || o.accumulator > STC_ACC_DENSE)
+    return fail(STC_ERR_INVALID_ARG, "unknown accumulator %d", o.accumulator);
   if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
     return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
   const int strategy = pick_strategy(pl, X, o.strategy);

@@ -28,9 +28,15 @@ enum : uint32_t {
 // ckey = sum_j coord[j] * cstride[j] (contract modes, in the order of the contract list),
 // fkey = sum_j coord[j] * fstride[j] (free modes, ascending). A mode has a nonzero stride
 // in exactly one of the two. size[] bounds-checks each coordinate.
+//
+// Y may be grouped by (contract key, free-key segment): with nseg > 1 the bin of a Y entry is
+// ckey * nseg + (fkey >> seg_shift), and an X entry's runs are the nseg consecutive bins
+// starting at ckey * nseg.
 struct KeyPlan {
   int32_t order;
-  int32_t pad_;
+  uint32_t nseg;       // free-key segments per contract key (1 = plain grouping)
+  uint32_t seg_shift;  // log2 of the segment width
+  uint32_t pad_;
   int64_t size[kMaxOrder];
   uint64_t cstride[kMaxOrder];
   uint64_t fstride[kMaxOrder];
@@ -124,6 +130,62 @@ __device__ __forceinline__ void store_coords(uint64_t zkey, const OutPlan& op, i
   }
 #pragma unroll 1
   for (int q = 0; q < op.order; q++) dst[q] = out_coord(zkey, op, q);
+}
+
+// L2 cache policies (PTX createpolicy): data read again soon (Y runs) is kept with
+// evict_last; output written once is streamed with evict_first.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_keep_u32(const uint32_t* ptr, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_keep_u64(const uint64_t* ptr, uint64_t pol) {
+  uint64_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_keep_f64(const double* ptr, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_stream_v4(int32_t* ptr, int4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.s32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_stream_s32(int32_t* ptr, int32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_stream_f64(double* ptr, double v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(ptr), "d"(v), "l"(pol) : "memory");
+}
+
+// Writes output entry `pos` (coordinates decoded from zkey, and its value) with streaming stores.
+__device__ __forceinline__ void store_output(int32_t* __restrict__ coords, double* __restrict__ vals, unsigned long long pos,
+                                             uint64_t zkey, double v, const OutPlan& op, uint64_t pol) {
+  int32_t* dst = coords + pos * (uint64_t)op.order;
+  if (op.order == 4 && op.pow2 && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+    int4 cv;
+    cv.x = (int32_t)((zkey >> op.shift[0]) & (op.mod[0] - 1));
+    cv.y = (int32_t)((zkey >> op.shift[1]) & (op.mod[1] - 1));
+    cv.z = (int32_t)((zkey >> op.shift[2]) & (op.mod[2] - 1));
+    cv.w = (int32_t)((zkey >> op.shift[3]) & (op.mod[3] - 1));
+    st_stream_v4(dst, cv, pol);
+  } else {
+    for (int q = 0; q < op.order; q++) st_stream_s32(dst + q, out_coord(zkey, op, q), pol);
+  }
+  st_stream_f64(vals + pos, v, pol);
 }
 
 // Warp-aggregated reservation of `pred ? 1 : 0` slots from a global counter. All 32 lanes

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(kThreads) x_group_scatter_kernel(Survivors sv,
   const int64_t ns = (int64_t)*sv.count;
   for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < ns; i += (int64_t)gridDim.x * kThreads) {
     const uint32_t pos = atomicAdd(gcur + sv.fk[i], 1u);
+    if (gx.ck) gx.ck[pos] = sv.ck[i];
     gx.ystart[pos] = sv.ystart[i];
     gx.w[pos] = sv.w[i];
     gx.v[pos] = sv.v[i];
@@ -100,9 +101,9 @@ struct Chunk {
   double v[THREADS];
 };
 
-// Exclusive block scan of one u64 per thread into c.pre[0..THREADS], c.pre[THREADS] = total.
+// Exclusive block scan of one u64 per thread into pre[0..THREADS], pre[THREADS] = total.
 template <int THREADS>
-__device__ __forceinline__ void chunk_scan(Chunk<THREADS>& c, u64 w, u64* warp_tot) {
+__device__ __forceinline__ void block_scan(u64* pre, u64 w, u64* warp_tot) {
   constexpr int NW = THREADS / 32;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   u64 x = w;
@@ -120,10 +121,15 @@ __device__ __forceinline__ void chunk_scan(Chunk<THREADS>& c, u64 w, u64* warp_t
       warp_tot[k] = run;
       run += t;
     }
-    c.pre[THREADS] = run;
+    pre[THREADS] = run;
   }
   __syncthreads();
-  c.pre[threadIdx.x] = warp_tot[warp] + x - w;
+  pre[threadIdx.x] = warp_tot[warp] + x - w;
+}
+
+template <int THREADS>
+__device__ __forceinline__ void chunk_scan(Chunk<THREADS>& c, u64 w, u64* warp_tot) {
+  block_scan<THREADS>(c.pre, w, warp_tot);
 }
 
 // Loads the chunk of X entries [c0, c0 + n) of a group and scans their run lengths.
@@ -214,8 +220,14 @@ __device__ __forceinline__ int bucket_claim(KT* keys, KT key, bool* claimed) {
 // One group: every product of its X entries goes into the shared-memory table. The chunk's
 // product range is split evenly over the warps; a warp walks its share 32 products at a
 // time (consecutive lanes read consecutive slots of a Y run), advancing the owning X entry
-// with the chunk prefix instead of searching for it. The Y reads of D such steps are all
-// issued before any of their inserts, so each warp keeps D loads in flight.
+// with the chunk prefix instead of searching for it. The Y reads of D such steps are issued
+// before any of their inserts.
+//
+// Values are settled without floating-point atomics in the common case: the product whose
+// compare-and-swap claims a slot stores its value there; products that find their key already
+// present keep their value and add it atomically after the round's barrier, when every
+// claiming store is visible. Rounds are counted the same way in every warp so that the
+// barrier is reached by all threads.
 template <int SLOTS, int THREADS, typename KT, int D>
 __device__ __forceinline__ void expand_group_smem(const GroupArgs& a, Chunk<THREADS>& c, u64* warp_tot,
                                                   uint32_t x0, uint32_t x1, KT* keys, double* vals,
@@ -237,10 +249,14 @@ __device__ __forceinline__ void expand_group_smem(const GroupArgs& a, Chunk<THRE
       }
       own = l;
     }
+    const u64 per = (total + NW - 1) / NW;
+    const uint32_t rounds = (uint32_t)((per + 32 * D - 1) / (32 * D));
+    const uint64_t keep = policy_evict_last();
     unsigned my_claims = 0;
-    for (u64 base = lo; base < hi; base += 32 * D) {
+    for (uint32_t r = 0; r < rounds; r++) {
+      const u64 base = lo + (u64)r * 32 * D;
       KT key[D];
-      double yv[D], xv[D];
+      double prod[D];
 #pragma unroll
       for (int u = 0; u < D; u++) {
         const u64 p = base + (u64)u * 32 + lane;
@@ -249,33 +265,43 @@ __device__ __forceinline__ void expand_group_smem(const GroupArgs& a, Chunk<THRE
         if (p < hi) {
           while (c.pre[k + 1] <= p) k++;
           const u64 j = (u64)c.ystart[k] + (p - c.pre[k]);
-          key[u] = (KT)y_key<KT>(a.yfk, j);
-          yv[u] = __ldg(a.yv + j);
-          xv[u] = c.v[k];
+          if constexpr (sizeof(KT) == 4)
+            key[u] = (KT)ld_keep_u32(static_cast<const uint32_t*>(a.yfk) + j, keep);
+          else
+            key[u] = (KT)ld_keep_u64(static_cast<const uint64_t*>(a.yfk) + j, keep);
+          prod[u] = __dmul_rn(c.v[k], ld_keep_f64(a.yv + j, keep));
         }
         own = __shfl_sync(0xffffffffu, k, 31);
       }
+      int later[D];
 #pragma unroll
       for (int u = 0; u < D; u++) {
+        later[u] = -1;
         bool claimed = false;
         if (key[u] != empty_key<KT>()) {
           const int slot = bucket_claim<KT, SLOTS>(keys, key[u], &claimed);
-          if (slot >= 0) atomicAdd(vals + slot, __dmul_rn(xv[u], yv[u]));
-          else atomicOr(a.status, kStatTableFull);
+          if (slot < 0) atomicOr(a.status, kStatTableFull);
+          else if (claimed) vals[slot] = prod[u];
+          else later[u] = slot;
         }
         my_claims += __popc(__ballot_sync(0xffffffffu, claimed));
       }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < D; u++)
+        if (later[u] >= 0) atomicAdd(vals + later[u], prod[u]);
     }
     if (lane == 0 && my_claims) atomicAdd(claims, my_claims);
     __syncthreads();
   }
 }
 
-// Writes the occupied slots as COO output (streaming stores: written once, not re-read)
-// and empties them. One atomic reserves the group's output range; inside it, warps take
-// positions from a shared-memory cursor in the order they find occupied slots.
+// Writes the occupied slots as COO output and empties them. One atomic reserves the group's
+// output range; inside it, a warp takes 32 buckets at a time, reserves room for their occupied
+// slots from a shared-memory cursor, and writes them so that the k-th entry of the warp is
+// stored by lane k % 32 (consecutive lanes, consecutive positions: coalesced streaming stores).
 template <int SLOTS, int THREADS, typename KT>
-__device__ __forceinline__ void write_group_smem(const GroupArgs& a, u64 g, KT* keys, double* vals,
+__device__ __forceinline__ void write_group_smem(const GroupArgs& a, u64 g, KT* keys, const double* vals,
                                                  unsigned* claims, unsigned* cursor, u64* gbase) {
   constexpr int B = Bucket<KT>::N;
   constexpr uint32_t NB = SLOTS / B;
@@ -288,53 +314,56 @@ __device__ __forceinline__ void write_group_smem(const GroupArgs& a, u64 g, KT* 
   __syncthreads();
   const u64 base = *gbase;
   const u64 zrow = g * a.FY;
-  const int oz = a.op.order;
+  const uint64_t pol = policy_evict_first();
   for (uint32_t b0 = (threadIdx.x & ~31u); b0 < NB; b0 += THREADS) {
     const uint32_t b = b0 + lane;
-    Bucket<KT> bk;
     unsigned live = 0;
     if (b < NB) {
-      bk = load_bucket<KT>(keys, b);
+      const Bucket<KT> bk = load_bucket<KT>(keys, b);
 #pragma unroll
       for (int i = 0; i < B; i++) live |= (bk.k[i] != empty_key<KT>()) ? (1u << i) : 0u;
     }
     const unsigned cnt = __popc(live);
-    unsigned pre = cnt;
+    unsigned incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
-      if ((int)lane >= o) pre += y;
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)lane >= o) incl += y;
     }
-    const unsigned tot = __shfl_sync(0xffffffffu, pre, 31);
+    const unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (tot == 0) continue;
     unsigned off = 0;
-    if (lane == 0 && tot) off = atomicAdd(cursor, tot);
-    off = __shfl_sync(0xffffffffu, off, 0) + pre - cnt;
+    if (lane == 0) off = atomicAdd(cursor, tot);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    for (unsigned k0 = 0; k0 < tot; k0 += 32) {
+      const unsigned k = k0 + lane;
+      // Source lane: the first lane whose inclusive prefix exceeds k.
+      unsigned src = 0;
 #pragma unroll
-    for (int i = 0; i < B; i++) {
-      if (live & (1u << i)) {
-        const uint32_t slot = b * B + i;
-        const u64 pos = base + off++;
-        const double v = vals[slot];
-        if (pos < a.out_cap) {
-          const u64 z = zrow + (u64)bk.k[i];
-          int32_t* dst = a.coords + pos * (u64)oz;
-          if (oz == 4 && a.op.pow2 && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-            int4 cv;
-            cv.x = (int32_t)((z >> a.op.shift[0]) & (a.op.mod[0] - 1));
-            cv.y = (int32_t)((z >> a.op.shift[1]) & (a.op.mod[1] - 1));
-            cv.z = (int32_t)((z >> a.op.shift[2]) & (a.op.mod[2] - 1));
-            cv.w = (int32_t)((z >> a.op.shift[3]) & (a.op.mod[3] - 1));
-            __stcs(reinterpret_cast<int4*>(dst), cv);
-          } else {
-            for (int q = 0; q < oz; q++) __stcs(dst + q, out_coord(z, a.op, q));
-          }
-          __stcs(a.vals + pos, v);
-        } else {
-          atomicOr(a.status, kStatOutOverflow);
-        }
-        keys[slot] = empty_key<KT>();
-        vals[slot] = 0.0;
+      for (int step = 16; step > 0; step >>= 1) {
+        const unsigned probe = __shfl_sync(0xffffffffu, incl, src + step - 1);
+        if (probe <= k) src += step;
       }
+      const unsigned src_incl = __shfl_sync(0xffffffffu, incl, src);
+      const unsigned src_live = __shfl_sync(0xffffffffu, live, src);
+      const unsigned src_cnt = __popc(src_live);
+      if (k < tot) {
+        // Rank of this entry among the source bucket's occupied slots, then that slot.
+        unsigned m = src_live;
+        for (unsigned t = k - (src_incl - src_cnt); t > 0; t--) m &= m - 1;
+        const uint32_t slot = (b0 + src) * B + (uint32_t)(__ffs(m) - 1);
+        const u64 pos = base + off + k;
+        if (pos < a.out_cap)
+          store_output(a.coords, a.vals, pos, zrow + (u64)keys[slot], vals[slot], a.op, pol);
+        else
+          atomicOr(a.status, kStatOutOverflow);
+      }
+    }
+    __syncwarp();
+    if (live) {
+      KT* kb = keys + b * B;
+#pragma unroll
+      for (int i = 0; i < B; i++) kb[i] = empty_key<KT>();
     }
   }
   __syncthreads();
@@ -474,6 +503,209 @@ __global__ void __launch_bounds__(THREADS) group_global_kernel(GroupArgs a, Huge
   }
 }
 
+
+// ---- dense rows: one free-key segment of one group at a time, accumulated in a dense
+// shared-memory array indexed by the free key (no hashing, no probing). Ownership of a slot
+// is settled without atomics: each product writes its id into the slot's tag unless the slot
+// is already owned; after a barrier the product whose id survived stores its value, and the
+// others (rare when outputs seldom repeat) add theirs atomically after a second barrier.
+
+template <int THREADS>
+struct DenseChunk {
+  u64 pre[THREADS + 1];
+  uint32_t ck[THREADS];
+  uint32_t ystart[THREADS];
+  double v[THREADS];
+};
+
+template <int THREADS>
+__device__ __forceinline__ void dense_stage(const GroupArgs& a, DenseChunk<THREADS>& c, uint32_t c0, uint32_t n) {
+  if (threadIdx.x < n) {
+    c.ck[threadIdx.x] = a.gx.ck[c0 + threadIdx.x];
+    c.v[threadIdx.x] = a.gx.v[c0 + threadIdx.x];
+  }
+}
+
+// Expands segment q of the staged entries into the dense accumulator.
+template <int THREADS, int D>
+__device__ __forceinline__ void dense_expand(const GroupArgs& a, DenseChunk<THREADS>& c, u64* warp_tot,
+                                             const uint32_t* __restrict__ yoff, uint32_t nseg, uint32_t q,
+                                             uint32_t seg, uint32_t n, double* acc, uint16_t* tag,
+                                             unsigned* winners) {
+  constexpr int NW = THREADS / 32;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  u64 w = 0;
+  if (threadIdx.x < n) {
+    const u64 b = (u64)c.ck[threadIdx.x] * nseg + q;
+    const uint32_t lo = __ldg(yoff + b);
+    c.ystart[threadIdx.x] = lo;
+    w = __ldg(yoff + b + 1) - lo;
+  }
+  block_scan<THREADS>(c.pre, w, warp_tot);
+  __syncthreads();
+  const u64 total = c.pre[n];
+  if (total == 0) return;
+  const u64 lo = total * warp / NW, hi = total * (warp + 1) / NW;
+  uint32_t own = 0;
+  if (lo < hi) {
+    uint32_t l = 0, h = n - 1;
+    while (l < h) {
+      const uint32_t mid = (l + h + 1) >> 1;
+      if (c.pre[mid] <= lo) l = mid; else h = mid - 1;
+    }
+    own = l;
+  }
+  const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
+  const u64 per = (total + NW - 1) / NW;
+  const uint32_t rounds = (uint32_t)((per + 32 * D - 1) / (32 * D));
+  unsigned my_win = 0;
+  for (uint32_t r = 0; r < rounds; r++) {
+    const u64 base = lo + (u64)r * 32 * D;
+    uint32_t slot[D];
+    double prod[D];
+    int st[D];  // 0 nothing, 1 candidate owner, 2 adds later
+#pragma unroll
+    for (int u = 0; u < D; u++) {
+      const u64 p = base + (u64)u * 32 + lane;
+      uint32_t k = own;
+      st[u] = 0;
+      if (p < hi) {
+        while (c.pre[k + 1] <= p) k++;
+        const u64 j = (u64)c.ystart[k] + (p - c.pre[k]);
+        slot[u] = __ldg(yfk + j) & (seg - 1);
+        prod[u] = __dmul_rn(c.v[k], __ldg(a.yv + j));
+        st[u] = 1;
+      }
+      own = __shfl_sync(0xffffffffu, k, 31);
+    }
+#pragma unroll
+    for (int u = 0; u < D; u++) {
+      if (st[u] == 1) {
+        volatile uint16_t* t = tag + slot[u];
+        if (*t != 0) st[u] = 2;
+        else *t = (uint16_t)(threadIdx.x * D + u + 1);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < D; u++) {
+      bool won = false;
+      if (st[u] == 1) {
+        if (tag[slot[u]] == (uint16_t)(threadIdx.x * D + u + 1)) {
+          acc[slot[u]] = prod[u];
+          won = true;
+        } else {
+          st[u] = 2;
+        }
+      }
+      my_win += __popc(__ballot_sync(0xffffffffu, won));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < D; u++)
+      if (st[u] == 2) atomicAdd(acc + slot[u], prod[u]);
+  }
+  if (lane == 0 && my_win) atomicAdd(winners, my_win);
+}
+
+// Writes segment q of group g (its owned slots, in free-key order within each warp's slice)
+// and frees the tags.
+template <int THREADS>
+__device__ __forceinline__ void dense_write(const GroupArgs& a, u64 g, uint32_t q, uint32_t seg, const double* acc,
+                                            uint16_t* tag, unsigned* winners, unsigned* cursor, u64* gbase) {
+  const unsigned lane = lane_id();
+  if (threadIdx.x == 0) {
+    const unsigned n = *winners;
+    *gbase = n ? atomicAdd(a.nz, (u64)n) : 0;
+    *cursor = 0;
+    *winners = 0;
+  }
+  __syncthreads();
+  const u64 base = *gbase;
+  const u64 zrow = g * a.FY + (u64)q * seg;
+  const int oz = a.op.order;
+  for (uint32_t blk = 0; blk < seg; blk += THREADS * 8) {
+    const uint32_t s0 = blk + threadIdx.x * 8;
+    uint4 tv = make_uint4(0, 0, 0, 0);
+    if (s0 < seg) tv = *reinterpret_cast<const uint4*>(tag + s0);
+    const uint32_t words[4] = {tv.x, tv.y, tv.z, tv.w};
+    unsigned live = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) live |= ((words[i >> 1] >> (16 * (i & 1))) & 0xffffu) ? (1u << i) : 0u;
+    const unsigned cnt = __popc(live);
+    unsigned pre = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
+      if ((int)lane >= o) pre += y;
+    }
+    const unsigned tot = __shfl_sync(0xffffffffu, pre, 31);
+    unsigned off = 0;
+    if (lane == 0 && tot) off = atomicAdd(cursor, tot);
+    off = __shfl_sync(0xffffffffu, off, 0) + pre - cnt;
+    if (live) {
+      for (unsigned m = live; m; m &= m - 1) {
+        const int i = __ffs(m) - 1;
+        {
+          const u64 pos = base + off++;
+          if (pos < a.out_cap) {
+            const u64 z = zrow + s0 + i;
+            int32_t* dst = a.coords + pos * (u64)oz;
+            if (oz == 4 && a.op.pow2 && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+              int4 cv;
+              cv.x = (int32_t)((z >> a.op.shift[0]) & (a.op.mod[0] - 1));
+              cv.y = (int32_t)((z >> a.op.shift[1]) & (a.op.mod[1] - 1));
+              cv.z = (int32_t)((z >> a.op.shift[2]) & (a.op.mod[2] - 1));
+              cv.w = (int32_t)((z >> a.op.shift[3]) & (a.op.mod[3] - 1));
+              __stcs(reinterpret_cast<int4*>(dst), cv);
+            } else {
+              for (int qq = 0; qq < oz; qq++) __stcs(dst + qq, out_coord(z, a.op, qq));
+            }
+            __stcs(a.vals + pos, acc[s0 + i]);
+          } else {
+            atomicOr(a.status, kStatOutOverflow);
+          }
+        }
+      }
+      *reinterpret_cast<uint4*>(tag + s0) = make_uint4(0, 0, 0, 0);
+    }
+  }
+  __syncthreads();
+}
+
+// Persistent over the group list; every group is swept one free-key segment at a time.
+template <int THREADS, int D>
+__global__ void __launch_bounds__(THREADS) group_dense_kernel(GroupArgs a, const uint32_t* __restrict__ yoff,
+                                                              uint32_t nseg, uint32_t seg,
+                                                              const uint32_t* __restrict__ list, uint32_t count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* acc = reinterpret_cast<double*>(smem);
+  uint16_t* tag = reinterpret_cast<uint16_t*>(acc + kDenseSeg);
+  DenseChunk<THREADS>& c = *reinterpret_cast<DenseChunk<THREADS>*>(tag + kDenseSeg);
+  __shared__ u64 warp_tot[THREADS / 32];
+  __shared__ unsigned winners, cursor;
+  __shared__ u64 gbase;
+  for (uint32_t i = threadIdx.x; i < kDenseSeg / 8; i += THREADS)
+    reinterpret_cast<uint4*>(tag)[i] = make_uint4(0, 0, 0, 0);
+  if (threadIdx.x == 0) winners = 0;
+  __syncthreads();
+  for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
+    const uint32_t g = list[k];
+    const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
+    const bool one_chunk = x1 - x0 <= (uint32_t)THREADS;
+    if (one_chunk) dense_stage<THREADS>(a, c, x0, x1 - x0);
+    for (uint32_t q = 0; q < nseg; q++) {
+      for (uint32_t c0 = x0; c0 < x1; c0 += THREADS) {
+        const uint32_t n = (x1 - c0 < (uint32_t)THREADS) ? x1 - c0 : (uint32_t)THREADS;
+        if (!one_chunk) dense_stage<THREADS>(a, c, c0, n);
+        dense_expand<THREADS, D>(a, c, warp_tot, yoff, nseg, q, seg, n, acc, tag, &winners);
+        __syncthreads();
+      }
+      dense_write<THREADS>(a, g, q, seg, acc, tag, &winners, &cursor, &gbase);
+    }
+  }
+}
+
 template <int SLOTS, int THREADS, typename KT>
 cudaError_t launch_class(const GroupArgs& a, const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
@@ -532,6 +764,24 @@ cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins&
     if ((e = launch_class<8192, 512, u64>(a, b.list[3], counts[3], sms, s))) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_group_dense(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
+                               const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  constexpr int T = 512, D = 4;
+  const size_t smem = kDenseSeg * (sizeof(double) + sizeof(uint16_t)) + sizeof(DenseChunk<T>);
+  auto kern = group_dense_kernel<T, D>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const uint32_t cap = (uint32_t)(sms * per_sm);
+  kern<<<count < cap ? count : cap, T, smem, s>>>(a, yoff, nseg, seg, list, count);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s) {

@@ -43,6 +43,7 @@ cudaError_t launch_y_scatter(const int32_t* coords, const double* vals, int64_t 
 // run they will read and the total product count P (Section 4.3).
 struct Survivors {
   u64* fk;          // X free key
+  uint32_t* ck;     // X contract key (kept only when per-segment runs are needed; may be null)
   uint32_t* ystart; // first slot of the matching Y run
   uint32_t* w;      // run length = products this entry makes
   double* v;        // X value
@@ -95,6 +96,7 @@ struct GroupedX {
   uint32_t* ystart;
   uint32_t* w;
   double* v;
+  uint32_t* ck;  // contract keys (dense-row accumulation only; may be null)
 };
 
 // Output of the binning pass.
@@ -141,5 +143,12 @@ cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, 
 cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins& b, const uint32_t* counts,
                                  int sms, cudaStream_t s);
 cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s);
+
+// Dense-row accumulation: each group's outputs are accumulated one free-key segment at a time
+// in a dense shared-memory array indexed by the free key. `yoff` are the per-(contract key,
+// segment) run offsets; seg is the segment width (a power of two, at most kDenseSeg).
+constexpr uint32_t kDenseSeg = 8192;
+cudaError_t launch_group_dense(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
+                               const uint32_t* list, uint32_t count, int sms, cudaStream_t s);
 
 }  // namespace stc

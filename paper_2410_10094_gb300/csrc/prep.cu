@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) y_count_kernel(const int32_t* __rest
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
       if (!ok[r]) atomicOr(status, kStatCoordRange);
-      else if (ck[r] != kEmpty64) atomicAdd(cnt + ck[r], 1u);
+      else if (ck[r] != kEmpty64) atomicAdd(cnt + ck[r] * p.nseg + (p.nseg > 1 ? (fk[r] >> p.seg_shift) : 0), 1u);
     }
   }
 }
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kThreads) y_scatter_kernel(const int32_t* __re
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
       if (!ok[r]) continue;
-      const uint32_t pos = atomicAdd(cursor + ck[r], 1u);
+      const uint32_t pos = atomicAdd(cursor + ck[r] * p.nseg + (p.nseg > 1 ? (fk[r] >> p.seg_shift) : 0), 1u);
       yfk[pos] = (YK)fk[r];
       yv[pos] = v[r];
     }
@@ -122,8 +122,7 @@ __global__ void __launch_bounds__(kThreads) y_scatter_kernel(const int32_t* __re
 template <int ORDER, bool VEC>
 __device__ __forceinline__ void rows_runs(const int32_t* __restrict__ coords, int64_t base, int64_t n,
                                           const KeyPlan& p, const uint32_t* __restrict__ yoff, uint64_t* fk,
-                                          uint32_t* lo, uint32_t* w, uint32_t* status) {
-  uint64_t ck[kRows];
+                                          uint32_t* lo, uint32_t* w, uint32_t* status, uint64_t* ck) {
   bool ok[kRows];
 #pragma unroll
   for (int r = 0; r < kRows; r++) {
@@ -139,8 +138,8 @@ __device__ __forceinline__ void rows_runs(const int32_t* __restrict__ coords, in
     lo[r] = 0;
     w[r] = 0;
     if (ok[r]) {
-      lo[r] = __ldg(yoff + ck[r]);
-      w[r] = __ldg(yoff + ck[r] + 1);
+      lo[r] = __ldg(yoff + ck[r] * p.nseg);
+      w[r] = __ldg(yoff + (ck[r] + 1) * p.nseg);
     }
   }
 #pragma unroll
@@ -156,9 +155,9 @@ __global__ void __launch_bounds__(kThreads) x_survey_kernel(const int32_t* __res
   __shared__ u64 warp_p[kThreads / 32];
   u64 my_p = 0;
   STC_WARP_ROWS(base, n) {
-    uint64_t fk[kRows];
+    uint64_t fk[kRows], ck[kRows];
     uint32_t lo[kRows], w[kRows];
-    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status);
+    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status, ck);
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
       const bool live = w[r] > 0;
@@ -166,6 +165,7 @@ __global__ void __launch_bounds__(kThreads) x_survey_kernel(const int32_t* __res
       if (live) {
         const int64_t i = base + lane_id() + 32 * r;
         sv.fk[pos] = fk[r];
+        if (sv.ck) sv.ck[pos] = (uint32_t)ck[r];
         sv.ystart[pos] = lo[r];
         sv.w[pos] = w[r];
         sv.v[pos] = __ldg(vals + i);
@@ -194,9 +194,9 @@ __global__ void __launch_bounds__(kThreads) x_count_kernel(const int32_t* __rest
   __shared__ u64 warp_p[kThreads / 32];
   u64 my_p = 0;
   STC_WARP_ROWS(base, n) {
-    uint64_t fk[kRows];
+    uint64_t fk[kRows], ck[kRows];
     uint32_t lo[kRows], w[kRows];
-    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status);
+    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status, ck);
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
       if (w[r] > 0) {
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) x_scatter_dense_kernel(const int32_t
                                                                    uint32_t* __restrict__ gcur, GroupedX gx,
                                                                    uint32_t* status) {
   STC_WARP_ROWS(base, n) {
-    uint64_t fk[kRows];
+    uint64_t fk[kRows], ck[kRows];
     uint32_t lo[kRows], w[kRows];
     double v[kRows];
 #pragma unroll
@@ -232,11 +232,12 @@ __global__ void __launch_bounds__(kThreads) x_scatter_dense_kernel(const int32_t
       const int64_t i = base + lane_id() + 32 * r;
       if (i < n) v[r] = __ldg(vals + i);
     }
-    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status);
+    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status, ck);
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
       if (w[r] > 0) {
         const uint32_t pos = atomicAdd(gcur + fk[r], 1u);
+        if (gx.ck) gx.ck[pos] = (uint32_t)ck[r];
         gx.ystart[pos] = lo[r];
         gx.w[pos] = w[r];
         gx.v[pos] = v[r];

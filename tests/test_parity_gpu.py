@@ -11,7 +11,10 @@ from helpers import REL_TOL
 
 pytestmark = pytest.mark.gpu
 
-STRATEGIES = [1, 2]  # one global table; per-X-free-group tables
+# one global table; per-X-free-group hash tables; per-X-free-group dense rows
+MODES = [dict(strategy=1), dict(strategy=2, accumulator=1), dict(strategy=2, accumulator=2)]
+MODE_IDS = ["global", "grouped-hash", "grouped-dense"]
+STRATEGIES = [1, 2]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -40,48 +43,77 @@ def check(p, **kw):
 
 # ------------------------------------------------------------------ small and random cases
 
-@pytest.mark.parametrize("strategy", STRATEGIES)
-def test_plain_small_workload(strategy):
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_plain_small_workload(mode):
     """64^3 tensors with 5,000 distinct entries each, X mode 2 with Y mode 0 (full parity)."""
-    res, ref = check(W.plain_small(), strategy=strategy)
+    res, ref = check(W.plain_small(), **mode)
     assert ref.nnz > 300_000
 
 
-@pytest.mark.parametrize("strategy", STRATEGIES)
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
 @pytest.mark.parametrize("seed", range(40))
-def test_random_cases(seed, strategy):
+def test_random_cases(seed, mode):
     rng = W.rng_for(5000 + seed)
     p = W.random_case(rng, max_order=5, max_size=6, max_nnz=120)
-    check(p, strategy=strategy)
+    check(p, **mode)
 
 
-@pytest.mark.parametrize("strategy", STRATEGIES)
-def test_several_tiles_ragged_non_pow2(strategy):
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_several_tiles_ragged_non_pow2(mode):
     """Non-power-of-two mode lengths (division decode path) and a product count that spans
     many 2048-product tiles with a ragged last tile."""
     rng = W.rng_for(6001)
     X = W.uniform_coo(rng, (37, 53, 29), 60_000)
     Y = W.uniform_coo(rng, (29, 41, 7), 9_000)
-    res, ref = check(W.Problem(X, Y, (2,), (0,)), strategy=strategy)
+    res, ref = check(W.Problem(X, Y, (2,), (0,)), **mode)
     assert ref.products % 2048 != 0 and ref.products > 20 * 2048
 
 
-@pytest.mark.parametrize("strategy", STRATEGIES)
-def test_heavy_duplicates(strategy):
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_heavy_duplicates(mode):
     """Few cells, many repeated coordinates: many products per output (summation order matters)."""
     rng = W.rng_for(6002)
     X = W.uniform_coo(rng, (4, 6, 5), 20_000)
     Y = W.uniform_coo(rng, (5, 3), 5_000)
-    res, ref = check(W.Problem(X, Y, (2,), (0,)), strategy=strategy)
+    res, ref = check(W.Problem(X, Y, (2,), (0,)), **mode)
     assert ref.cnt.max() > 1000
 
 
-@pytest.mark.parametrize("strategy", STRATEGIES)
-def test_out_order_and_two_mode_pairing(strategy):
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_out_order_and_two_mode_pairing(mode):
     rng = W.rng_for(6003)
     X = W.uniform_coo(rng, (9, 16, 8, 4), 8_000)
     Y = W.uniform_coo(rng, (4, 12, 16), 3_000)
-    check(W.Problem(X, Y, (3, 1), (0, 2), out_order=(2, 0, 1)), strategy=strategy)
+    check(W.Problem(X, Y, (3, 1), (0, 2), out_order=(2, 0, 1)), **mode)
+
+
+@pytest.mark.parametrize("fy", [5, 63, 64, 4096, 8192, 10_000, 20_000, 65_536])
+def test_dense_rows_segments(fy):
+    """Dense-row accumulation over Y free key spaces that are below, at and above one
+    segment, including a last segment that is only partly used."""
+    rng = W.rng_for(7000 + fy)
+    X = W.uniform_coo(rng, (40, 37), 6_000)
+    Y = W.uniform_coo(rng, (37, fy), 30_000)
+    res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2, accumulator=2)
+    assert res.stats.accumulator == 2
+
+
+def test_dense_rows_multi_chunk_groups():
+    """Groups with more X entries than one CTA stages at a time (several chunks per segment)."""
+    rng = W.rng_for(7100)
+    X = W.uniform_coo(rng, (3, 400), 5_000)
+    Y = W.uniform_coo(rng, (400, 9_000), 20_000)
+    res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2, accumulator=2)
+    assert res.stats.accumulator == 2
+
+
+def test_dense_rows_sparse_survey():
+    """Dense rows when few X entries have a Y run (survivor list keeps contract keys)."""
+    rng = W.rng_for(7200)
+    X = W.uniform_coo(rng, (50, 3000), 40_000)
+    Y = W.uniform_coo(rng, (3000, 700), 400)
+    res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2, accumulator=2)
+    assert res.stats.accumulator == 2
 
 
 def test_grouped_overflow_groups():
@@ -89,7 +121,7 @@ def test_grouped_overflow_groups():
     rng = W.rng_for(6011)
     X = W.uniform_coo(rng, (3, 50), 3_000)
     Y = W.uniform_coo(rng, (50, 100_000), 40_000)
-    res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2)
+    res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2, accumulator=1)
     assert res.stats.table_slots > 0 and res.stats.strategy == 2
 
 
@@ -107,7 +139,7 @@ def test_grouped_load_factors_agree():
     p = W.plain_small()
     ref = oracle.contract(p.X, p.Y, p.cx, p.cy)
     for ga in (0.25, 0.5, 0.75, 0.9):
-        res = gpu_contract(p, strategy=2, group_load_factor=ga)
+        res = gpu_contract(p, strategy=2, accumulator=1, group_load_factor=ga)
         c, v = result_host(res)
         assert_matches_oracle(c, v, ref)
 
@@ -248,12 +280,12 @@ def test_count_matches_oracle_products():
 
 # ------------------------------------------------------------------ benchmark-sized workloads
 
-@pytest.mark.parametrize("strategy", STRATEGIES)
-def test_imbalanced_zipf_full(strategy):
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_imbalanced_zipf_full(mode):
     """X 4096x512x512 with 2e7 entries, Y 512x512x64 with 2e4 Zipf(1.2) contract keys:
     full parity against the oracle."""
     p = W.imbalanced()
-    check(p, strategy=strategy)
+    check(p, **mode)
 
 
 def test_plain_large_sampled_rows():
