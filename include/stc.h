@@ -135,6 +135,28 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
  * number of live results. held_bytes and live_results may be NULL. */
 stc_status stc_ctx_stats(const stc_ctx* ctx, uint64_t* held_bytes, int64_t* live_results);
 
+/* One contraction of a batch: the arguments of stc_contract. */
+typedef struct stc_problem {
+  stc_coo X;
+  stc_coo Y;
+  int32_t ncontract;
+  const int32_t* cx;        /* host, [ncontract] */
+  const int32_t* cy;        /* host, [ncontract] */
+  const int32_t* out_order; /* host or NULL */
+} stc_problem;
+
+/* Contract n independent problems together (each exactly as stc_contract would). The batch
+ * shares every pass: Y of all problems is grouped in one counting sort over the concatenated
+ * contract-key bins, X of all problems is surveyed once, its entries are grouped by
+ * (problem, X free key) through one probing table that gives each pair a small number
+ * (Section 4.1.2), and one launch per table class accumulates the groups of all problems
+ * (small groups one warp each). outs: host, [n], receives one result per problem; the
+ * results share one device allocation that is released when the last of them is freed.
+ * Limits: the batch's total nnz of X and of Y each at most STC_MAX_NNZ, the sum of the
+ * contract key spaces at most 2^26. Errors as stc_contract; on error no result is returned. */
+stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* problems, const stc_opts* opts,
+                              void* stream, stc_result** outs);
+
 /* The exact product count of the contraction (Section 4.3: each X entry meets exactly
  * count_Y[its contract key] Y entries) and the device bytes a stc_contract of the same
  * inputs would hold at its peak (scratch + result). Used to admit work under a budget. */

@@ -33,6 +33,11 @@ class stc_coo(C.Structure):
                 ("coords", C.c_void_p), ("vals", C.c_void_p)]
 
 
+class stc_problem(C.Structure):
+    _fields_ = [("X", stc_coo), ("Y", stc_coo), ("ncontract", C.c_int32), ("cx", C.POINTER(C.c_int32)),
+                ("cy", C.POINTER(C.c_int32)), ("out_order", C.POINTER(C.c_int32))]
+
+
 class stc_opts(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double),
                 ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("reserved_", C.c_int32)]
@@ -53,6 +58,8 @@ EXPORTS = {
     "stc_ctx_stats": ([C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int64)], C.c_int),
     "stc_contract": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
                       C.c_void_p, C.POINTER(stc_opts), C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "stc_contract_batch": ([C.c_void_p, C.c_int32, C.POINTER(stc_problem), C.POINTER(stc_opts), C.c_void_p,
+                            C.POINTER(C.c_void_p)], C.c_int),
     "stc_count": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
                    C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
     "stc_linearize": ([C.c_void_p, C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -167,6 +174,29 @@ def stc_contract(ctx: int, X, Y, cx: Sequence[int], cy: Sequence[int], out_order
                               C.byref(opts) if opts is not None else None, C.c_void_p(_stream_handle(stream)),
                               C.byref(r)))
     return r.value
+
+
+def stc_contract_batch(ctx: int, problems, opts: stc_opts = None, stream=None):
+    """Calls stc_contract_batch; problems is a sequence of (X, Y, cx, cy, out_order) with X and Y
+    as (shape, coords, vals) CUDA tensors. Returns the list of stc_result handles."""
+    n = len(problems)
+    keep = []
+    arr = (stc_problem * max(n, 1))()
+    for i, (X, Y, cx, cy, out_order) in enumerate(problems):
+        xa, ya = _CooArg(*X), _CooArg(*Y)
+        acx, acy = _mode_array(cx), _mode_array(cy)
+        oo = _mode_array(out_order) if out_order is not None else None
+        keep.extend([xa, ya, acx, acy, oo])
+        arr[i].X = xa.coo
+        arr[i].Y = ya.coo
+        arr[i].ncontract = len(cx)
+        arr[i].cx = C.cast(acx, C.POINTER(C.c_int32))
+        arr[i].cy = C.cast(acy, C.POINTER(C.c_int32))
+        arr[i].out_order = C.cast(oo, C.POINTER(C.c_int32)) if oo is not None else None
+    outs = (C.c_void_p * max(n, 1))()
+    check(load().stc_contract_batch(C.c_void_p(ctx), n, arr, C.byref(opts) if opts is not None else None,
+                                    C.c_void_p(_stream_handle(stream)), outs))
+    return [outs[i] for i in range(n)]
 
 
 def stc_count(ctx: int, X, Y, cx, cy, stream=None):
@@ -323,6 +353,16 @@ def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, stra
     o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor), float(group_load_factor),
                  int(accumulator), 0)
     return Result(stc_contract(ctx.handle, X, Y, cx, cy, out_order, o, stream))
+
+
+def contract_batch(problems, *, group_load_factor: float = 0.0, record_times: bool = False, stream=None,
+                   ctx: Context = None):
+    """Many independent contractions in one batch (shared passes). problems: sequence of
+    (X, Y, cx, cy) or (X, Y, cx, cy, out_order). Returns one Result per problem."""
+    ctx = ctx or default_context()
+    probs = [tuple(p) + (None,) * (5 - len(p)) for p in problems]
+    o = stc_opts(STRATEGY_GROUPED, 1 if record_times else 0, 0.0, float(group_load_factor), ACC_HASH, 0)
+    return [Result(h) for h in stc_contract_batch(ctx.handle, probs, o, stream)]
 
 
 def count(X, Y, cx, cy, *, stream=None, ctx: Context = None):

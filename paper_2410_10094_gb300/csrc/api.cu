@@ -2,6 +2,7 @@
 // order of the stages of one contraction.
 #include <algorithm>
 #include <atomic>
+#include <memory>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -21,6 +22,15 @@ struct stc_ctx {
   int sms = 0;
 };
 
+// Device memory owned by one or more results (a batch's results share one block); returned to
+// the context's pool, in the order of the stream it was made on, when the last owner goes.
+struct DeviceBlock {
+  stc_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<std::pair<void*, size_t>> parts;
+  ~DeviceBlock();
+};
+
 struct stc_result {
   stc_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
@@ -29,7 +39,7 @@ struct stc_result {
   std::vector<int64_t> shape;
   int32_t* coords = nullptr;
   double* vals = nullptr;
-  size_t bytes = 0;
+  std::shared_ptr<DeviceBlock> mem;
   stc_stats stats{};
 };
 
@@ -120,6 +130,16 @@ struct Arena {
 };
 
 bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
+
+// Moves the listed blocks from an arena into a shared block that results can own.
+std::shared_ptr<DeviceBlock> adopt(Arena& ar, stc_ctx* ctx, cudaStream_t s, std::initializer_list<void*> ptrs) {
+  auto blk = std::make_shared<DeviceBlock>();
+  blk->ctx = ctx;
+  blk->stream = s;
+  for (void* p : ptrs)
+    if (p) blk->parts.push_back({p, ar.keep(p)});
+  return blk;
+}
 
 uint64_t pow2_at_least(uint64_t v) {
   uint64_t c = 1;
@@ -532,6 +552,15 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
     STC_CUDA(cudaMemsetAsync(hh.keys, 0xff, hg.huge_slots * sizeof(u64), s));
     STC_CUDA(cudaMemsetAsync(hh.vals, 0, hg.huge_slots * sizeof(double), s));
   }
+  BatchOut hbo{};
+  hbo.FY = pl.FY;
+  hbo.out_cap = out_cap;
+  hbo.coords = r->coords;
+  hbo.vals = r->vals;
+  hbo.op = pl.op;
+  BatchOut* dbo = nullptr;
+  STC_TRY(ar.alloc(&dbo, 1));
+  STC_CUDA(cudaMemcpyAsync(dbo, &hbo, sizeof(BatchOut), cudaMemcpyHostToDevice, s));
   GroupArgs a{};
   a.goff = goff;
   a.gx = gx;
@@ -544,6 +573,8 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   a.out_cap = out_cap;
   a.nz = &pr.ctr->nz;
   a.status = &pr.ctr->status;
+  a.bout = dbo;
+  a.bnz = &pr.ctr->nz;
   if (dense_rows) {
     STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.list[0], hg.count[0], ctx->sms, s));
   } else {
@@ -555,7 +586,7 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   STC_TRY(read_counters(pr, s, h2));
   r->nnz = (int64_t)h2.nz;
   r->stats.out_capacity = out_cap;
-  r->bytes = ar.keep(r->coords) + ar.keep(r->vals);
+  r->mem = adopt(ar, ctx, s, {r->coords, r->vals});
   return STC_OK;
 }
 
@@ -569,6 +600,14 @@ int pick_strategy(const Plan& pl, const stc_coo* X, int requested) {
 }
 
 }  // namespace
+
+DeviceBlock::~DeviceBlock() {
+  DeviceGuard g(ctx->device);
+  for (auto& p : parts) {
+    cudaFreeAsync(p.first, stream);
+    ctx->held -= p.second;
+  }
+}
 
 namespace stc {
 // Lets other translation units of the library set the calling thread's last error.
@@ -737,7 +776,7 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
       delete r;  // its blocks are still owned by the arena and are released with it
       return st;
     }
-    r->bytes = ar.keep(r->coords) + ar.keep(r->vals);
+    r->mem = adopt(ar, ctx, s, {r->coords, r->vals});
     r->stats.out_capacity = out_cap;
     r->stats.table_slots = cap;
   }
@@ -745,6 +784,243 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
   r->stats.launches = take_launches();
   ctx->live_results++;
   *out = r;
+  return STC_OK;
+}
+
+
+stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* problems, const stc_opts* opts,
+                              void* stream, stc_result** outs) {
+  if (!ctx || n < 0 || (n > 0 && (!problems || !outs))) return fail(STC_ERR_INVALID_ARG, "bad batch arguments");
+  for (int32_t i = 0; i < n; i++) outs[i] = nullptr;
+  if (n == 0) return STC_OK;
+  const stc_opts o = opts ? *opts : stc_opts{};
+  const double ga = (o.group_load_factor > 0.0) ? o.group_load_factor : 0.75;
+  if (!(ga > 0.0 && ga <= 0.9)) return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", ga);
+
+  std::vector<Plan> plans(n);
+  std::vector<BatchProb> hb(n);
+  std::vector<int64_t> xrow(n + 1, 0), yrow(n + 1, 0);
+  std::vector<u64> fxoff(n + 1, 0);
+  unsigned __int128 bins = 0, fxsum = 0;
+  bool key32 = true;
+  for (int32_t i = 0; i < n; i++) {
+    const stc_problem& q = problems[i];
+    STC_TRY(make_plan(&q.X, &q.Y, q.ncontract, q.cx, q.cy, q.out_order, plans[i]));
+    const Plan& pl = plans[i];
+    if (pl.FY > 0xffffffffull) key32 = false;
+    BatchProb& b = hb[i];
+    b = BatchProb{};
+    b.xc = q.X.coords;
+    b.xv = q.X.vals;
+    b.yc = q.Y.coords;
+    b.yv = q.Y.vals;
+    b.kx = pl.kx;
+    b.ky = pl.ky;
+    b.koff = (u64)bins;
+    b.fxoff = (u64)fxsum;
+    b.FY = pl.FY;
+    bins += pl.K;
+    fxsum += pl.FX;
+    xrow[i + 1] = xrow[i] + q.X.nnz;
+    yrow[i + 1] = yrow[i] + q.Y.nnz;
+    fxoff[i + 1] = (u64)fxsum;
+    if (bins > kMaxDirectBins) return fail(STC_ERR_UNSUPPORTED, "the batch's contract key spaces exceed 2^26 bins");
+    if (fxsum >= ((unsigned __int128)1 << 63)) return fail(STC_ERR_KEY_OVERFLOW, "the batch's X free key spaces exceed 2^63");
+    if (xrow[i + 1] > STC_MAX_NNZ || yrow[i + 1] > STC_MAX_NNZ)
+      return fail(STC_ERR_INVALID_ARG, "the batch holds more than STC_MAX_NNZ entries of X or of Y");
+  }
+  const int64_t total_x = xrow[n], total_y = yrow[n];
+
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(ctx, s);
+  StageTimer tm;
+  tm.start(o.record_times != 0, s);
+  take_launches();
+
+  BatchArgs ba{};
+  ba.n = n;
+  ba.total_x = total_x;
+  ba.total_y = total_y;
+  ba.bins = (u64)bins;
+  ba.key32 = key32;
+  BatchProb* dpb = nullptr;
+  int64_t *dxrow = nullptr, *dyrow = nullptr;
+  u64* dfxoff = nullptr;
+  Counters* ctr = nullptr;
+  u64* per = nullptr;  // [3n]: products, output bound, output count per problem
+  STC_TRY(ar.alloc(&dpb, (size_t)n));
+  STC_TRY(ar.alloc(&dxrow, (size_t)n + 1));
+  STC_TRY(ar.alloc(&dyrow, (size_t)n + 1));
+  STC_TRY(ar.alloc(&dfxoff, (size_t)n + 1));
+  STC_TRY(ar.alloc(&ctr, 1));
+  STC_TRY(ar.alloc(&per, 3 * (size_t)n));
+  STC_CUDA(cudaMemcpyAsync(dpb, hb.data(), n * sizeof(BatchProb), cudaMemcpyHostToDevice, s));
+  STC_CUDA(cudaMemcpyAsync(dxrow, xrow.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  STC_CUDA(cudaMemcpyAsync(dyrow, yrow.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  STC_CUDA(cudaMemcpyAsync(dfxoff, fxoff.data(), (n + 1) * sizeof(u64), cudaMemcpyHostToDevice, s));
+  STC_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
+  STC_CUDA(cudaMemsetAsync(per, 0, 3 * n * sizeof(u64), s));
+  ba.pb = dpb;
+  ba.xrow = dxrow;
+  ba.yrow = dyrow;
+  ba.fxoff = dfxoff;
+  ba.P = &ctr->P;
+  ba.Pp = per;
+  ba.pcap = per + n;
+  ba.status = &ctr->status;
+
+  const u64 gcap = pow2_at_least(std::max<u64>(64, 2 * (u64)std::max<int64_t>(total_x, 1)));
+  STC_TRY(ar.alloc(&ba.ycnt, ba.bins));
+  STC_TRY(ar.alloc(&ba.yoff, ba.bins + 1));
+  STC_TRY(ar.alloc(&ba.ycur, ba.bins));
+  if (key32) {
+    uint32_t* k = nullptr;
+    STC_TRY(ar.alloc(&k, (size_t)total_y));
+    ba.yfk = k;
+  } else {
+    u64* k = nullptr;
+    STC_TRY(ar.alloc(&k, (size_t)total_y));
+    ba.yfk = k;
+  }
+  STC_TRY(ar.alloc(&ba.yv, (size_t)total_y));
+  STC_TRY(ar.alloc(&ba.sv.fk, (size_t)total_x));
+  STC_TRY(ar.alloc(&ba.sv.ystart, (size_t)total_x));
+  STC_TRY(ar.alloc(&ba.sv.w, (size_t)total_x));
+  STC_TRY(ar.alloc(&ba.sv.v, (size_t)total_x));
+  ba.sv.count = &ctr->ns;
+  STC_TRY(ar.alloc(&ba.idmap.keys, gcap));
+  ba.idmap.mask = gcap - 1;
+  STC_TRY(ar.alloc(&ba.gid, (size_t)total_x));
+  STC_TRY(ar.alloc(&ba.gcnt, gcap));
+  STC_TRY(ar.alloc(&ba.goff, gcap + 1));
+  STC_TRY(ar.alloc(&ba.gcur, gcap));
+  STC_TRY(ar.alloc(&ba.scan_scratch32, (size_t)std::max(scan_scratch_elems((int64_t)ba.bins),
+                                                          scan_scratch_elems((int64_t)gcap))));
+  if (ba.bins) STC_CUDA(cudaMemsetAsync(ba.ycnt, 0, ba.bins * sizeof(uint32_t), s));
+  STC_CUDA(cudaMemsetAsync(ba.idmap.keys, 0xff, gcap * sizeof(u64), s));
+  STC_CUDA(cudaMemsetAsync(ba.gcnt, 0, gcap * sizeof(uint32_t), s));
+  STC_CUDA(launch_batch_prepare(ba, ctx->sms, s));
+  tm.mark(1);
+
+  // Group X, bin the groups into table classes.
+  const bool wide = !key32;
+  const int ncls = wide ? kNumClasses64 : kNumClasses32;
+  const ClassShape* shapes = wide ? kClassShapes64 : kClassShapes32;
+  const size_t maxg = (size_t)std::max<int64_t>(total_x, 1);
+  GroupedX gx{};
+  Bins b{};
+  GroupCounters* gc = nullptr;
+  uint32_t* gprob = nullptr;
+  u64* gfk = nullptr;
+  STC_TRY(ar.alloc(&gx.ystart, maxg));
+  STC_TRY(ar.alloc(&gx.w, maxg));
+  STC_TRY(ar.alloc(&gx.v, maxg));
+  STC_TRY(ar.alloc(&gc, 1));
+  STC_TRY(ar.alloc(&gprob, gcap));
+  STC_TRY(ar.alloc(&gfk, gcap));
+  b.nclasses = ncls;
+  for (int c = 0; c < ncls; c++) {
+    b.tmax[c] = (u64)(ga * shapes[c].slots);
+    STC_TRY(ar.alloc(&b.list[c], maxg));
+  }
+  STC_TRY(ar.alloc(&b.huge_list, maxg));
+  STC_TRY(ar.alloc(&b.huge_off, maxg));
+  STC_TRY(ar.alloc(&b.huge_cap, maxg));
+  b.count = gc->count;
+  b.huge_slots = &gc->huge_slots;
+  b.out_cap = &gc->out_cap;
+  b.status = &ctr->status;
+  STC_CUDA(cudaMemsetAsync(gc, 0, sizeof(GroupCounters), s));
+  STC_CUDA(launch_batch_group(ba, gx, b, gprob, gfk, ctx->sms, s));
+  tm.mark(2);
+
+  Counters h{};
+  GroupCounters hg{};
+  std::vector<u64> hper(3 * (size_t)n);
+  STC_CUDA(cudaMemcpyAsync(&hg, gc, sizeof(GroupCounters), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaMemcpyAsync(hper.data(), per, 2 * n * sizeof(u64), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaStreamSynchronize(s));
+  STC_TRY(status_word(h.status));
+  tm.mark(3);
+
+  // One output allocation: every problem's values, then every problem's coordinates.
+  std::vector<u64> voff(n + 1, 0), coff(n + 1, 0);
+  for (int32_t i = 0; i < n; i++) {
+    voff[i + 1] = voff[i] + hper[n + i];
+    coff[i + 1] = coff[i] + hper[n + i] * (u64)plans[i].oz;
+  }
+  double* vals = nullptr;
+  int32_t* coords = nullptr;
+  STC_TRY(ar.alloc(&vals, voff[n]));
+  STC_TRY(ar.alloc(&coords, coff[n]));
+  std::vector<BatchOut> hbo(n);
+  for (int32_t i = 0; i < n; i++) {
+    hbo[i].FY = plans[i].FY;
+    hbo[i].out_cap = hper[n + i];
+    hbo[i].coords = coords ? coords + coff[i] : nullptr;
+    hbo[i].vals = vals ? vals + voff[i] : nullptr;
+    hbo[i].op = plans[i].op;
+  }
+  BatchOut* dbo = nullptr;
+  STC_TRY(ar.alloc(&dbo, (size_t)n));
+  STC_CUDA(cudaMemcpyAsync(dbo, hbo.data(), n * sizeof(BatchOut), cudaMemcpyHostToDevice, s));
+  HugeGroups hh{};
+  hh.count = hg.count[kMaxClasses];
+  hh.list = b.huge_list;
+  hh.off = b.huge_off;
+  hh.cap = b.huge_cap;
+  if (hh.count) {
+    STC_TRY(ar.alloc(&hh.keys, hg.huge_slots));
+    STC_TRY(ar.alloc(&hh.vals, hg.huge_slots));
+    STC_CUDA(cudaMemsetAsync(hh.keys, 0xff, hg.huge_slots * sizeof(u64), s));
+  }
+  GroupArgs a{};
+  a.goff = ba.goff;
+  a.gx = gx;
+  a.yfk = ba.yfk;
+  a.yv = ba.yv;
+  a.status = &ctr->status;
+  a.nz = &ctr->nz;
+  a.bout = dbo;
+  a.bnz = per + 2 * n;
+  a.gprob = gprob;
+  a.gfk = gfk;
+  if (h.P > 0) {
+    STC_CUDA(launch_group_classes(a, wide, b, hg.count, ctx->sms, s));
+    STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
+  }
+  tm.mark(4);
+  STC_CUDA(cudaMemcpyAsync(hper.data() + 2 * n, per + 2 * n, n * sizeof(u64), cudaMemcpyDeviceToHost, s));
+  Counters h2{};
+  STC_CUDA(cudaMemcpyAsync(&h2, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaStreamSynchronize(s));
+  STC_TRY(status_word(h2.status));
+
+  auto blk = adopt(ar, ctx, s, {vals, coords});
+  stc_stats common{};
+  tm.collect(common);
+  common.launches = take_launches();
+  common.strategy = STC_STRATEGY_GROUPED;
+  common.accumulator = STC_ACC_HASH;
+  for (int32_t i = 0; i < n; i++) {
+    stc_result* r = new stc_result;
+    r->ctx = ctx;
+    r->stream = s;
+    r->order = plans[i].oz;
+    r->shape = plans[i].zshape;
+    r->nnz = (int64_t)hper[2 * n + i];
+    r->coords = hbo[i].coords;
+    r->vals = hbo[i].vals;
+    r->mem = blk;
+    r->stats = common;
+    r->stats.products = hper[i];
+    r->stats.out_capacity = hper[n + i];
+    ctx->live_results++;
+    outs[i] = r;
+  }
   return STC_OK;
 }
 
@@ -862,10 +1138,6 @@ stc_status stc_result_stats(const stc_result* r, stc_stats* stats) {
 
 stc_status stc_result_free(stc_result* r) {
   if (!r) return STC_OK;
-  DeviceGuard g(r->ctx->device);
-  if (r->coords) cudaFreeAsync(r->coords, r->stream);
-  if (r->vals) cudaFreeAsync(r->vals, r->stream);
-  r->ctx->held -= r->bytes;
   r->ctx->live_results--;
   delete r;
   return STC_OK;

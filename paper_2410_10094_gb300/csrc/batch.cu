@@ -1,0 +1,323 @@
+// Batches of independent contractions that share every pass: the inputs of all problems are
+// processed as one flattened row space (each row finds its problem by binary search over the
+// row offsets), Y is grouped over the concatenation of all problems' contract-key bins, and
+// X's survivors are grouped by (problem, X free key). Because the problems' X free key spaces
+// together are far too large to count directly, each distinct (problem, free key) pair gets a
+// small number through a probing table, in order of first sight (Section 4.1.2, Fig. 6).
+// The per-group accumulation then runs in the same class kernels as a single contraction.
+#include "launch.h"
+
+namespace stc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n, int sms, int per_sm = 8) {
+  const int64_t want = (n + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)sms * per_sm;
+  return (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+// The problem owning flattened row r: the largest p with off[p] <= r (off has n + 1 entries).
+__device__ __forceinline__ int row_problem(const int64_t* __restrict__ off, int n, int64_t r) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int key_problem(const u64* __restrict__ off, int n, u64 key) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= key) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Contract and free keys of row i of a tensor whose order is only known at run time.
+__device__ __forceinline__ bool row_keys_any(const int32_t* __restrict__ coords, int64_t i, const KeyPlan& p,
+                                             uint64_t& ck, uint64_t& fk) {
+  bool ok = true;
+  ck = 0;
+  fk = 0;
+  for (int j = 0; j < p.order; j++) {
+    const int32_t c = __ldg(coords + i * p.order + j);
+    ok &= (c >= 0) & ((int64_t)c < p.size[j]);
+    ck += (uint64_t)(uint32_t)c * p.cstride[j];
+    fk += (uint64_t)(uint32_t)c * p.fstride[j];
+  }
+  return ok;
+}
+
+__global__ void __launch_bounds__(kThreads) y_count_batch_kernel(const BatchProb* __restrict__ pb,
+                                                                 const int64_t* __restrict__ yrow, int n,
+                                                                 int64_t total, uint32_t* __restrict__ cnt,
+                                                                 uint32_t* status) {
+  for (int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x; r < total; r += (int64_t)gridDim.x * kThreads) {
+    const int p = row_problem(yrow, n, r);
+    const BatchProb& q = pb[p];
+    uint64_t ck, fk;
+    if (!row_keys_any(q.yc, r - yrow[p], q.ky, ck, fk)) {
+      atomicOr(status, kStatCoordRange);
+      continue;
+    }
+    atomicAdd(cnt + q.koff + ck, 1u);
+  }
+}
+
+template <typename YK>
+__global__ void __launch_bounds__(kThreads) y_scatter_batch_kernel(const BatchProb* __restrict__ pb,
+                                                                   const int64_t* __restrict__ yrow, int n,
+                                                                   int64_t total, uint32_t* __restrict__ cursor,
+                                                                   YK* __restrict__ yfk, double* __restrict__ yv) {
+  for (int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x; r < total; r += (int64_t)gridDim.x * kThreads) {
+    const int p = row_problem(yrow, n, r);
+    const BatchProb& q = pb[p];
+    const int64_t i = r - yrow[p];
+    uint64_t ck, fk;
+    if (!row_keys_any(q.yc, i, q.ky, ck, fk)) continue;
+    const uint32_t pos = atomicAdd(cursor + q.koff + ck, 1u);
+    yfk[pos] = (YK)fk;
+    yv[pos] = __ldg(q.yv + i);
+  }
+}
+
+// Survivors of all problems: their combined group key fxoff[p] + fX, Y run, value; the
+// product count per problem and in total.
+__global__ void __launch_bounds__(kThreads) x_survey_batch_kernel(const BatchProb* __restrict__ pb,
+                                                                  const int64_t* __restrict__ xrow, int n,
+                                                                  int64_t total, const uint32_t* __restrict__ yoff,
+                                                                  Survivors sv, u64* __restrict__ P,
+                                                                  u64* __restrict__ Pp, uint32_t* status) {
+  for (int64_t base = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u); base < total;
+       base += (int64_t)gridDim.x * kThreads) {
+    const int64_t r = base + lane_id();
+    bool live = false;
+    u64 gkey = 0;
+    uint32_t lo = 0, w = 0;
+    int p = 0;
+    if (r < total) {
+      p = row_problem(xrow, n, r);
+      const BatchProb& q = pb[p];
+      uint64_t ck, fk;
+      if (!row_keys_any(q.xc, r - xrow[p], q.kx, ck, fk)) {
+        atomicOr(status, kStatCoordRange);
+      } else {
+        lo = __ldg(yoff + q.koff + ck);
+        w = __ldg(yoff + q.koff + ck + 1) - lo;
+        live = w > 0;
+        gkey = q.fxoff + fk;
+      }
+    }
+    const unsigned pos = warp_reserve<unsigned>(live, sv.count);
+    if (live) {
+      sv.fk[pos] = gkey;
+      sv.ystart[pos] = lo;
+      sv.w[pos] = w;
+      sv.v[pos] = __ldg(pb[p].xv + (r - xrow[p]));
+    }
+    // Products per problem: rows are in problem order, so a warp spans few problems; one
+    // atomic per (warp, problem).
+    unsigned todo = __ballot_sync(0xffffffffu, live);
+    while (todo) {
+      const int leader = __ffs(todo) - 1;
+      const int pl = __shfl_sync(0xffffffffu, p, leader);
+      const bool mine = live && p == pl;
+      u64 sum = mine ? (u64)w : 0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if ((int)lane_id() == leader) {
+        atomicAdd(Pp + pl, sum);
+        atomicAdd(P, sum);
+      }
+      todo &= ~__ballot_sync(0xffffffffu, mine);
+    }
+  }
+}
+
+// The small-number map (Section 4.1.2) on the GPU: every distinct group key claims a slot of
+// a probing table, and a group's number is its slot. Numbers are then sparse in [0, table
+// size) rather than dense in order of first sight (which would serialise on one counter);
+// empty slots are empty groups and are skipped.
+__global__ void __launch_bounds__(kThreads) idmap_insert_kernel(Survivors sv, IdMap m, uint32_t* status) {
+  const int64_t ns = (int64_t)*sv.count;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < ns; i += (int64_t)gridDim.x * kThreads) {
+    const u64 key = sv.fk[i];
+    u64 slot = mix64(key) & m.mask;
+    bool done = false;
+    for (u64 probe = 0; probe <= m.mask; probe++) {
+      u64 cur = __ldcg(m.keys + slot);
+      if (cur == kEmpty64) {
+        const u64 prev = atomicCAS(m.keys + slot, kEmpty64, key);
+        cur = (prev == kEmpty64) ? key : prev;
+      }
+      if (cur == key) {
+        done = true;
+        break;
+      }
+      slot = (slot + 1) & m.mask;
+    }
+    if (!done) atomicOr(status, kStatTableFull);
+  }
+}
+
+// Second pass (a separate launch, so the table is complete): each survivor finds its key's
+// slot, which is its group number, and is counted in its group.
+__global__ void __launch_bounds__(kThreads) idmap_lookup_kernel(Survivors sv, IdMap m, uint32_t* __restrict__ gid,
+                                                                uint32_t* __restrict__ gcnt) {
+  const int64_t ns = (int64_t)*sv.count;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < ns; i += (int64_t)gridDim.x * kThreads) {
+    const u64 key = sv.fk[i];
+    u64 slot = mix64(key) & m.mask;
+    for (u64 probe = 0; probe <= m.mask; probe++) {
+      if (__ldcg(m.keys + slot) == key) {
+        gid[i] = (uint32_t)slot;
+        atomicAdd(gcnt + slot, 1u);
+        break;
+      }
+      slot = (slot + 1) & m.mask;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) batch_group_scatter_kernel(Survivors sv, const uint32_t* __restrict__ gid,
+                                                                       uint32_t* __restrict__ gcur, GroupedX gx) {
+  const int64_t ns = (int64_t)*sv.count;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < ns; i += (int64_t)gridDim.x * kThreads) {
+    const uint32_t pos = atomicAdd(gcur + gid[i], 1u);
+    gx.ystart[pos] = sv.ystart[i];
+    gx.w[pos] = sv.w[i];
+    gx.v[pos] = sv.v[i];
+  }
+}
+
+// One thread per group: its bound (sum of its entries' run lengths; groups here are mostly a
+// single X entry), its problem and X free key, its class. Appends to the class lists are
+// aggregated per warp; each problem's output bound sums min(B_g, F_Y) over its groups.
+__global__ void __launch_bounds__(kThreads) bin_batch_kernel(u64 G, const uint32_t* __restrict__ goff,
+                                                             const uint32_t* __restrict__ gw,
+                                                             const u64* __restrict__ gkey,
+                                                             const u64* __restrict__ fxoff, int n,
+                                                             const BatchProb* __restrict__ pb, Bins b,
+                                                             uint32_t* __restrict__ gprob, u64* __restrict__ gfk,
+                                                             u64* __restrict__ pcap) {
+  __shared__ u64 s_cap[kThreads / 32];
+  const unsigned lane = lane_id();
+  u64 my_cap = 0;
+  for (u64 base = (u64)blockIdx.x * kThreads + (threadIdx.x & ~31u); base < G; base += (u64)gridDim.x * kThreads) {
+    const u64 g = base + lane;
+    int cls = -1;
+    int p = -1;
+    u64 t = 0;
+    if (g < G && goff[g] != goff[g + 1]) {
+      u64 bnd = 0;
+      for (uint32_t i = goff[g]; i < goff[g + 1]; i++) bnd += gw[i];
+      const u64 key = gkey[g];
+      p = key_problem(fxoff, n, key);
+      gprob[g] = (uint32_t)p;
+      gfk[g] = key - fxoff[p];
+      const u64 FY = pb[p].FY;
+      t = bnd < FY ? bnd : FY;
+      my_cap += t;
+      cls = 0;
+      while (cls < b.nclasses && t > b.tmax[cls]) cls++;
+      if (cls == b.nclasses && t > (1ull << 30)) {
+        atomicOr(b.status, kStatTooLarge);
+        cls = -1;
+      }
+    }
+    for (int c = 0; c <= b.nclasses; c++) {
+      const bool in = cls == c;
+      const uint32_t pos = warp_reserve<uint32_t>(in, b.count + (c < b.nclasses ? c : kMaxClasses));
+      if (in) {
+        if (c < b.nclasses) {
+          b.list[c][pos] = (uint32_t)g;
+        } else {
+          u64 cap = 64;
+          while (cap < 2 * t) cap <<= 1;
+          b.huge_list[pos] = (uint32_t)g;
+          b.huge_off[pos] = atomicAdd(b.huge_slots, cap);
+          b.huge_cap[pos] = cap;
+        }
+      }
+    }
+    // Output bound per problem, one atomic per (warp, problem).
+    unsigned todo = __ballot_sync(0xffffffffu, p >= 0);
+    while (todo) {
+      const int leader = __ffs(todo) - 1;
+      const int pl = __shfl_sync(0xffffffffu, p, leader);
+      const bool mine = p == pl;
+      u64 sum = mine ? t : 0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if ((int)lane == leader) atomicAdd(pcap + pl, sum);
+      todo &= ~__ballot_sync(0xffffffffu, mine);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_cap += __shfl_down_sync(0xffffffffu, my_cap, o);
+  if (lane == 0) s_cap[threadIdx.x >> 5] = my_cap;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 tot = 0;
+    for (int w = 0; w < kThreads / 32; w++) tot += s_cap[w];
+    if (tot) atomicAdd(b.out_cap, tot);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_batch_prepare(const BatchArgs& ba, int sms, cudaStream_t s) {
+  if (ba.total_y > 0) {
+    y_count_batch_kernel<<<grid_for(ba.total_y, sms), kThreads, 0, s>>>(ba.pb, ba.yrow, ba.n, ba.total_y, ba.ycnt,
+                                                                       ba.status);
+    note_launch();
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = scan_u32(ba.ycnt, ba.yoff, (int64_t)ba.bins, ba.scan_scratch32, s);
+  if (e != cudaSuccess) return e;
+  if (ba.bins) {
+    e = cudaMemcpyAsync(ba.ycur, ba.yoff, ba.bins * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (ba.total_y > 0) {
+    if (ba.key32)
+      y_scatter_batch_kernel<uint32_t><<<grid_for(ba.total_y, sms), kThreads, 0, s>>>(
+          ba.pb, ba.yrow, ba.n, ba.total_y, ba.ycur, static_cast<uint32_t*>(ba.yfk), ba.yv);
+    else
+      y_scatter_batch_kernel<u64><<<grid_for(ba.total_y, sms), kThreads, 0, s>>>(
+          ba.pb, ba.yrow, ba.n, ba.total_y, ba.ycur, static_cast<u64*>(ba.yfk), ba.yv);
+    note_launch();
+  }
+  if (ba.total_x > 0) {
+    x_survey_batch_kernel<<<grid_for(ba.total_x, sms), kThreads, 0, s>>>(ba.pb, ba.xrow, ba.n, ba.total_x, ba.yoff,
+                                                                        ba.sv, ba.P, ba.Pp, ba.status);
+    note_launch();
+    idmap_insert_kernel<<<grid_for(ba.total_x, sms), kThreads, 0, s>>>(ba.sv, ba.idmap, ba.status);
+    idmap_lookup_kernel<<<grid_for(ba.total_x, sms), kThreads, 0, s>>>(ba.sv, ba.idmap, ba.gid, ba.gcnt);
+    note_launch(2);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_group(const BatchArgs& ba, GroupedX gx, const Bins& b, uint32_t* gprob, u64* gfk,
+                               int sms, cudaStream_t s) {
+  const int64_t G = (int64_t)ba.idmap.mask + 1;
+  cudaError_t e = scan_u32(ba.gcnt, ba.goff, G, ba.scan_scratch32, s);
+  if (e != cudaSuccess) return e;
+  if (ba.total_x <= 0) return cudaSuccess;
+  e = cudaMemcpyAsync(ba.gcur, ba.goff, (size_t)G * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  batch_group_scatter_kernel<<<grid_for(ba.total_x, sms), kThreads, 0, s>>>(ba.sv, ba.gid, ba.gcur, gx);
+  bin_batch_kernel<<<grid_for(G, sms), kThreads, 0, s>>>((u64)G, ba.goff, gx.w, ba.idmap.keys, ba.fxoff, ba.n, ba.pb,
+                                                         b, gprob, gfk, ba.pcap);
+  note_launch(2);
+  return cudaGetLastError();
+}
+
+}  // namespace stc

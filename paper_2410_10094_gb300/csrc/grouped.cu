@@ -92,6 +92,23 @@ __global__ void __launch_bounds__(kThreads) bin_groups_kernel(u64 FX, const uint
 
 // ---------------------------------------------------------------- accumulation
 
+// Resolves group g's output target and reserves n output positions (thread 0 only). The
+// problem's descriptor is read from global memory word by word.
+__device__ __forceinline__ void resolve_target(const GroupArgs& a, u64 g, unsigned n, OutTarget& t) {
+  const uint32_t p = a.gprob ? a.gprob[g] : 0u;
+  const BatchOut* bo = a.bout + p;
+  const u64 FY = bo->FY;
+  t.zrow = (a.gfk ? a.gfk[g] : g) * FY;
+  t.base = n ? atomicAdd(a.bnz + p, (u64)n) : 0;
+  t.cap = bo->out_cap;
+  t.coords = bo->coords;
+  t.vals = bo->vals;
+  const u64* src = reinterpret_cast<const u64*>(&bo->op);
+  u64* dst = reinterpret_cast<u64*>(&t.op);
+#pragma unroll 1
+  for (unsigned i = 0; i < sizeof(OutPlan) / sizeof(u64); i++) dst[i] = src[i];
+}
+
 // Shared-memory staging of one chunk of a group's X entries: the exclusive prefix of their
 // run lengths (products), the first slot of each run, and the X values.
 template <int THREADS>
@@ -302,18 +319,17 @@ __device__ __forceinline__ void expand_group_smem(const GroupArgs& a, Chunk<THRE
 // stored by lane k % 32 (consecutive lanes, consecutive positions: coalesced streaming stores).
 template <int SLOTS, int THREADS, typename KT>
 __device__ __forceinline__ void write_group_smem(const GroupArgs& a, u64 g, KT* keys, const double* vals,
-                                                 unsigned* claims, unsigned* cursor, u64* gbase) {
+                                                 unsigned* claims, unsigned* cursor, OutTarget& tg) {
   constexpr int B = Bucket<KT>::N;
   constexpr uint32_t NB = SLOTS / B;
   const unsigned lane = lane_id();
   if (threadIdx.x == 0) {
-    const unsigned n = *claims;
-    *gbase = n ? atomicAdd(a.nz, (u64)n) : 0;
+    resolve_target(a, g, *claims, tg);
     *cursor = 0;
   }
   __syncthreads();
-  const u64 base = *gbase;
-  const u64 zrow = g * a.FY;
+  const u64 base = tg.base;
+  const u64 zrow = tg.zrow;
   const uint64_t pol = policy_evict_first();
   for (uint32_t b0 = (threadIdx.x & ~31u); b0 < NB; b0 += THREADS) {
     const uint32_t b = b0 + lane;
@@ -353,8 +369,8 @@ __device__ __forceinline__ void write_group_smem(const GroupArgs& a, u64 g, KT* 
         for (unsigned t = k - (src_incl - src_cnt); t > 0; t--) m &= m - 1;
         const uint32_t slot = (b0 + src) * B + (uint32_t)(__ffs(m) - 1);
         const u64 pos = base + off + k;
-        if (pos < a.out_cap)
-          store_output(a.coords, a.vals, pos, zrow + (u64)keys[slot], vals[slot], a.op, pol);
+        if (pos < tg.cap)
+          store_output(tg.coords, tg.vals, pos, zrow + (u64)keys[slot], vals[slot], tg.op, pol);
         else
           atomicOr(a.status, kStatOutOverflow);
       }
@@ -381,18 +397,15 @@ __global__ void __launch_bounds__(THREADS) group_smem_kernel(GroupArgs a, const 
   Chunk<THREADS>& c = *reinterpret_cast<Chunk<THREADS>*>(smem + SLOTS * (sizeof(double) + sizeof(KT)));
   __shared__ u64 warp_tot[THREADS / 32];
   __shared__ unsigned claims, cursor;
-  __shared__ u64 gbase;
-  for (int i = threadIdx.x; i < SLOTS; i += THREADS) {
-    keys[i] = empty_key<KT>();
-    vals[i] = 0.0;
-  }
+  __shared__ OutTarget tg;
+  for (int i = threadIdx.x; i < SLOTS; i += THREADS) keys[i] = empty_key<KT>();
   if (threadIdx.x == 0) claims = 0;
   __syncthreads();
   for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
     const uint32_t g = list[k];
     expand_group_smem<SLOTS, THREADS, KT, sizeof(KT) == 4 ? 8 : 4>(a, c, warp_tot, a.goff[g], a.goff[g + 1], keys,
                                                                    vals, &claims);
-    write_group_smem<SLOTS, THREADS, KT>(a, g, keys, vals, &claims, &cursor, &gbase);
+    write_group_smem<SLOTS, THREADS, KT>(a, g, keys, vals, &claims, &cursor, tg);
   }
 }
 
@@ -442,7 +455,7 @@ __device__ __forceinline__ void expand_group_global(const GroupArgs& a, Chunk<TH
 template <int THREADS>
 __device__ __forceinline__ void write_group_global(const GroupArgs& a, u64 g, const u64* keys,
                                                    const double* vals, uint32_t slots, uint32_t* warp_cnt,
-                                                   u64* warp_base) {
+                                                   u64* warp_base, OutTarget& tg) {
   constexpr int NW = THREADS / 32;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t per = (slots + NW - 1) / NW;
@@ -457,7 +470,8 @@ __device__ __forceinline__ void write_group_global(const GroupArgs& a, u64 g, co
   if (threadIdx.x == 0) {
     u64 tot = 0;
     for (int k = 0; k < NW; k++) tot += warp_cnt[k];
-    u64 base = tot ? atomicAdd(a.nz, tot) : 0;
+    resolve_target(a, g, (unsigned)tot, tg);
+    u64 base = tg.base;
     for (int k = 0; k < NW; k++) {
       warp_base[k] = base;
       base += warp_cnt[k];
@@ -465,7 +479,7 @@ __device__ __forceinline__ void write_group_global(const GroupArgs& a, u64 g, co
   }
   __syncthreads();
   u64 run = warp_base[warp];
-  const u64 zrow = g * a.FY;
+  const u64 zrow = tg.zrow;
   for (uint32_t i0 = s0; i0 < s1; i0 += 32) {
     const uint32_t i = i0 + lane;
     const u64 k = (i < s1) ? keys[i] : kEmpty64;
@@ -473,9 +487,9 @@ __device__ __forceinline__ void write_group_global(const GroupArgs& a, u64 g, co
     const unsigned m = __ballot_sync(0xffffffffu, live);
     if (live) {
       const u64 pos = run + __popc(m & lanemask_lt());
-      if (pos < a.out_cap) {
-        store_coords(zrow + k, a.op, a.coords + pos * (u64)a.op.order);
-        a.vals[pos] = vals[i];
+      if (pos < tg.cap) {
+        store_coords(zrow + k, tg.op, tg.coords + pos * (u64)tg.op.order);
+        tg.vals[pos] = vals[i];
       } else {
         atomicOr(a.status, kStatOutOverflow);
       }
@@ -493,13 +507,14 @@ __global__ void __launch_bounds__(THREADS) group_global_kernel(GroupArgs a, Huge
   __shared__ u64 warp_tot[THREADS / 32];
   __shared__ uint32_t warp_cnt[THREADS / 32];
   __shared__ u64 warp_base[THREADS / 32];
+  __shared__ OutTarget tg;
   for (uint32_t k = blockIdx.x; k < h.count; k += gridDim.x) {
     const uint32_t g = h.list[k];
     u64* keys = h.keys + h.off[k];
     double* vals = h.vals + h.off[k];
     const uint32_t cap = (uint32_t)h.cap[k];
     expand_group_global<THREADS, YK>(a, c, warp_tot, a.goff[g], a.goff[g + 1], keys, vals, cap - 1);
-    write_group_global<THREADS>(a, g, keys, vals, cap, warp_cnt, warp_base);
+    write_group_global<THREADS>(a, g, keys, vals, cap, warp_cnt, warp_base, tg);
   }
 }
 
@@ -706,6 +721,174 @@ __global__ void __launch_bounds__(THREADS) group_dense_kernel(GroupArgs a, const
   }
 }
 
+
+// ---- small groups: one warp per group, each warp with its own table (group-per-warp
+// granularity). Everything a group needs stays inside its warp, so warp-level
+// synchronisation replaces block barriers and warps progress independently.
+
+template <int SLOTS, typename KT>
+struct alignas(16) WarpSlice {
+  double vals[SLOTS];
+  KT keys[SLOTS];
+  u64 pre[33];
+  uint32_t ystart[32];
+  double v[32];
+  OutTarget tg;
+};
+
+static_assert(sizeof(WarpSlice<256, uint32_t>) % 16 == 0 && sizeof(WarpSlice<1024, uint32_t>) % 16 == 0 &&
+                  sizeof(WarpSlice<256, u64>) % 16 == 0 && sizeof(WarpSlice<1024, u64>) % 16 == 0,
+              "per-warp slices must keep the key buckets 16-byte aligned");
+
+template <int SLOTS, typename KT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) group_warp_kernel(GroupArgs a, const uint32_t* __restrict__ list,
+                                                                uint32_t count) {
+  constexpr int B = Bucket<KT>::N;
+  constexpr uint32_t NB = SLOTS / B;
+  constexpr int D = 4;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  WarpSlice<SLOTS, KT>& ws = reinterpret_cast<WarpSlice<SLOTS, KT>*>(smem)[warp];
+  for (uint32_t i = lane; i < SLOTS; i += 32) ws.keys[i] = empty_key<KT>();
+  __syncwarp();
+  const uint64_t keep = policy_evict_last();
+  const uint64_t pol = policy_evict_first();
+  for (uint32_t k = blockIdx.x * WARPS + warp; k < count; k += gridDim.x * WARPS) {
+    const uint32_t g = list[k];
+    const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
+    unsigned claims = 0;
+    for (uint32_t c0 = x0; c0 < x1; c0 += 32) {
+      const uint32_t n = (x1 - c0 < 32u) ? x1 - c0 : 32u;
+      u64 w = 0;
+      if (lane < n) {
+        w = a.gx.w[c0 + lane];
+        ws.ystart[lane] = a.gx.ystart[c0 + lane];
+        ws.v[lane] = a.gx.v[c0 + lane];
+      }
+      u64 incl = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      ws.pre[lane] = incl - w;
+      const u64 total = __shfl_sync(0xffffffffu, incl, 31);
+      if (lane == 0) ws.pre[32] = total;
+      __syncwarp();
+      // pre[n] must bound the walk: entries at or past n have w = 0, so pre[n..32] = total.
+      uint32_t own = 0;
+      for (u64 base = 0; base < total; base += 32 * D) {
+        KT key[D];
+        double prod[D];
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          const u64 p = base + (u64)u * 32 + lane;
+          uint32_t kk = own;
+          key[u] = empty_key<KT>();
+          if (p < total) {
+            while (ws.pre[kk + 1] <= p) kk++;
+            const u64 j = (u64)ws.ystart[kk] + (p - ws.pre[kk]);
+            if constexpr (sizeof(KT) == 4)
+              key[u] = (KT)ld_keep_u32(static_cast<const uint32_t*>(a.yfk) + j, keep);
+            else
+              key[u] = (KT)ld_keep_u64(static_cast<const uint64_t*>(a.yfk) + j, keep);
+            prod[u] = __dmul_rn(ws.v[kk], ld_keep_f64(a.yv + j, keep));
+          }
+          own = __shfl_sync(0xffffffffu, kk, 31);
+        }
+        int later[D];
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          later[u] = -1;
+          bool claimed = false;
+          if (key[u] != empty_key<KT>()) {
+            const int slot = bucket_claim<KT, SLOTS>(ws.keys, key[u], &claimed);
+            if (slot < 0) atomicOr(a.status, kStatTableFull);
+            else if (claimed) ws.vals[slot] = prod[u];
+            else later[u] = slot;
+          }
+          claims += __popc(__ballot_sync(0xffffffffu, claimed));
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < D; u++)
+          if (later[u] >= 0) atomicAdd(ws.vals + later[u], prod[u]);
+        __syncwarp();
+      }
+    }
+    // Write the group's occupied slots, consecutive lanes storing consecutive outputs.
+    if (lane == 0) resolve_target(a, g, claims, ws.tg);
+    __syncwarp();
+    unsigned off = 0;
+    for (uint32_t b0 = 0; b0 < NB; b0 += 32) {
+      const uint32_t b = b0 + lane;
+      unsigned live = 0;
+      if (b < NB) {
+        const Bucket<KT> bk = load_bucket<KT>(ws.keys, b);
+#pragma unroll
+        for (int i = 0; i < B; i++) live |= (bk.k[i] != empty_key<KT>()) ? (1u << i) : 0u;
+      }
+      const unsigned cnt = __popc(live);
+      unsigned incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      const unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
+      for (unsigned k0 = 0; k0 < tot; k0 += 32) {
+        const unsigned kq = k0 + lane;
+        unsigned src = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const unsigned probe = __shfl_sync(0xffffffffu, incl, src + step - 1);
+          if (probe <= kq) src += step;
+        }
+        const unsigned src_incl = __shfl_sync(0xffffffffu, incl, src);
+        const unsigned src_live = __shfl_sync(0xffffffffu, live, src);
+        if (kq < tot) {
+          unsigned m = src_live;
+          for (unsigned t = kq - (src_incl - __popc(src_live)); t > 0; t--) m &= m - 1;
+          const uint32_t slot = (b0 + src) * B + (uint32_t)(__ffs(m) - 1);
+          const u64 pos = ws.tg.base + off + kq;
+          if (pos < ws.tg.cap)
+            store_output(ws.tg.coords, ws.tg.vals, pos, ws.tg.zrow + (u64)ws.keys[slot], ws.vals[slot], ws.tg.op,
+                         pol);
+          else
+            atomicOr(a.status, kStatOutOverflow);
+        }
+      }
+      off += tot;
+      __syncwarp();
+      if (live) {
+        KT* kb = ws.keys + b * B;
+#pragma unroll
+        for (int i = 0; i < B; i++) kb[i] = empty_key<KT>();
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int SLOTS, typename KT>
+cudaError_t launch_warp_class(const GroupArgs& a, const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  constexpr int WARPS = 8;
+  const size_t smem = WARPS * sizeof(WarpSlice<SLOTS, KT>);
+  auto kern = group_warp_kernel<SLOTS, KT, WARPS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const uint32_t need = (count + WARPS - 1) / WARPS;
+  const uint32_t cap = (uint32_t)(sms * per_sm);
+  kern<<<need < cap ? need : cap, WARPS * 32, smem, s>>>(a, list, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <int SLOTS, int THREADS, typename KT>
 cudaError_t launch_class(const GroupArgs& a, const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
@@ -725,10 +908,10 @@ cudaError_t launch_class(const GroupArgs& a, const uint32_t* list, uint32_t coun
 
 }  // namespace
 
-// Table classes: slots and threads per CTA. The binning threshold of class c is
-// tmax[c] = floor(alpha_c * slots_c) (set by the host; default alpha 0.5).
-const ClassShape kClassShapes32[] = {{256, 64}, {1024, 128}, {4096, 256}, {8192, 512}, {16384, 1024}};
-const ClassShape kClassShapes64[] = {{256, 64}, {1024, 128}, {4096, 256}, {8192, 512}};
+// Table classes: slots and threads per group (32 = one warp per group). The binning threshold
+// of class c is tmax[c] = floor(alpha * slots_c), alpha set by the host (default 0.75).
+const ClassShape kClassShapes32[] = {{256, 32}, {1024, 32}, {4096, 256}, {8192, 512}, {16384, 1024}};
+const ClassShape kClassShapes64[] = {{256, 32}, {1024, 32}, {4096, 256}, {8192, 512}};
 const int kNumClasses32 = 5;
 const int kNumClasses64 = 4;
 
@@ -752,14 +935,14 @@ cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins&
                                  int sms, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (!wide_keys) {
-    if ((e = launch_class<256, 64, uint32_t>(a, b.list[0], counts[0], sms, s))) return e;
-    if ((e = launch_class<1024, 128, uint32_t>(a, b.list[1], counts[1], sms, s))) return e;
+    if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], counts[0], sms, s))) return e;
+    if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], counts[1], sms, s))) return e;
     if ((e = launch_class<4096, 256, uint32_t>(a, b.list[2], counts[2], sms, s))) return e;
     if ((e = launch_class<8192, 512, uint32_t>(a, b.list[3], counts[3], sms, s))) return e;
     if ((e = launch_class<16384, 1024, uint32_t>(a, b.list[4], counts[4], sms, s))) return e;
   } else {
-    if ((e = launch_class<256, 64, u64>(a, b.list[0], counts[0], sms, s))) return e;
-    if ((e = launch_class<1024, 128, u64>(a, b.list[1], counts[1], sms, s))) return e;
+    if ((e = launch_warp_class<256, u64>(a, b.list[0], counts[0], sms, s))) return e;
+    if ((e = launch_warp_class<1024, u64>(a, b.list[1], counts[1], sms, s))) return e;
     if ((e = launch_class<4096, 256, u64>(a, b.list[2], counts[2], sms, s))) return e;
     if ((e = launch_class<8192, 512, u64>(a, b.list[3], counts[3], sms, s))) return e;
   }

@@ -113,6 +113,16 @@ struct Bins {
   uint32_t* status;
 };
 
+// Output region of one problem of a batch.
+struct BatchOut {
+  u64 FY;
+  u64 out_cap;
+  int32_t* coords;
+  double* vals;
+  OutPlan op;  // a whole number of 8-byte words (copied word by word)
+};
+static_assert(sizeof(OutPlan) % 8 == 0, "OutPlan must be a whole number of 8-byte words");
+
 struct GroupArgs {
   const uint32_t* goff;
   GroupedX gx;
@@ -125,6 +135,23 @@ struct GroupArgs {
   u64 out_cap;
   u64* nz;
   uint32_t* status;
+  // Output regions and counters, one per problem (one entry for a single contraction). For
+  // batches also the problem of each group and the group's X free key within that problem
+  // (both null for a single contraction, where the group index is the X free key).
+  const BatchOut* bout;
+  u64* bnz;
+  const uint32_t* gprob;
+  const u64* gfk;
+};
+
+// Where one group's outputs go, resolved once per group.
+struct OutTarget {
+  u64 zrow;   // output key of the group's row: fX * F_Y
+  u64 base;   // first output position reserved for the group
+  u64 cap;    // output capacity of the group's problem
+  int32_t* coords;
+  double* vals;
+  OutPlan op;
 };
 
 struct HugeGroups {
@@ -143,6 +170,56 @@ cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, 
 cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins& b, const uint32_t* counts,
                                  int sms, cudaStream_t s);
 cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s);
+
+// ------------------------------------------------------------------ batches (batch.cu)
+// One problem of a batch as the device kernels see it.
+struct BatchProb {
+  const int32_t* xc;
+  const double* xv;
+  const int32_t* yc;
+  const double* yv;
+  KeyPlan kx, ky;
+  u64 koff;   // first contract-key bin of this problem in the concatenated bins
+  u64 fxoff;  // offset of this problem's X free keys in the combined group-key space
+  u64 FY;
+};
+
+// A probing table giving each distinct group key a number: its slot.
+struct IdMap {
+  u64* keys;  // [mask + 1], kEmpty64 when free
+  u64 mask;
+};
+
+struct BatchArgs {
+  int n;
+  const BatchProb* pb;
+  const int64_t* xrow;  // [n + 1] row offsets of X in the flattened row space
+  const int64_t* yrow;  // [n + 1]
+  const u64* fxoff;     // [n + 1]
+  int64_t total_x, total_y;
+  u64 bins;             // concatenated contract-key bins
+  uint32_t* ycnt;
+  uint32_t* yoff;       // [bins + 1]
+  uint32_t* ycur;
+  void* yfk;
+  bool key32;
+  double* yv;
+  Survivors sv;
+  u64* P;               // total products
+  u64* Pp;              // [n] products per problem
+  IdMap idmap;
+  uint32_t* gid;        // [total_x] group number (table slot) of each survivor
+  uint32_t* gcnt;       // [table size] survivors per group
+  uint32_t* goff;       // [table size + 1]
+  uint32_t* gcur;       // [table size]
+  u64* pcap;            // [n] output bound per problem
+  uint32_t* scan_scratch32;
+  uint32_t* status;
+};
+
+cudaError_t launch_batch_prepare(const BatchArgs& ba, int sms, cudaStream_t s);
+cudaError_t launch_batch_group(const BatchArgs& ba, GroupedX gx, const Bins& b, uint32_t* gprob, u64* gfk, int sms,
+                               cudaStream_t s);
 
 // Dense-row accumulation: each group's outputs are accumulated one free-key segment at a time
 // in a dense shared-memory array indexed by the free key. `yoff` are the per-(contract key,
