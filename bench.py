@@ -39,15 +39,17 @@ def plain_large_slice(seed):
 
 
 WORKLOADS = {
+    "batched": lambda seed: W.batched(seed=seed),
     "plain_large": lambda seed: W.plain_large(seed=seed),
     "plain_large_slice": plain_large_slice,
     "imbalanced": lambda seed: W.imbalanced(seed=seed),
     "imbalanced_both": lambda seed: W.imbalanced(seed=seed, both_zipf=True),
     "plain_small": lambda seed: W.plain_small(seed=seed),
 }
-SEEDS = {"plain_large": W.SEED_BASE + 2, "plain_large_slice": W.SEED_BASE + 2, "imbalanced": W.SEED_BASE + 3, "imbalanced_both": W.SEED_BASE + 3,
+SEEDS = {"batched": W.SEED_BASE + 4, "plain_large": W.SEED_BASE + 2, "plain_large_slice": W.SEED_BASE + 2, "imbalanced": W.SEED_BASE + 3, "imbalanced_both": W.SEED_BASE + 3,
          "plain_small": W.SEED_BASE + 1}
 DESCRIPTIONS = {
+    "batched": "2,048 order-3 pairs, lengths 16..512, one paired mode, nnz log-uniform 1e2..1e5 each, one batch call",
     "plain_large_slice": "X 16x256^3 3.125e5 nnz, Y 256^4 5e6 nnz, X modes (2,3) x Y modes (0,1) (profiling slice)",
     "plain_large": "X,Y order-4 256^4 COO, 5e6 uniform nnz each, X modes (2,3) x Y modes (0,1), FP64",
     "imbalanced": "X 4096x512x512 2e7 nnz, Y 512x512x64 2e4 nnz with Zipf(1.2) contract keys, X (1,2) x Y (0,1)",
@@ -55,7 +57,7 @@ DESCRIPTIONS = {
     "plain_small": "X,Y order-3 64^3 COO, 5e3 distinct nnz each, X mode 2 x Y mode 0",
 }
 # Rows of X (first coordinate < bound) that make the oracle's bounded CPU sample.
-CPU_SAMPLE_X0 = {"plain_large": 7, "plain_large_slice": 1, "imbalanced": 4096, "imbalanced_both": 64, "plain_small": 64}
+CPU_SAMPLE_X0 = {"batched": 0, "plain_large": 7, "plain_large_slice": 1, "imbalanced": 4096, "imbalanced_both": 64, "plain_small": 64}
 
 
 def peaks():
@@ -147,6 +149,12 @@ def cpu_sample(p, workload):
 def run_oracle_sample(p, workload):
     import oracle
 
+    if workload == "batched":
+        t0 = time.perf_counter()
+        prods = 0
+        for q in p[:48]:
+            prods += oracle.contract(q.X, q.Y, q.cx, q.cy).products
+        return prods, time.perf_counter() - t0, "the first 48 of the 2,048 pairs, one after another"
     sp, desc = cpu_sample(p, workload)
     t0 = time.perf_counter()
     r = oracle.contract(sp.X, sp.Y, sp.cx, sp.cy, sp.out_order)
@@ -183,24 +191,108 @@ def reference_arm(args):
     return 0
 
 
+def serve_bench(args):
+    """Requests with Poisson arrivals through the server: one-at-a-time launches against
+    continuous batching on the same arrival trace (p50/p99 latency and throughput)."""
+    import torch
+
+    import paper_2410_10094_gb300 as stc
+
+    torch.cuda.set_device(0)
+    stc.load()
+    ctx = stc.default_context(0)
+    rng = W.rng_for(W.SEED_BASE + 5)
+    small = [W.small_pair(rng) for _ in range(96)]
+    large = [W.served_large(rng) for _ in range(12)]
+    dev = lambda t: (t.shape, torch.from_numpy(t.coords).cuda(), torch.from_numpy(t.vals).cuda())
+    dsmall = [(dev(q.X), dev(q.Y), q.cx, q.cy) for q in small]
+    dlarge = [(dev(q.X), dev(q.Y), q.cx, q.cy) for q in large]
+    R = args.requests
+    is_large = rng.random(R) < 0.2
+    pick = [(dlarge[int(rng.integers(len(dlarge)))] if big else dsmall[int(rng.integers(len(dsmall)))])
+            for big in is_large]
+    prod = {}
+
+    def run(trace, plain):
+        srv = stc.Server(plain=plain, mem_budget_bytes=int(150e9), ctx=ctx)
+        tickets = [None] * len(trace)
+        ready = threading.Semaphore(0)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, at in enumerate(trace):
+                delay = at - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[i] = srv.submit(*pick[i])
+                ready.release()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, first, last, products = [], None, 0.0, 0
+        for i in range(len(trace)):
+            ready.acquire()
+            r, (ts, tst, td) = srv.wait(tickets[i])
+            lat.append(td - ts)
+            first = ts if first is None else min(first, ts)
+            last = max(last, td)
+            products += r.stats.products
+            del r
+        th.join()
+        srv.close()
+        lat = np.asarray(lat)
+        span = last - first
+        return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "requests_per_s": len(trace) / span, "products_per_s": products / span, "span_s": span}
+
+    warm = run(np.zeros(min(40, R)), plain=False)
+    base = run(np.zeros(min(200, R)), plain=True)
+    mu_plain = base["requests_per_s"]
+    rows = []
+    for f in args.rates:
+        lam = f * mu_plain
+        trace = np.cumsum(rng.exponential(1.0 / lam, size=R))
+        plain_r = run(trace, plain=True)
+        batch_r = run(trace, plain=False)
+        rows.append({"rate_over_mu_plain": f, "lambda_per_s": lam, "plain": plain_r, "served": batch_r})
+    best = rows[-1]["served"]
+    line = {
+        "metric": "p50/p99 latency served vs plain", "value": best["p99_ms"], "unit": "ms (p99, highest rate)",
+        "n_gpus": 1, "steps": R, "warmup": len(warm) if isinstance(warm, list) else 40,
+        "ms_per_step": 1e3 / best["requests_per_s"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"served: {R} requests, 80% batched-mix pairs, 20% order-4 128^4 pairs with 1e6 nnz "
+                               "each contracting 2 modes; Poisson arrivals; 150 GB admission budget",
+                   "mu_plain_requests_per_s": mu_plain, "pools": "96 small and 12 large distinct problems"},
+        "rates": rows,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain_large", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="plain_large", choices=sorted(WORKLOADS) + ["served"])
     ap.add_argument("--strategy", type=int, default=0, help="0 auto, 1 global table, 2 grouped")
     ap.add_argument("--group-load-factor", type=float, default=0.0, help="0 = library default")
     ap.add_argument("--accumulator", type=int, default=0, help="0 auto, 1 hash tables, 2 dense rows")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--requests", type=int, default=1000, help="served workload: requests per arrival rate")
+    ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 0.9, 1.2],
+                    help="served workload: arrival rates as multiples of the one-at-a-time service rate")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "served":
+        return serve_bench(args)
 
     import torch
 
@@ -220,14 +312,31 @@ def main(argv=None):
 
     seed = SEEDS[args.workload] + 1000 * rank
     p = WORKLOADS[args.workload](seed)
-    X = (p.X.shape, torch.from_numpy(p.X.coords).cuda(), torch.from_numpy(p.X.vals).cuda())
-    Y = (p.Y.shape, torch.from_numpy(p.Y.coords).cuda(), torch.from_numpy(p.Y.vals).cuda())
+    workload_problem = p
     stream = torch.cuda.current_stream()
+    dev = lambda t: (t.shape, torch.from_numpy(t.coords).cuda(), torch.from_numpy(t.vals).cuda())
+    if args.workload == "batched":
+        batch = [(dev(q.X), dev(q.Y), q.cx, q.cy, q.out_order) for q in p]
 
-    def step(record=False):
-        return stc.contract(X, Y, p.cx, p.cy, p.out_order, strategy=args.strategy, record_times=record,
-                            group_load_factor=args.group_load_factor, accumulator=args.accumulator, stream=stream,
-                            ctx=ctx)
+        class _Agg:  # one step's results seen as one
+            def __init__(self, rs):
+                self.rs = rs
+                self.nnz = sum(r.nnz for r in rs)
+                self.order = rs[0].order
+                st = rs[0].stats
+                self.stats = type(st)(sum(r.stats.products for r in rs), 0, sum(r.stats.out_capacity for r in rs),
+                                      0, 0, st.strategy, st.launches, st.accumulator, st.stage_ms)
+
+        def step(record=False):
+            return _Agg(stc.contract_batch(batch, group_load_factor=args.group_load_factor, record_times=record,
+                                           stream=stream, ctx=ctx))
+    else:
+        X, Y = dev(p.X), dev(p.Y)
+
+        def step(record=False):
+            return stc.contract(X, Y, p.cx, p.cy, p.out_order, strategy=args.strategy, record_times=record,
+                                group_load_factor=args.group_load_factor, accumulator=args.accumulator,
+                                stream=stream, ctx=ctx)
 
     for _ in range(args.warmup):
         r = step()
@@ -267,7 +376,19 @@ def main(argv=None):
 
     # ---- e2e: the public API call with host buffers, copies inside the timed region
     e2e = None
-    if not args.no_e2e:
+    sequential = None
+    if args.workload == "batched":
+        # The same 2,048 problems as 2,048 separate stc_contract calls (one at a time).
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (Xq, Yq, cxq, cyq, ooq) in batch:
+            rq = stc.contract(Xq, Yq, cxq, cyq, ooq, stream=stream, ctx=ctx)
+            del rq
+        torch.cuda.synchronize()
+        seq_s = time.perf_counter() - t0
+        sequential = {"ms": 1e3 * seq_s, "value": total_products / seq_s, "unit": "products/s",
+                      "speedup_of_batch": (total_products / seq_s) and value / (total_products / seq_s)}
+    if not args.no_e2e and args.workload != "batched":
         hx = [torch.from_numpy(p.X.coords).pin_memory(), torch.from_numpy(p.X.vals).pin_memory()]
         hy = [torch.from_numpy(p.Y.coords).pin_memory(), torch.from_numpy(p.Y.vals).pin_memory()]
         hc = torch.empty((nz, oz), dtype=torch.int32).pin_memory()
@@ -307,6 +428,15 @@ def main(argv=None):
     stage_names = ["group_y", "survey_x", "group_x", "plan", "accumulate", "compact"]
     per_step = stage / args.steps
     dom = int(np.argmax(per_step[:6]))
+    if args.workload == "batched":
+        class _P:
+            pass
+        agg = _P()
+        agg.X = _P(); agg.Y = _P()
+        agg.X.order, agg.Y.order = 3, 3
+        agg.X.nnz = sum(q.X.nnz for q in p)
+        agg.Y.nnz = sum(q.Y.nnz for q in p)
+        p = agg
     bytes_in = (4 * p.X.order + 8) * p.X.nnz + (4 * p.Y.order + 8) * p.Y.nnz
     kernel_bytes = {
         0: (4 * p.Y.order + 8) * p.Y.nnz + 16 * p.Y.nnz,            # read Y, write grouped Y
@@ -324,7 +454,7 @@ def main(argv=None):
 
     cpu = None
     if not args.no_cpu_baseline:
-        prods, dt, desc = run_oracle_sample(p, args.workload)
+        prods, dt, desc = run_oracle_sample(workload_problem, args.workload)
         cpu = {"value": prods / dt, "unit": "products/s", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": dt}
 
@@ -341,6 +471,7 @@ def main(argv=None):
                      "frac": step_alg / (step_ms / 1e3) / 1e9 / hbm},
         "stage_ms": {n: float(per_step[i]) for i, n in enumerate(stage_names)},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches) * args.steps,
+        "sequential_calls": sequential,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -157,6 +157,46 @@ typedef struct stc_problem {
 stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* problems, const stc_opts* opts,
                               void* stream, stc_result** outs);
 
+/* ---------------------------------------------------------------- serving
+ * A server takes contraction requests as they arrive and runs them on worker threads, each
+ * with its own CUDA stream. Each request is admitted by its exact device-memory bound
+ * (computed from the product count of Section 4.3 at submission) against the server's
+ * budget; queued requests that fit are run together as one stc_contract_batch by the next
+ * free worker, so requests that arrive while others run join the next batch and batches of
+ * different workers overlap on the device (continuous batching). With `plain` set, one
+ * worker runs one request at a time with stc_contract: the one-at-a-time baseline. */
+typedef struct stc_server stc_server;
+
+typedef struct stc_server_opts {
+  uint64_t mem_budget_bytes; /* admission budget for requests in flight; 0 = no limit */
+  int32_t max_batch;         /* most requests per batch; 0 = no limit */
+  int32_t workers;           /* worker threads (streams); 0 = 2 */
+  int32_t plain;             /* nonzero: one request per launch, one worker (baseline) */
+  int32_t reserved_;
+} stc_server_opts;
+
+/* Create a server on ctx's device; the calling thread's current device must be ctx's. */
+stc_status stc_server_create(stc_ctx* ctx, const stc_server_opts* opts, stc_server** out);
+
+/* Queue a request. Its device arrays must stay valid and unchanged until the request is
+ * finished; its host arrays (shapes, mode lists) are copied. Runs the counting pass that
+ * sizes the request before returning. ticket receives the request's id. */
+stc_status stc_server_submit(stc_server* s, const stc_problem* request, uint64_t* ticket);
+
+/* done receives 1 when the request has finished (successfully or not), else 0. */
+stc_status stc_server_poll(stc_server* s, uint64_t ticket, int32_t* done);
+
+/* Wait up to timeout_ms (negative: no limit) for a request and take its result (the caller
+ * frees it with stc_result_free, which may happen after the server is destroyed; its memory
+ * then goes back on the legacy default stream, so work reading it must be finished). times: host, [3] or NULL, receives the request's submit,
+ * start and finish times in seconds since the server was created. STC_ERR_TIMEOUT if the
+ * request is still running (the ticket stays valid); otherwise the ticket is consumed and the
+ * request's own status is returned. */
+stc_status stc_server_wait(stc_server* s, uint64_t ticket, int64_t timeout_ms, stc_result** out, double* times);
+
+/* Finish every queued request, stop the workers, free uncollected results, destroy. */
+stc_status stc_server_destroy(stc_server* s);
+
 /* The exact product count of the contraction (Section 4.3: each X entry meets exactly
  * count_Y[its contract key] Y entries) and the device bytes a stc_contract of the same
  * inputs would hold at its peak (scratch + result). Used to admit work under a budget. */

@@ -38,6 +38,11 @@ class stc_problem(C.Structure):
                 ("cy", C.POINTER(C.c_int32)), ("out_order", C.POINTER(C.c_int32))]
 
 
+class stc_server_opts(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_batch", C.c_int32), ("workers", C.c_int32),
+                ("plain", C.c_int32), ("reserved_", C.c_int32)]
+
+
 class stc_opts(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double),
                 ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("reserved_", C.c_int32)]
@@ -60,6 +65,11 @@ EXPORTS = {
                       C.c_void_p, C.POINTER(stc_opts), C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
     "stc_contract_batch": ([C.c_void_p, C.c_int32, C.POINTER(stc_problem), C.POINTER(stc_opts), C.c_void_p,
                             C.POINTER(C.c_void_p)], C.c_int),
+    "stc_server_create": ([C.c_void_p, C.POINTER(stc_server_opts), C.POINTER(C.c_void_p)], C.c_int),
+    "stc_server_submit": ([C.c_void_p, C.POINTER(stc_problem), C.POINTER(C.c_uint64)], C.c_int),
+    "stc_server_poll": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_int32)], C.c_int),
+    "stc_server_wait": ([C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(C.c_void_p), C.POINTER(C.c_double)], C.c_int),
+    "stc_server_destroy": ([C.c_void_p], C.c_int),
     "stc_count": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
                    C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
     "stc_linearize": ([C.c_void_p, C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -363,6 +373,53 @@ def contract_batch(problems, *, group_load_factor: float = 0.0, record_times: bo
     probs = [tuple(p) + (None,) * (5 - len(p)) for p in problems]
     o = stc_opts(STRATEGY_GROUPED, 1 if record_times else 0, 0.0, float(group_load_factor), ACC_HASH, 0)
     return [Result(h) for h in stc_contract_batch(ctx.handle, probs, o, stream)]
+
+
+class Server:
+    """The contraction server (stc_server_*). submit() takes (X, Y, cx, cy[, out_order]) with
+    CUDA tensors (kept alive here until the request finishes) and returns a ticket;
+    wait(ticket) returns (Result, (t_submit, t_start, t_done))."""
+
+    def __init__(self, *, mem_budget_bytes: int = 0, max_batch: int = 0, workers: int = 0, plain: bool = False,
+                 ctx: Context = None):
+        self.ctx = ctx or default_context()
+        o = stc_server_opts(int(mem_budget_bytes), int(max_batch), int(workers), 1 if plain else 0, 0)
+        h = C.c_void_p()
+        check(load().stc_server_create(C.c_void_p(self.ctx.handle), C.byref(o), C.byref(h)))
+        self.handle = h.value
+        self._inputs = {}
+
+    def submit(self, X, Y, cx, cy, out_order=None) -> int:
+        xa, ya = _CooArg(*X), _CooArg(*Y)
+        acx, acy = _mode_array(cx), _mode_array(cy)
+        oo = _mode_array(out_order) if out_order is not None else None
+        req = stc_problem(xa.coo, ya.coo, len(cx), C.cast(acx, C.POINTER(C.c_int32)),
+                          C.cast(acy, C.POINTER(C.c_int32)),
+                          C.cast(oo, C.POINTER(C.c_int32)) if oo is not None else None)
+        t = C.c_uint64()
+        check(load().stc_server_submit(C.c_void_p(self.handle), C.byref(req), C.byref(t)))
+        self._inputs[t.value] = (X, Y)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = C.c_int32()
+        check(load().stc_server_poll(C.c_void_p(self.handle), ticket, C.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        r = C.c_void_p()
+        times = (C.c_double * 3)()
+        st = load().stc_server_wait(C.c_void_p(self.handle), ticket, int(timeout_ms), C.byref(r), times)
+        if st != 6:  # a timeout leaves the ticket (and its inputs) in place
+            self._inputs.pop(ticket, None)
+        check(st)
+        return Result(r.value), (times[0], times[1], times[2])
+
+    def close(self):
+        if self.handle:
+            check(load().stc_server_destroy(C.c_void_p(self.handle)))
+            self.handle = 0
+            self._inputs.clear()
 
 
 def count(X, Y, cx, cy, *, stream=None, ctx: Context = None):

@@ -612,6 +612,14 @@ DeviceBlock::~DeviceBlock() {
 namespace stc {
 // Lets other translation units of the library set the calling thread's last error.
 stc_status report_error(stc_status s, const char* msg) { return fail(s, "%s", msg); }
+int ctx_device(const stc_ctx* ctx) { return ctx->device; }
+// Results handed out by a server outlive its streams: their memory is returned on the legacy
+// default stream instead (their data is complete when they are handed out).
+void result_release_on_default_stream(stc_result* r) {
+  if (!r) return;
+  r->stream = nullptr;
+  if (r->mem) r->mem->stream = nullptr;
+}
 }  // namespace stc
 
 extern "C" {

@@ -1,0 +1,270 @@
+// A contraction server: requests (each one stc_contract's arguments) are queued, admitted
+// against a device-memory budget by their exact bound (the product count of Section 4.3
+// gives the output bound before any product is formed), and run in batches by worker
+// threads, each on its own stream, so that batches overlap on the device. Requests that
+// arrive while batches are running join the next batch of a free worker (continuous
+// batching). With `plain` set the server runs one request at a time with stc_contract on
+// one worker: the one-at-a-time baseline on the same arrival trace.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "launch.h"
+
+namespace stc {
+stc_status report_error(stc_status s, const char* msg);
+int ctx_device(const stc_ctx* ctx);
+void result_release_on_default_stream(stc_result* r);
+}
+using namespace stc;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Ticket {
+  stc_problem req{};
+  std::vector<int64_t> xshape, yshape;
+  std::vector<int32_t> cx, cy, oo;
+  bool has_oo = false;
+  uint64_t bytes = 0;  // admission bound
+  bool done = false;
+  stc_status status = STC_OK;
+  std::string error;
+  stc_result* result = nullptr;
+  double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct stc_server {
+  stc_ctx* ctx = nullptr;
+  stc_server_opts opts{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, Ticket> tickets;
+  uint64_t next_ticket = 1;
+  uint64_t reserved = 0;
+  int running_batches = 0;
+  bool stopping = false;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t count_stream = nullptr;
+  std::mutex count_mu;
+  Clock::time_point epoch;
+  double now() const { return std::chrono::duration<double>(Clock::now() - epoch).count(); }
+};
+
+namespace {
+
+// Copies the host-side parts of a request (shapes, mode lists) so the caller's arrays may go.
+void own_request(Ticket& t, const stc_problem& r) {
+  t.req = r;
+  t.xshape.assign(r.X.shape, r.X.shape + r.X.order);
+  t.yshape.assign(r.Y.shape, r.Y.shape + r.Y.order);
+  t.cx.assign(r.cx, r.cx + r.ncontract);
+  t.cy.assign(r.cy, r.cy + r.ncontract);
+  t.req.X.shape = t.xshape.data();
+  t.req.Y.shape = t.yshape.data();
+  t.req.cx = t.cx.data();
+  t.req.cy = t.cy.data();
+  if (r.out_order) {
+    const int oz = (r.X.order - r.ncontract) + (r.Y.order - r.ncontract);
+    t.oo.assign(r.out_order, r.out_order + (oz > 0 ? oz : 0));
+    t.req.out_order = t.oo.data();
+    t.has_oo = true;
+  }
+}
+
+void worker_main(stc_server* sv, int w) {
+  cudaStream_t s = sv->streams[w];
+  cudaSetDevice(ctx_device(sv->ctx));
+  for (;;) {
+    std::vector<uint64_t> batch;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv_work.wait(lk, [&] { return sv->stopping || !sv->queue.empty(); });
+      if (sv->queue.empty()) return;  // stopping and drained
+      // Take queued requests in arrival order while they fit the budget; a request larger
+      // than the whole budget runs alone once nothing else is reserved.
+      const uint64_t budget = sv->opts.mem_budget_bytes;
+      const int maxb = sv->opts.plain ? 1 : (sv->opts.max_batch > 0 ? sv->opts.max_batch : 1 << 30);
+      while (!sv->queue.empty() && (int)batch.size() < maxb) {
+        Ticket& t = sv->tickets[sv->queue.front()];
+        const bool fits = budget == 0 || sv->reserved + t.bytes <= budget || (sv->reserved == 0 && batch.empty());
+        if (!fits) break;
+        sv->reserved += t.bytes;
+        batch.push_back(sv->queue.front());
+        sv->queue.pop_front();
+      }
+      if (batch.empty()) {
+        // Nothing fits until memory is released: wait for a batch to finish.
+        sv->cv_work.wait(lk, [&] { return sv->stopping || sv->running_batches == 0 || sv->reserved == 0; });
+        continue;
+      }
+      sv->running_batches++;
+      const double t0 = sv->now();
+      for (uint64_t id : batch) sv->tickets[id].t_start = t0;
+    }
+    // Run the batch (outside the lock).
+    std::vector<stc_problem> probs;
+    probs.reserve(batch.size());
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (uint64_t id : batch) probs.push_back(sv->tickets[id].req);
+    }
+    std::vector<stc_result*> outs(batch.size(), nullptr);
+    stc_status st;
+    std::string err;
+    if (sv->opts.plain) {
+      const stc_problem& q = probs[0];
+      st = stc_contract(sv->ctx, &q.X, &q.Y, q.ncontract, q.cx, q.cy, q.out_order, nullptr, s, &outs[0]);
+    } else {
+      stc_opts o{};
+      o.strategy = STC_STRATEGY_GROUPED;
+      st = stc_contract_batch(sv->ctx, (int32_t)probs.size(), probs.data(), &o, s, outs.data());
+    }
+    if (st != STC_OK) err = stc_last_error();
+    for (stc_result* r : outs) result_release_on_default_stream(r);
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      const double t1 = sv->now();
+      for (size_t k = 0; k < batch.size(); k++) {
+        Ticket& t = sv->tickets[batch[k]];
+        t.done = true;
+        t.status = st;
+        t.error = err;
+        t.result = outs[k];
+        t.t_done = t1;
+        sv->reserved -= t.bytes;
+      }
+      sv->running_batches--;
+    }
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+stc_status stc_server_create(stc_ctx* ctx, const stc_server_opts* opts, stc_server** out) {
+  if (!ctx || !out) return report_error(STC_ERR_INVALID_ARG, "ctx or out is NULL");
+  *out = nullptr;
+  stc_server* sv = new stc_server;
+  sv->ctx = ctx;
+  if (opts) sv->opts = *opts;
+  if (sv->opts.workers <= 0) sv->opts.workers = sv->opts.plain ? 1 : 2;
+  if (sv->opts.plain) sv->opts.workers = 1;
+  sv->epoch = Clock::now();
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx_device(ctx)) {
+    delete sv;
+    return report_error(STC_ERR_INVALID_ARG, "the current device is not the context's device");
+  }
+  for (int w = 0; w < sv->opts.workers + 1; w++) {
+    cudaStream_t s = nullptr;
+    const cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (auto x : sv->streams) cudaStreamDestroy(x);
+      delete sv;
+      return report_error(STC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (w < sv->opts.workers) sv->streams.push_back(s);
+    else sv->count_stream = s;
+  }
+  for (int w = 0; w < sv->opts.workers; w++) sv->workers.emplace_back(worker_main, sv, w);
+  *out = sv;
+  return STC_OK;
+}
+
+stc_status stc_server_submit(stc_server* sv, const stc_problem* req, uint64_t* ticket) {
+  if (!sv || !req || !ticket) return report_error(STC_ERR_INVALID_ARG, "NULL argument");
+  const double t_arrive = sv->now();
+  Ticket t;
+  own_request(t, *req);
+  // Admission bound: the exact product count bounds the output (Section 4.3).
+  {
+    std::lock_guard<std::mutex> lk(sv->count_mu);
+    uint64_t P = 0, bytes = 0;
+    const stc_status st = stc_count(sv->ctx, &t.req.X, &t.req.Y, t.req.ncontract, t.req.cx, t.req.cy,
+                                    sv->count_stream, &P, &bytes);
+    if (st != STC_OK) return st;
+    t.bytes = bytes;
+  }
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->stopping) return report_error(STC_ERR_INVALID_ARG, "server is shutting down");
+  const uint64_t id = sv->next_ticket++;
+  t.t_submit = t_arrive;
+  sv->tickets.emplace(id, std::move(t));
+  // Re-point the copied host arrays at the map's copy.
+  Ticket& tt = sv->tickets[id];
+  tt.req.X.shape = tt.xshape.data();
+  tt.req.Y.shape = tt.yshape.data();
+  tt.req.cx = tt.cx.data();
+  tt.req.cy = tt.cy.data();
+  tt.req.out_order = tt.has_oo ? tt.oo.data() : nullptr;
+  sv->queue.push_back(id);
+  *ticket = id;
+  sv->cv_work.notify_one();
+  return STC_OK;
+}
+
+stc_status stc_server_poll(stc_server* sv, uint64_t ticket, int32_t* done) {
+  if (!sv || !done) return report_error(STC_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->tickets.find(ticket);
+  if (it == sv->tickets.end()) return report_error(STC_ERR_INVALID_ARG, "unknown ticket");
+  *done = it->second.done ? 1 : 0;
+  return STC_OK;
+}
+
+stc_status stc_server_wait(stc_server* sv, uint64_t ticket, int64_t timeout_ms, stc_result** out,
+                           double* times) {
+  if (!sv || !out) return report_error(STC_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->tickets.find(ticket);
+  if (it == sv->tickets.end()) return report_error(STC_ERR_INVALID_ARG, "unknown ticket");
+  const auto pred = [&] { return sv->tickets[ticket].done; };
+  if (timeout_ms < 0) {
+    sv->cv_done.wait(lk, pred);
+  } else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) {
+    return report_error(STC_ERR_TIMEOUT, "request not finished within the timeout");
+  }
+  Ticket t = std::move(sv->tickets[ticket]);
+  sv->tickets.erase(ticket);
+  if (times) {
+    times[0] = t.t_submit;
+    times[1] = t.t_start;
+    times[2] = t.t_done;
+  }
+  if (t.status != STC_OK) return report_error(t.status, t.error.c_str());
+  *out = t.result;
+  return STC_OK;
+}
+
+stc_status stc_server_destroy(stc_server* sv) {
+  if (!sv) return STC_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stopping = true;
+  }
+  sv->cv_work.notify_all();
+  for (auto& th : sv->workers) th.join();
+  // Results nobody collected are freed here.
+  for (auto& kv : sv->tickets)
+    if (kv.second.result) stc_result_free(kv.second.result);
+  for (auto s : sv->streams) cudaStreamDestroy(s);
+  if (sv->count_stream) cudaStreamDestroy(sv->count_stream);
+  delete sv;
+  return STC_OK;
+}
+
+}  // extern "C"
