@@ -68,10 +68,12 @@ typedef struct stc_coo {
 enum { STC_STRATEGY_AUTO = 0, STC_STRATEGY_GLOBAL = 1, STC_STRATEGY_GROUPED = 2 };
 
 /* Per-group accumulator of the GROUPED strategy. HASH: a probing table sized from the
- * group's bound (Section 4.3). DENSE: the group's output row swept in segments of the Y free
- * key space, each accumulated in a dense array indexed by the free key; used when F_Y is at
- * most 2^20 and rows are dense enough. AUTO picks between them. */
-enum { STC_ACC_AUTO = 0, STC_ACC_HASH = 1, STC_ACC_DENSE = 2 };
+ * group's bound (Section 4.3); where keys and output positions fit 32 bits, each output is
+ * written as soon as its key is first claimed. HASH_SCAN: the same table, accumulated in
+ * shared memory and written by a scan of the table after the group. DENSE: the group's output
+ * row swept in segments of the Y free key space, each accumulated in a dense array indexed
+ * by the free key (F_Y at most 2^20). AUTO = HASH. */
+enum { STC_ACC_AUTO = 0, STC_ACC_HASH = 1, STC_ACC_DENSE = 2, STC_ACC_HASH_SCAN = 3 };
 
 typedef struct stc_opts {
   int32_t strategy;       /* STC_STRATEGY_*; 0 = AUTO */

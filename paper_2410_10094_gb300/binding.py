@@ -18,7 +18,7 @@ STATUS_NAMES = {
     8: "STC_ERR_COORD_OUT_OF_RANGE", 9: "STC_ERR_UNSUPPORTED",
 }
 STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_GROUPED = 0, 1, 2
-ACC_AUTO, ACC_HASH, ACC_DENSE = 0, 1, 2
+ACC_AUTO, ACC_HASH, ACC_DENSE, ACC_HASH_SCAN = 0, 1, 2, 3
 STC_MAX_ORDER = 8
 
 

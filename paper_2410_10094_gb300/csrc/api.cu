@@ -578,7 +578,8 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   if (dense_rows) {
     STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.list[0], hg.count[0], ctx->sms, s));
   } else {
-    STC_CUDA(launch_group_classes(a, wide, b, hg.count, ctx->sms, s));
+    const bool direct = !wide && out_cap < 0xffffffffull && o.accumulator != STC_ACC_HASH_SCAN;
+    STC_CUDA(launch_group_classes(a, wide, direct, b, hg.count, ctx->sms, s));
     STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
   }
   tm.mark(4);
@@ -696,7 +697,7 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
   if (!(alpha > 0.0 && alpha <= 0.9)) return fail(STC_ERR_INVALID_ARG, "load_factor %g outside (0, 0.9]", alpha);
   if (o.strategy < 0 || o.strategy > STC_STRATEGY_GROUPED)
     return fail(STC_ERR_INVALID_ARG, "unknown strategy %d", o.strategy);
-  if (o.accumulator < 0 || o.accumulator > STC_ACC_DENSE)
+  if (o.accumulator < 0 || o.accumulator > STC_ACC_HASH_SCAN)
     return fail(STC_ERR_INVALID_ARG, "unknown accumulator %d", o.accumulator);
   if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
     return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
@@ -997,7 +998,10 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
   a.gprob = gprob;
   a.gfk = gfk;
   if (h.P > 0) {
-    STC_CUDA(launch_group_classes(a, wide, b, hg.count, ctx->sms, s));
+    u64 maxcap = 0;
+    for (int32_t i = 0; i < n; i++) maxcap = std::max<u64>(maxcap, hper[n + i]);
+    const bool direct = !wide && maxcap < 0xffffffffull && o.accumulator != STC_ACC_HASH_SCAN;
+    STC_CUDA(launch_group_classes(a, wide, direct, b, hg.count, ctx->sms, s));
     STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
   }
   tm.mark(4);

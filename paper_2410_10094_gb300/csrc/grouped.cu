@@ -99,6 +99,7 @@ __device__ __forceinline__ void resolve_target(const GroupArgs& a, u64 g, unsign
   const BatchOut* bo = a.bout + p;
   const u64 FY = bo->FY;
   t.zrow = (a.gfk ? a.gfk[g] : g) * FY;
+  t.counter = a.bnz + p;
   t.base = n ? atomicAdd(a.bnz + p, (u64)n) : 0;
   t.cap = bo->out_cap;
   t.coords = bo->coords;
@@ -889,6 +890,143 @@ cudaError_t launch_warp_class(const GroupArgs& a, const uint32_t* list, uint32_t
   return cudaGetLastError();
 }
 
+
+// ---- direct output: a product that claims a new key writes its output entry at once.
+// The table holds keys and output positions only. A claimer takes a rank inside its round
+// (warp-aggregated); after the round's claims are counted, one atomic per round reserves the
+// output positions, and claimers store their entry at base + rank (consecutive lanes,
+// consecutive positions). Products whose key was already present add their value to that
+// entry in global memory after a device-scope fence and a barrier, when the claiming store
+// is visible. No values are kept in shared memory and no table scan writes the output.
+template <int SLOTS, int THREADS, int D, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) group_direct_kernel(GroupArgs a, const uint32_t* __restrict__ list,
+                                                                     uint32_t count) {
+  constexpr int NW = THREADS / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* spos = keys + SLOTS;
+  Chunk<THREADS>& c = *reinterpret_cast<Chunk<THREADS>*>(smem + 2 * SLOTS * sizeof(uint32_t));
+  __shared__ u64 warp_tot[NW];
+  __shared__ unsigned round_claims;
+  __shared__ u64 round_base;
+  __shared__ OutTarget tg;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  for (uint32_t i = threadIdx.x; i < SLOTS / 4; i += THREADS)
+    reinterpret_cast<uint4*>(keys)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+  if (threadIdx.x == 0) round_claims = 0;
+  const uint64_t keep = policy_evict_last();
+  const uint64_t pol = policy_evict_first();
+  for (uint32_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
+    const uint32_t g = list[gi];
+    if (threadIdx.x == 0) resolve_target(a, g, 0, tg);
+    const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
+    for (uint32_t c0 = x0; c0 < x1; c0 += THREADS) {
+      const uint32_t n = (x1 - c0 < (uint32_t)THREADS) ? x1 - c0 : (uint32_t)THREADS;
+      load_chunk<THREADS>(a, c, warp_tot, c0, n);  // its barriers also publish tg
+      const u64 total = c.pre[n];
+      const u64 lo = total * warp / NW, hi = total * (warp + 1) / NW;
+      uint32_t own = 0;
+      if (lo < hi) {
+        uint32_t l = 0, h = n - 1;
+        while (l < h) {
+          const uint32_t mid = (l + h + 1) >> 1;
+          if (c.pre[mid] <= lo) l = mid; else h = mid - 1;
+        }
+        own = l;
+      }
+      const u64 per = (total + NW - 1) / NW;
+      const uint32_t rounds = (uint32_t)((per + 32 * D - 1) / (32 * D));
+      for (uint32_t r = 0; r < rounds; r++) {
+        const u64 base = lo + (u64)r * 32 * D;
+        uint32_t key[D];
+        double prod[D];
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          const u64 p = base + (u64)u * 32 + lane;
+          uint32_t k = own;
+          key[u] = kEmpty32;
+          if (p < hi) {
+            while (c.pre[k + 1] <= p) k++;
+            const u64 j = (u64)c.ystart[k] + (p - c.pre[k]);
+            key[u] = ld_keep_u32(static_cast<const uint32_t*>(a.yfk) + j, keep);
+            prod[u] = __dmul_rn(c.v[k], ld_keep_f64(a.yv + j, keep));
+          }
+          own = __shfl_sync(0xffffffffu, k, 31);
+        }
+        int slot[D];
+        unsigned rank[D];
+        bool mine[D];
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          slot[u] = -1;
+          mine[u] = false;
+          if (key[u] != kEmpty32) {
+            slot[u] = bucket_claim<uint32_t, SLOTS>(keys, key[u], &mine[u]);
+            if (slot[u] < 0) atomicOr(a.status, kStatTableFull);
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, mine[u]);
+          unsigned wbase = 0;
+          if (m) {
+            const int leader = __ffs(m) - 1;
+            if ((int)lane == leader) wbase = atomicAdd(&round_claims, (unsigned)__popc(m));
+            wbase = __shfl_sync(0xffffffffu, wbase, leader);
+          }
+          rank[u] = wbase + __popc(m & lanemask_lt());
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const unsigned nclaim = round_claims;
+          round_base = nclaim ? atomicAdd(tg.counter, (u64)nclaim) : 0;
+          round_claims = 0;
+        }
+        __syncthreads();
+        const u64 rb = round_base;
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          if (mine[u]) {
+            const u64 pos = rb + rank[u];
+            spos[slot[u]] = (uint32_t)pos;
+            if (pos < tg.cap)
+              store_output(tg.coords, tg.vals, pos, tg.zrow + (u64)key[u], prod[u], tg.op, pol);
+            else
+              atomicOr(a.status, kStatOutOverflow);
+          }
+        }
+        __threadfence();
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          if (slot[u] >= 0 && !mine[u]) {
+            const u64 pos = spos[slot[u]];
+            if (pos < tg.cap) atomicAdd(tg.vals + pos, prod[u]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    for (uint32_t i = threadIdx.x; i < SLOTS / 4; i += THREADS)
+      reinterpret_cast<uint4*>(keys)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+    __syncthreads();
+  }
+}
+
+template <int SLOTS, int THREADS, int D, int MINB>
+cudaError_t launch_direct_class(const GroupArgs& a, const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const size_t smem = 2 * SLOTS * sizeof(uint32_t) + sizeof(Chunk<THREADS>);
+  auto kern = group_direct_kernel<SLOTS, THREADS, D, MINB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const uint32_t cap = (uint32_t)(sms * per_sm);
+  kern<<<count < cap ? count : cap, THREADS, smem, s>>>(a, list, count);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <int SLOTS, int THREADS, typename KT>
 cudaError_t launch_class(const GroupArgs& a, const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
@@ -931,10 +1069,16 @@ cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins& b, const uint32_t* counts,
-                                 int sms, cudaStream_t s) {
+cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct, const Bins& b,
+                                 const uint32_t* counts, int sms, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (!wide_keys) {
+  if (!wide_keys && direct) {
+    if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], counts[0], sms, s))) return e;
+    if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], counts[1], sms, s))) return e;
+    if ((e = launch_direct_class<4096, 256, 6, 4>(a, b.list[2], counts[2], sms, s))) return e;
+    if ((e = launch_direct_class<8192, 512, 6, 2>(a, b.list[3], counts[3], sms, s))) return e;
+    if ((e = launch_direct_class<16384, 1024, 4, 1>(a, b.list[4], counts[4], sms, s))) return e;
+  } else if (!wide_keys) {
     if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], counts[0], sms, s))) return e;
     if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], counts[1], sms, s))) return e;
     if ((e = launch_class<4096, 256, uint32_t>(a, b.list[2], counts[2], sms, s))) return e;

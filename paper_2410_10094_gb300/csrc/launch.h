@@ -146,11 +146,12 @@ struct GroupArgs {
 
 // Where one group's outputs go, resolved once per group.
 struct OutTarget {
-  u64 zrow;   // output key of the group's row: fX * F_Y
-  u64 base;   // first output position reserved for the group
-  u64 cap;    // output capacity of the group's problem
+  u64 zrow;      // output key of the group's row: fX * F_Y
+  u64 base;      // first output position reserved for the group
+  u64 cap;       // output capacity of the group's problem
   int32_t* coords;
   double* vals;
+  u64* counter;  // the problem's output counter (positions are reserved from it)
   OutPlan op;
 };
 
@@ -167,8 +168,10 @@ cudaError_t launch_x_group_scatter(Survivors sv, uint32_t* gcur, GroupedX gx, in
                                    cudaStream_t s);
 cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, u64 FY, const Bins& b, int sms,
                               cudaStream_t s);
-cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, const Bins& b, const uint32_t* counts,
-                                 int sms, cudaStream_t s);
+// direct: the shared-memory classes may write outputs as keys are first claimed (needs 32-bit
+// keys and output positions below 2^32 in every problem).
+cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct, const Bins& b,
+                                 const uint32_t* counts, int sms, cudaStream_t s);
 cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s);
 
 // ------------------------------------------------------------------ batches (batch.cu)

@@ -12,8 +12,9 @@ from helpers import REL_TOL
 pytestmark = pytest.mark.gpu
 
 # one global table; per-X-free-group hash tables; per-X-free-group dense rows
-MODES = [dict(strategy=1), dict(strategy=2, accumulator=1), dict(strategy=2, accumulator=2)]
-MODE_IDS = ["global", "grouped-hash", "grouped-dense"]
+MODES = [dict(strategy=1), dict(strategy=2, accumulator=1), dict(strategy=2, accumulator=3),
+         dict(strategy=2, accumulator=2)]
+MODE_IDS = ["global", "grouped-hash", "grouped-hash-scan", "grouped-dense"]
 STRATEGIES = [1, 2]
 
 
