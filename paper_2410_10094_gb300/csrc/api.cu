@@ -495,9 +495,12 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   if (dense_rows) STC_TRY(ar.alloc(&gx.ck, (size_t)nX));
   STC_TRY(ar.alloc(&gc, 1));
   if (dense_rows) {
-    b.nclasses = 1;
-    b.tmax[0] = ~0ull;
+    b.nclasses = 2;
+    b.by_products = 1;
+    b.tmax[0] = dense_stash_cap();
+    b.tmax[1] = ~0ull;
     STC_TRY(ar.alloc(&b.list[0], maxg));
+    STC_TRY(ar.alloc(&b.list[1], maxg));
   } else {
     b.nclasses = ncls;
     for (int c = 0; c < ncls; c++) {
@@ -576,7 +579,7 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   a.bout = dbo;
   a.bnz = &pr.ctr->nz;
   if (dense_rows) {
-    STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.list[0], hg.count[0], ctx->sms, s));
+    STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.list[0], hg.count[0], b.list[1], hg.count[1], ctx->sms, s));
   } else {
     const bool direct = !wide && out_cap < 0xffffffffull && o.accumulator != STC_ACC_HASH_SCAN;
     STC_CUDA(launch_group_classes(a, wide, direct, b, hg.count, ctx->sms, s));

@@ -64,8 +64,9 @@ __global__ void __launch_bounds__(kThreads) bin_groups_kernel(u64 FX, const uint
     if (lane == 0) {
       const u64 t = bnd < FY ? bnd : FY;
       my_cap += t;
+      const u64 key = b.by_products ? bnd : t;
       int c = 0;
-      while (c < b.nclasses && t > b.tmax[c]) c++;
+      while (c < b.nclasses && key > b.tmax[c]) c++;
       if (c < b.nclasses) {
         const uint32_t idx = atomicAdd(b.count + c, 1u);
         b.list[c][idx] = (uint32_t)g;
@@ -520,204 +521,731 @@ __global__ void __launch_bounds__(THREADS) group_global_kernel(GroupArgs a, Huge
 }
 
 
-// ---- dense rows: one free-key segment of one group at a time, accumulated in a dense
-// shared-memory array indexed by the free key (no hashing, no probing). Ownership of a slot
-// is settled without atomics: each product writes its id into the slot's tag unless the slot
-// is already owned; after a barrier the product whose id survived stores its value, and the
-// others (rare when outputs seldom repeat) add theirs atomically after a second barrier.
+// ---- bitmap rows: each group is swept one free-key segment at a time. Pass 1 sets, for
+// every product, the bit of its free key in a bitmap over the segment. An exclusive scan of
+// the words' population counts then ranks the keys present: the group's n outputs of the
+// segment take n consecutive output positions in ascending free-key order, reserved with one
+// atomic. Pass 2 forms the products again, finds each one's rank from its bitmap word and
+// the word's prefix, and accumulates it into a compact value array indexed by rank, which is
+// then written out with coalesced stores. No hashing or probing.
+//
+// Products are enumerated in slots of 32 consecutive Y entries of one X entry's run (one per
+// lane, coalesced). In the common case (a group that fits one chunk, with at most kSlotCap
+// slots per segment) the slots are listed in a table, and pass 1 also records, per slot, the
+// lanes whose key had already been marked (repeats): pass 2 then stores every first product
+// of a key without atomics and queues the repeats, which are added after one barrier.
+// Otherwise (long groups, many repeats or more keys than the value array) the first product
+// of a key is settled with a second bitmap in pass 2, repeats add after a per-round barrier,
+// and pass 2 is run once per window of ranks that fits the value array.
+
+constexpr uint32_t kSlotCap = 512;  // slot-table entries
+constexpr uint32_t kRepCap = 512;   // queued repeats
 
 template <int THREADS>
-struct DenseChunk {
-  u64 pre[THREADS + 1];
-  uint32_t ck[THREADS];
-  uint32_t ystart[THREADS];
-  double v[THREADS];
+struct BitmapStage {
+  uint32_t ys[THREADS];          // first Y slot of each entry's run in the current segment
+  uint32_t len[THREADS];         // run length
+  uint32_t ck[THREADS];          // contract key
+  uint32_t sstart[THREADS + 4];  // exclusive prefix of the entries' slot counts
+  double v[THREADS];             // X value
 };
 
+// Dynamic shared memory of the bitmap kernel, laid out for the widest segment (kDenseSeg
+// free keys, kBitmapWords words), in order: the words {bits, rank of the word's first key};
+// a region used either as the first-product bitmap or as the repeat masks and queue; the
+// slot table; kBitmapVcap values and as many 16-bit keys; the stage.
+constexpr uint32_t kBitmapWords = kDenseSeg / 32;
+constexpr size_t kBitmapUnion = (size_t)kBitmapWords * 4 > (size_t)kSlotCap * 4 + (size_t)kRepCap * 12
+                                    ? (size_t)kBitmapWords * 4
+                                    : (size_t)kSlotCap * 4 + (size_t)kRepCap * 12;
+constexpr size_t kBitmapFixed = (size_t)kBitmapWords * 8 + kBitmapUnion + (size_t)kSlotCap * 8;
 template <int THREADS>
-__device__ __forceinline__ void dense_stage(const GroupArgs& a, DenseChunk<THREADS>& c, uint32_t c0, uint32_t n) {
-  if (threadIdx.x < n) {
-    c.ck[threadIdx.x] = a.gx.ck[c0 + threadIdx.x];
-    c.v[threadIdx.x] = a.gx.v[c0 + threadIdx.x];
-  }
+__host__ __device__ constexpr uint32_t bitmap_vcap() {
+  return (uint32_t)((kBitmapSmemPerCta - kBitmapFixed - sizeof(BitmapStage<THREADS>)) / 10) & ~7u;
+}
+template <int THREADS>
+__host__ __device__ constexpr size_t bitmap_smem() {
+  return kBitmapFixed + (size_t)bitmap_vcap<THREADS>() * 10 + sizeof(BitmapStage<THREADS>);
 }
 
-// Expands segment q of the staged entries into the dense accumulator.
-template <int THREADS, int D>
-__device__ __forceinline__ void dense_expand(const GroupArgs& a, DenseChunk<THREADS>& c, u64* warp_tot,
-                                             const uint32_t* __restrict__ yoff, uint32_t nseg, uint32_t q,
-                                             uint32_t seg, uint32_t n, double* acc, uint16_t* tag,
-                                             unsigned* winners) {
+// Runs of segment q of the n staged entries and the prefix of their slot counts; returns
+// the chunk's slot count. Entries' ck and v must be staged.
+template <int THREADS>
+__device__ __forceinline__ uint32_t bitmap_runs(BitmapStage<THREADS>& st, u64* warp_tot,
+                                                const uint32_t* __restrict__ yoff, uint32_t nseg, uint32_t q,
+                                                uint32_t n, bool have_runs, uint32_t pf_ys, uint32_t pf_len) {
+  uint32_t slots = 0;
+  if (threadIdx.x < n) {
+    uint32_t lo = pf_ys, len = pf_len;
+    if (!have_runs) {
+      const u64 b = (u64)st.ck[threadIdx.x] * nseg + q;
+      lo = __ldg(yoff + b);
+      len = __ldg(yoff + b + 1) - lo;
+    }
+    st.ys[threadIdx.x] = lo;
+    st.len[threadIdx.x] = len;
+    slots = (len + 31) >> 5;
+  }
   constexpr int NW = THREADS / 32;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-  u64 w = 0;
-  if (threadIdx.x < n) {
-    const u64 b = (u64)c.ck[threadIdx.x] * nseg + q;
-    const uint32_t lo = __ldg(yoff + b);
-    c.ystart[threadIdx.x] = lo;
-    w = __ldg(yoff + b + 1) - lo;
+  uint32_t x = slots;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if ((int)lane >= o) x += y;
   }
-  block_scan<THREADS>(c.pre, w, warp_tot);
+  if (lane == 31) warp_tot[warp] = x;
   __syncthreads();
-  const u64 total = c.pre[n];
-  if (total == 0) return;
-  const u64 lo = total * warp / NW, hi = total * (warp + 1) / NW;
-  uint32_t own = 0;
-  if (lo < hi) {
-    uint32_t l = 0, h = n - 1;
-    while (l < h) {
-      const uint32_t mid = (l + h + 1) >> 1;
-      if (c.pre[mid] <= lo) l = mid; else h = mid - 1;
-    }
-    own = l;
-  }
-  const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
-  const u64 per = (total + NW - 1) / NW;
-  const uint32_t rounds = (uint32_t)((per + 32 * D - 1) / (32 * D));
-  unsigned my_win = 0;
-  for (uint32_t r = 0; r < rounds; r++) {
-    const u64 base = lo + (u64)r * 32 * D;
-    uint32_t slot[D];
-    double prod[D];
-    int st[D];  // 0 nothing, 1 candidate owner, 2 adds later
-#pragma unroll
-    for (int u = 0; u < D; u++) {
-      const u64 p = base + (u64)u * 32 + lane;
-      uint32_t k = own;
-      st[u] = 0;
-      if (p < hi) {
-        while (c.pre[k + 1] <= p) k++;
-        const u64 j = (u64)c.ystart[k] + (p - c.pre[k]);
-        slot[u] = __ldg(yfk + j) & (seg - 1);
-        prod[u] = __dmul_rn(c.v[k], __ldg(a.yv + j));
-        st[u] = 1;
-      }
-      own = __shfl_sync(0xffffffffu, k, 31);
-    }
-#pragma unroll
-    for (int u = 0; u < D; u++) {
-      if (st[u] == 1) {
-        volatile uint16_t* t = tag + slot[u];
-        if (*t != 0) st[u] = 2;
-        else *t = (uint16_t)(threadIdx.x * D + u + 1);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < D; u++) {
-      bool won = false;
-      if (st[u] == 1) {
-        if (tag[slot[u]] == (uint16_t)(threadIdx.x * D + u + 1)) {
-          acc[slot[u]] = prod[u];
-          won = true;
-        } else {
-          st[u] = 2;
-        }
-      }
-      my_win += __popc(__ballot_sync(0xffffffffu, won));
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < D; u++)
-      if (st[u] == 2) atomicAdd(acc + slot[u], prod[u]);
-  }
-  if (lane == 0 && my_win) atomicAdd(winners, my_win);
-}
-
-// Writes segment q of group g (its owned slots, in free-key order within each warp's slice)
-// and frees the tags.
-template <int THREADS>
-__device__ __forceinline__ void dense_write(const GroupArgs& a, u64 g, uint32_t q, uint32_t seg, const double* acc,
-                                            uint16_t* tag, unsigned* winners, unsigned* cursor, u64* gbase) {
-  const unsigned lane = lane_id();
-  if (threadIdx.x == 0) {
-    const unsigned n = *winners;
-    *gbase = n ? atomicAdd(a.nz, (u64)n) : 0;
-    *cursor = 0;
-    *winners = 0;
-  }
-  __syncthreads();
-  const u64 base = *gbase;
-  const u64 zrow = g * a.FY + (u64)q * seg;
-  const int oz = a.op.order;
-  for (uint32_t blk = 0; blk < seg; blk += THREADS * 8) {
-    const uint32_t s0 = blk + threadIdx.x * 8;
-    uint4 tv = make_uint4(0, 0, 0, 0);
-    if (s0 < seg) tv = *reinterpret_cast<const uint4*>(tag + s0);
-    const uint32_t words[4] = {tv.x, tv.y, tv.z, tv.w};
-    unsigned live = 0;
-#pragma unroll
-    for (int i = 0; i < 8; i++) live |= ((words[i >> 1] >> (16 * (i & 1))) & 0xffffu) ? (1u << i) : 0u;
-    const unsigned cnt = __popc(live);
-    unsigned pre = cnt;
+  if (threadIdx.x < 32) {
+    const uint32_t t = (int)lane < NW ? (uint32_t)warp_tot[lane] : 0u;
+    uint32_t inc = t;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, pre, o);
-      if ((int)lane >= o) pre += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((int)lane >= o) inc += y;
     }
-    const unsigned tot = __shfl_sync(0xffffffffu, pre, 31);
-    unsigned off = 0;
-    if (lane == 0 && tot) off = atomicAdd(cursor, tot);
-    off = __shfl_sync(0xffffffffu, off, 0) + pre - cnt;
+    if ((int)lane < NW) warp_tot[lane] = inc - t;
+    if (lane == 31) st.sstart[THREADS] = inc;
+  }
+  __syncthreads();
+  st.sstart[threadIdx.x] = (uint32_t)warp_tot[warp] + x - slots;
+  const uint32_t total = st.sstart[THREADS];
+  __syncthreads();
+  return total;
+}
+
+// A warp's walk over its share of the staged slots (chunks without a slot table). All lanes
+// hold the same state.
+template <int THREADS>
+struct SlotWalk {
+  uint32_t s, s_end;  // current slot and end of the warp's share
+  uint32_t e;         // current entry
+  uint32_t t0;        // offset of the current slot in the entry's run
+  uint32_t ys, len;   // current entry's run
+  __device__ __forceinline__ void seek(const BitmapStage<THREADS>& st, uint32_t n, uint32_t total) {
+    constexpr int NW = THREADS / 32;
+    const unsigned warp = threadIdx.x >> 5;
+    s = (uint32_t)((u64)total * warp / NW);
+    s_end = (uint32_t)((u64)total * (warp + 1) / NW);
+    e = 0;
+    t0 = 0;
+    ys = len = 0;
+    if (s < s_end) {
+      uint32_t l = 0, h = n - 1;  // largest e with sstart[e] <= s
+      while (l < h) {
+        const uint32_t mid = (l + h + 1) >> 1;
+        if (st.sstart[mid] <= s) l = mid; else h = mid - 1;
+      }
+      e = l;
+      t0 = (s - st.sstart[e]) << 5;
+      ys = st.ys[e];
+      len = st.len[e];
+    }
+  }
+  // The lane's product of the current slot: its Y slot j, and whether it exists. Advances.
+  __device__ __forceinline__ bool next(const BitmapStage<THREADS>& st, uint32_t& j, uint32_t& entry) {
+    const uint32_t lane = lane_id();
+    const bool live = s < s_end;
+    const bool ok = live && t0 + lane < len;
+    j = ys + t0 + lane;
+    entry = e;
     if (live) {
-      for (unsigned m = live; m; m &= m - 1) {
-        const int i = __ffs(m) - 1;
-        {
-          const u64 pos = base + off++;
-          if (pos < a.out_cap) {
-            const u64 z = zrow + s0 + i;
-            int32_t* dst = a.coords + pos * (u64)oz;
-            if (oz == 4 && a.op.pow2 && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-              int4 cv;
-              cv.x = (int32_t)((z >> a.op.shift[0]) & (a.op.mod[0] - 1));
-              cv.y = (int32_t)((z >> a.op.shift[1]) & (a.op.mod[1] - 1));
-              cv.z = (int32_t)((z >> a.op.shift[2]) & (a.op.mod[2] - 1));
-              cv.w = (int32_t)((z >> a.op.shift[3]) & (a.op.mod[3] - 1));
-              __stcs(reinterpret_cast<int4*>(dst), cv);
-            } else {
-              for (int qq = 0; qq < oz; qq++) __stcs(dst + qq, out_coord(z, a.op, qq));
+      s++;
+      t0 += 32;
+      if (t0 >= len && s < s_end) {
+        t0 = 0;
+        do {
+          e++;
+          len = st.len[e];
+        } while (len == 0);
+        ys = st.ys[e];
+      }
+    }
+    return ok;
+  }
+};
+
+// One product slot as the slot table holds it: the Y slot of lane 0, and the staged entry
+// (high 16 bits) with the number of live lanes (low 16 bits).
+__device__ __forceinline__ bool slot_lane(uint2 rec, uint32_t lane, uint32_t& j, uint32_t& e) {
+  const bool ok = lane < (rec.y & 0xffffu);
+  j = rec.x + (ok ? lane : 0u);
+  e = rec.y >> 16;
+  return ok;
+}
+
+template <int THREADS, int U1, int U2>
+__global__ void __launch_bounds__(THREADS, 2) group_bitmap_kernel(GroupArgs a, const uint32_t* __restrict__ yoff,
+                                                                  uint32_t nseg, uint32_t seg,
+                                                                  const uint32_t* __restrict__ list, uint32_t count) {
+  constexpr int NW = THREADS / 32;
+  constexpr uint32_t vcap = bitmap_vcap<THREADS>();
+  constexpr uint32_t uni_words = (uint32_t)(kBitmapUnion / 4);
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t nwords = seg >> 5;
+  uint2* const bw = reinterpret_cast<uint2*>(smem);
+  unsigned char* const uni = smem + (size_t)kBitmapWords * 8;
+  uint32_t* const first = reinterpret_cast<uint32_t*>(uni);             // protocol mode
+  uint32_t* const repmask = reinterpret_cast<uint32_t*>(uni);           // table mode: [kSlotCap]
+  double* const rep_v = reinterpret_cast<double*>(uni + kSlotCap * 4);  // [kRepCap]
+  uint32_t* const rep_r = reinterpret_cast<uint32_t*>(uni + kSlotCap * 4 + kRepCap * 8);  // [kRepCap]
+  uint2* const stab = reinterpret_cast<uint2*>(uni + kBitmapUnion);
+  double* const zv = reinterpret_cast<double*>(smem + kBitmapFixed);
+  uint16_t* const zk = reinterpret_cast<uint16_t*>(smem + kBitmapFixed + (size_t)vcap * 8);
+  BitmapStage<THREADS>& st = *reinterpret_cast<BitmapStage<THREADS>*>(smem + kBitmapFixed + (size_t)vcap * 10);
+  __shared__ u64 warp_tot[NW];
+  __shared__ OutTarget tg;
+  __shared__ u64 gbase;
+  __shared__ uint32_t s_n, s_reps, s_queued;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint64_t keep = policy_evict_last();
+  const uint64_t pol = policy_evict_first();
+  const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
+  u64 my_base = 0;
+  for (uint32_t i = threadIdx.x; i < nwords; i += THREADS) bw[i] = make_uint2(0, 0);
+  for (uint32_t i = threadIdx.x; i < uni_words; i += THREADS) first[i] = 0;
+  // Prefetched staging of the next group (when it fits one chunk): its X entries' contract
+  // keys and values, and with a single segment their runs.
+  uint32_t pf_g = 0, pf_x0 = 0, pf_x1 = 0, pf_ck = 0, pf_ys = 0, pf_len = 0;
+  double pf_v = 0.0;
+  auto prefetch = [&](uint32_t gi) {
+    if (gi >= count) return;
+    pf_g = list[gi];
+    pf_x0 = a.goff[pf_g];
+    pf_x1 = a.goff[pf_g + 1];
+    if (pf_x1 - pf_x0 <= (uint32_t)THREADS && threadIdx.x < pf_x1 - pf_x0) {
+      pf_ck = a.gx.ck[pf_x0 + threadIdx.x];
+      pf_v = a.gx.v[pf_x0 + threadIdx.x];
+      if (nseg == 1) {
+        pf_ys = __ldg(yoff + pf_ck);
+        pf_len = __ldg(yoff + pf_ck + 1) - pf_ys;
+      }
+    }
+  };
+  prefetch(blockIdx.x);
+  for (uint32_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
+    const uint32_t g = pf_g, x0 = pf_x0, x1 = pf_x1;
+    const bool one_chunk = x1 - x0 <= (uint32_t)THREADS;
+    if (threadIdx.x == 0) resolve_target(a, g, 0, tg);
+    if (one_chunk && threadIdx.x < x1 - x0) {
+      st.ck[threadIdx.x] = pf_ck;
+      st.v[threadIdx.x] = pf_v;
+    }
+    const uint32_t r_ys = pf_ys, r_len = pf_len;
+    bool fetched = false;
+    for (uint32_t q = 0; q < nseg; q++) {
+      // ---- pass 1: mark the free keys of the segment's products.
+      uint32_t seg_slots = 0;
+      bool table = false;
+      for (uint32_t c0 = x0; c0 < x1; c0 += THREADS) {
+        const uint32_t n = (x1 - c0 < (uint32_t)THREADS) ? x1 - c0 : (uint32_t)THREADS;
+        if (!one_chunk) {
+          __syncthreads();
+          if (threadIdx.x < n) {
+            st.ck[threadIdx.x] = a.gx.ck[c0 + threadIdx.x];
+            st.v[threadIdx.x] = a.gx.v[c0 + threadIdx.x];
+          }
+        }
+        const uint32_t total =
+            bitmap_runs<THREADS>(st, warp_tot, yoff, nseg, q, n, one_chunk && nseg == 1, r_ys, r_len);
+        seg_slots += total;
+        if (total == 0) continue;
+        table = one_chunk && total <= kSlotCap;
+        if (table) {
+          if (threadIdx.x < n) {
+            const uint32_t s0 = st.sstart[threadIdx.x], ys = st.ys[threadIdx.x], len = st.len[threadIdx.x];
+            for (uint32_t k = 0; k * 32 < len; k++) {
+              const uint32_t live = len - k * 32 < 32 ? len - k * 32 : 32;
+              stab[s0 + k] = make_uint2(ys + k * 32, (threadIdx.x << 16) | live);
             }
-            __stcs(a.vals + pos, acc[s0 + i]);
-          } else {
-            atomicOr(a.status, kStatOutOverflow);
+          }
+          if (threadIdx.x == 0) s_reps = 0;
+          __syncthreads();
+          for (uint32_t sb = warp; sb < total; sb += NW * U1) {
+            uint32_t fk[U1];
+            bool ok[U1];
+#pragma unroll
+            for (int u = 0; u < U1; u++) {
+              const uint32_t s = sb + u * NW;
+              ok[u] = false;
+              if (s < total) {
+                uint32_t j, e;
+                ok[u] = slot_lane(stab[s], lane, j, e);
+                fk[u] = ld_keep_u32(yfk + j, keep) & (seg - 1);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < U1; u++) {
+              const uint32_t s = sb + u * NW;
+              if (s < total) {
+                bool rep = false;
+                if (ok[u]) {
+                  const uint32_t bit = 1u << (fk[u] & 31);
+                  rep = (atomicOr(&bw[fk[u] >> 5].x, bit) & bit) != 0;
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, rep);
+                if (lane == 0) {
+                  repmask[s] = m;
+                  if (m) atomicAdd(&s_reps, (uint32_t)__popc(m));
+                }
+              }
+            }
+          }
+        } else {
+          SlotWalk<THREADS> sw;
+          sw.seek(st, n, total);
+          while (__any_sync(0xffffffffu, sw.s < sw.s_end)) {
+            uint32_t fk[U1];
+            bool ok[U1];
+#pragma unroll
+            for (int u = 0; u < U1; u++) {
+              uint32_t j, e;
+              ok[u] = sw.next(st, j, e);
+              if (ok[u]) fk[u] = ld_keep_u32(yfk + j, keep) & (seg - 1);
+            }
+#pragma unroll
+            for (int u = 0; u < U1; u++)
+              if (ok[u]) atomicOr(&bw[fk[u] >> 5].x, 1u << (fk[u] & 31));
           }
         }
       }
-      *reinterpret_cast<uint4*>(tag + s0) = make_uint4(0, 0, 0, 0);
-    }
-  }
-  __syncthreads();
-}
-
-// Persistent over the group list; every group is swept one free-key segment at a time.
-template <int THREADS, int D>
-__global__ void __launch_bounds__(THREADS) group_dense_kernel(GroupArgs a, const uint32_t* __restrict__ yoff,
-                                                              uint32_t nseg, uint32_t seg,
-                                                              const uint32_t* __restrict__ list, uint32_t count) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  double* acc = reinterpret_cast<double*>(smem);
-  uint16_t* tag = reinterpret_cast<uint16_t*>(acc + kDenseSeg);
-  DenseChunk<THREADS>& c = *reinterpret_cast<DenseChunk<THREADS>*>(tag + kDenseSeg);
-  __shared__ u64 warp_tot[THREADS / 32];
-  __shared__ unsigned winners, cursor;
-  __shared__ u64 gbase;
-  for (uint32_t i = threadIdx.x; i < kDenseSeg / 8; i += THREADS)
-    reinterpret_cast<uint4*>(tag)[i] = make_uint4(0, 0, 0, 0);
-  if (threadIdx.x == 0) winners = 0;
-  __syncthreads();
-  for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
-    const uint32_t g = list[k];
-    const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
-    const bool one_chunk = x1 - x0 <= (uint32_t)THREADS;
-    if (one_chunk) dense_stage<THREADS>(a, c, x0, x1 - x0);
-    for (uint32_t q = 0; q < nseg; q++) {
-      for (uint32_t c0 = x0; c0 < x1; c0 += THREADS) {
-        const uint32_t n = (x1 - c0 < (uint32_t)THREADS) ? x1 - c0 : (uint32_t)THREADS;
-        if (!one_chunk) dense_stage<THREADS>(a, c, c0, n);
-        dense_expand<THREADS, D>(a, c, warp_tot, yoff, nseg, q, seg, n, acc, tag, &winners);
+      if (seg_slots == 0) continue;
+      __syncthreads();
+      // ---- ranks: exclusive scan of the words' population counts (a few consecutive words
+      // per thread, then a block scan of the per-thread sums); one atomic reserves the outputs.
+      {
+        const uint32_t wpt = (nwords + THREADS - 1) / THREADS;
+        const uint32_t w0 = threadIdx.x * wpt;
+        const uint32_t w1 = w0 + wpt < nwords ? w0 + wpt : nwords;
+        uint32_t sum = 0;
+        for (uint32_t w = w0; w < w1; w++) sum += __popc(bw[w].x);
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          const uint32_t t = (int)lane < NW ? (uint32_t)warp_tot[lane] : 0u;
+          uint32_t inc = t;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((int)lane >= o) inc += y;
+          }
+          if ((int)lane < NW) warp_tot[lane] = inc - t;
+          if (lane == 31) {
+            s_n = inc;
+            s_queued = 0;
+            my_base = inc ? atomicAdd(tg.counter, (u64)inc) : 0;  // consumed after pass 2
+          }
+        }
+        __syncthreads();
+        uint32_t rank = (uint32_t)warp_tot[warp] + x - sum;
+        for (uint32_t w = w0; w < w1; w++) {
+          bw[w].y = rank;
+          rank += __popc(bw[w].x);
+        }
+      }
+      // The next group's staging loads are issued here and land during pass 2 and the write.
+      if (q + 1 == nseg) {
+        prefetch(gi + gridDim.x);
+        fetched = true;
+      }
+      __syncthreads();
+      const uint32_t nkeys = s_n;
+      const u64 zseg = tg.zrow + (u64)q * seg;
+      const uint32_t tslots = st.sstart[THREADS];
+      const bool queue = table && s_reps <= kRepCap && nkeys <= vcap;
+      if (table && !queue) {
+        for (uint32_t i = threadIdx.x; i < uni_words; i += THREADS) first[i] = 0;
         __syncthreads();
       }
-      dense_write<THREADS>(a, g, q, seg, acc, tag, &winners, &cursor, &gbase);
+      for (uint32_t r0 = 0; r0 < nkeys; r0 += vcap) {
+        const uint32_t wn = nkeys - r0 < vcap ? nkeys - r0 : vcap;
+        // ---- pass 2: accumulate the products whose rank falls in [r0, r0 + wn).
+        if (queue) {
+          // First products store; repeats are queued and added after the barrier.
+          for (uint32_t sb = warp; sb < tslots; sb += NW * U2) {
+#pragma unroll
+            for (int u = 0; u < U2; u++) {
+              const uint32_t s = sb + u * NW;
+              if (s < tslots) {
+                uint32_t j, e;
+                const bool ok = slot_lane(stab[s], lane, j, e);
+                const uint32_t rm = repmask[s];
+                const uint32_t f = ld_keep_u32(yfk + j, keep) & (seg - 1);
+                const double prod = __dmul_rn(st.v[e], ld_keep_f64(a.yv + j, keep));
+                const uint2 wd = bw[f >> 5];
+                const uint32_t bit = 1u << (f & 31);
+                const uint32_t r = wd.y + __popc(wd.x & (bit - 1));
+                const bool rep = (rm >> lane) & 1u;
+                if (ok && !rep) {
+                  zv[r] = prod;
+                  zk[r] = (uint16_t)f;
+                }
+                if (rm) {
+                  const uint32_t at = warp_reserve(rep, &s_queued);
+                  if (rep) {
+                    rep_r[at] = r;
+                    rep_v[at] = prod;
+                  }
+                }
+              }
+            }
+          }
+          __syncthreads();
+          const uint32_t nq = s_queued;
+          for (uint32_t i = threadIdx.x; i < nq; i += THREADS) atomicAdd(zv + rep_r[i], rep_v[i]);
+        } else {
+          for (uint32_t c0 = x0; c0 < x1; c0 += THREADS) {
+            const uint32_t n = (x1 - c0 < (uint32_t)THREADS) ? x1 - c0 : (uint32_t)THREADS;
+            uint32_t total = tslots;
+            if (!one_chunk) {
+              __syncthreads();
+              if (threadIdx.x < n) {
+                st.ck[threadIdx.x] = a.gx.ck[c0 + threadIdx.x];
+                st.v[threadIdx.x] = a.gx.v[c0 + threadIdx.x];
+              }
+              total = bitmap_runs<THREADS>(st, warp_tot, yoff, nseg, q, n, false, 0, 0);
+            }
+            if (total == 0) continue;
+            // The first product of a key (first to set its bit in `first`) stores; the others
+            // add after the round's barrier. Every warp runs the same number of rounds.
+            SlotWalk<THREADS> sw;
+            if (!table) sw.seek(st, n, total);
+            const uint32_t per = (total + NW - 1) / NW;
+            const uint32_t rounds = (per + U2 - 1) / U2;
+            for (uint32_t rd = 0; rd < rounds; rd++) {
+              uint32_t slot[U2];
+              double prod[U2];
+              bool later[U2];
+#pragma unroll
+              for (int u = 0; u < U2; u++) {
+                uint32_t j = 0, e = 0;
+                bool ok = false;
+                later[u] = false;
+                if (table) {
+                  const uint32_t s = warp + NW * (rd * U2 + u);
+                  if (s < total) ok = slot_lane(stab[s], lane, j, e);
+                } else {
+                  ok = sw.next(st, j, e);
+                }
+                if (ok) {
+                  const uint32_t f = ld_keep_u32(yfk + j, keep) & (seg - 1);
+                  prod[u] = __dmul_rn(st.v[e], ld_keep_f64(a.yv + j, keep));
+                  const uint2 wd = bw[f >> 5];
+                  const uint32_t bit = 1u << (f & 31);
+                  slot[u] = wd.y + __popc(wd.x & (bit - 1)) - r0;
+                  if (slot[u] < wn) {
+                    if (atomicOr(first + (f >> 5), bit) & bit) {
+                      later[u] = true;
+                    } else {
+                      zv[slot[u]] = prod[u];
+                      zk[slot[u]] = (uint16_t)f;
+                    }
+                  }
+                }
+              }
+              __syncthreads();
+#pragma unroll
+              for (int u = 0; u < U2; u++)
+                if (later[u]) atomicAdd(zv + slot[u], prod[u]);
+            }
+          }
+        }
+        if (threadIdx.x == 31) gbase = my_base;
+        __syncthreads();
+        // ---- write the window: consecutive threads, consecutive output positions.
+        const u64 pbase = gbase + r0;
+        const u64 cap = tg.cap;
+        int32_t* const coords = tg.coords;
+        double* const vals = tg.vals;
+        if (tg.op.order == 4 && tg.op.pow2 && ((reinterpret_cast<uintptr_t>(coords) & 15u) == 0)) {
+          // Coordinates are below 2^31: 32-bit masks.
+          const uint32_t s0 = tg.op.shift[0], s1 = tg.op.shift[1], s2 = tg.op.shift[2], s3 = tg.op.shift[3];
+          const uint32_t m0 = (uint32_t)tg.op.mod[0] - 1, m1 = (uint32_t)tg.op.mod[1] - 1,
+                         m2 = (uint32_t)tg.op.mod[2] - 1, m3 = (uint32_t)tg.op.mod[3] - 1;
+          for (uint32_t i = threadIdx.x; i < wn; i += THREADS) {
+            const u64 pos = pbase + i;
+            const u64 z = zseg + zk[i];
+            if (pos < cap) {
+              const int4 cv = make_int4((int32_t)((uint32_t)(z >> s0) & m0), (int32_t)((uint32_t)(z >> s1) & m1),
+                                        (int32_t)((uint32_t)(z >> s2) & m2), (int32_t)((uint32_t)(z >> s3) & m3));
+              st_stream_v4(coords + pos * 4, cv, pol);
+              st_stream_f64(vals + pos, zv[i], pol);
+            } else {
+              atomicOr(a.status, kStatOutOverflow);
+            }
+          }
+        } else {
+          for (uint32_t i = threadIdx.x; i < wn; i += THREADS) {
+            const u64 pos = pbase + i;
+            if (pos < cap)
+              store_output(coords, vals, pos, zseg + zk[i], zv[i], tg.op, pol);
+            else
+              atomicOr(a.status, kStatOutOverflow);
+          }
+        }
+        if (r0 + vcap < nkeys) __syncthreads();
+      }
+      for (uint32_t i = threadIdx.x; i < nwords; i += THREADS) bw[i] = make_uint2(0, 0);
+      for (uint32_t i = threadIdx.x; i < uni_words; i += THREADS) first[i] = 0;
+      __syncthreads();
+    }
+    if (!fetched) prefetch(gi + gridDim.x);
+  }
+}
+
+
+// ---- product stash: groups whose product count fits the stash (the common case of the
+// bitmap path). Pass 1 forms every product once (Y key and value read together, one round
+// trip) and marks its free key in a bitmap over the segment: the first product of a key is
+// the one that finds its bit clear. First products take consecutive places at the front of
+// the stash (their order is the group's output order); repeats take places from the back
+// and mark their key in a second bitmap. After pass 1 the group's output count is the number
+// of first products, reserved with one atomic. First products of keys that never repeat are
+// written out at once; repeated keys are ranked by a scan over the second bitmap, their first
+// products record their place in a rank-indexed map, every repeat adds its value there, and
+// those outputs are written last. Products are enumerated in slots of up to 32 consecutive Y
+// entries of one X entry's run (one per lane, coalesced), listed in a slot table.
+
+constexpr int kStashThreads = 512;
+constexpr uint32_t kStashMaxEntries = kStashThreads;  // X entries staged per chunk
+// Shared memory (widest segment, kBitmapWords words), in order: key bitmap, repeat bitmap,
+// slot table, X values of the chunk, then per product a value, a key and a map byte pair
+// for every two products (repeat rank -> place of the key's first product).
+__host__ __device__ constexpr uint32_t stash_slots(uint32_t cap) { return cap / 32 + kStashMaxEntries; }
+__host__ __device__ constexpr size_t stash_smem(uint32_t cap) {
+  return (size_t)kBitmapWords * 8 + (size_t)stash_slots(cap) * 8 + (size_t)kStashMaxEntries * 8 +
+         (size_t)cap * 10 + (size_t)cap;
+}
+__host__ __device__ constexpr uint32_t stash_cap() {
+  uint32_t c = 16384;
+  while (stash_smem(c) > kBitmapSmemPerCta - 256) c -= 32;
+  return c;
+}
+constexpr uint32_t kStashCap = stash_cap();  // products of one group segment
+constexpr uint32_t kStashSlots = stash_slots(kStashCap);
+constexpr size_t kStashSmem = stash_smem(kStashCap);
+static_assert(kStashCap >= 4096 && kStashCap < 65536 && kStashCap % 32 == 0, "stash capacity");
+
+// Block-wide exclusive scan of one u32 per thread (THREADS threads); returns the exclusive
+// prefix and sets *total. Two barriers; warp_tot must hold THREADS / 32 + 1 entries.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exscan_u32(uint32_t v, uint32_t* total, u64* warp_tot) {
+  constexpr int NW = THREADS / 32;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if ((int)lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const uint32_t t = (int)lane < NW ? (uint32_t)warp_tot[lane] : 0u;
+    uint32_t inc = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if ((int)lane >= o) inc += y;
+    }
+    if ((int)lane < NW) warp_tot[lane] = inc - t;
+    if (lane == 31) warp_tot[NW] = inc;
+  }
+  __syncthreads();
+  *total = (uint32_t)warp_tot[NW];
+  return (uint32_t)warp_tot[warp] + x - v;
+}
+
+template <int U>
+__global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs a, const uint32_t* __restrict__ yoff,
+                                                                      uint32_t nseg, uint32_t seg,
+                                                                      const uint32_t* __restrict__ list,
+                                                                      uint32_t count) {
+  constexpr int T = kStashThreads, NW = T / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t nwords = seg >> 5;
+  uint32_t* const bits = reinterpret_cast<uint32_t*>(smem);             // key marks, then repeat ranks
+  uint32_t* const rbits = bits + kBitmapWords;                          // keys met again
+  uint2* const stab = reinterpret_cast<uint2*>(rbits + kBitmapWords);  // slot table
+  double* const sx = reinterpret_cast<double*>(stab + kStashSlots);    // X values of the chunk
+  double* const pv = sx + kStashMaxEntries;                             // stashed products
+  uint16_t* const pk = reinterpret_cast<uint16_t*>(pv + kStashCap);    // stashed keys
+  uint16_t* const map = pk + kStashCap;                                 // repeat rank -> first place
+  __shared__ u64 warp_tot[NW + 1];
+  __shared__ OutTarget tg;
+  __shared__ u64 s_gbase;
+  __shared__ uint32_t s_nf, s_nr;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t lt = lanemask_lt();
+  const uint64_t keep = policy_evict_last();
+  const uint64_t pol = policy_evict_first();
+  const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
+  for (uint32_t i = threadIdx.x; i < 2 * kBitmapWords; i += T) bits[i] = 0;
+  if (threadIdx.x == 0) s_nf = s_nr = 0;
+  // Prefetched staging of the next group (when it fits one chunk).
+  uint32_t pf_g = 0, pf_x0 = 0, pf_x1 = 0, pf_ck = 0;
+  double pf_v = 0.0;
+  auto prefetch = [&](uint32_t gi) {
+    if (gi >= count) return;
+    pf_g = list[gi];
+    pf_x0 = a.goff[pf_g];
+    pf_x1 = a.goff[pf_g + 1];
+    if (pf_x1 - pf_x0 <= (uint32_t)T && threadIdx.x < pf_x1 - pf_x0) {
+      pf_ck = a.gx.ck[pf_x0 + threadIdx.x];
+      pf_v = a.gx.v[pf_x0 + threadIdx.x];
+    }
+  };
+  prefetch(blockIdx.x);
+  for (uint32_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
+    const uint32_t g = pf_g, x0 = pf_x0, x1 = pf_x1;
+    const bool one_chunk = x1 - x0 <= (uint32_t)T;
+    if (threadIdx.x == 0) resolve_target(a, g, 0, tg);
+    const uint32_t my_ck = pf_ck;
+    const double my_v = pf_v;
+    prefetch(gi + gridDim.x);
+    for (uint32_t q = 0; q < nseg; q++) {
+      // ---- pass 1, one chunk of X entries at a time.
+      for (uint32_t c0 = x0; c0 < x1; c0 += T) {
+        const uint32_t n = (x1 - c0 < (uint32_t)T) ? x1 - c0 : (uint32_t)T;
+        uint32_t ys = 0, len = 0;
+        if (threadIdx.x < n) {
+          const uint32_t ck = one_chunk ? my_ck : a.gx.ck[c0 + threadIdx.x];
+          sx[threadIdx.x] = one_chunk ? my_v : a.gx.v[c0 + threadIdx.x];
+          const u64 b = (u64)ck * nseg + q;
+          ys = __ldg(yoff + b);
+          len = __ldg(yoff + b + 1) - ys;
+        }
+        uint32_t S;
+        uint32_t s = block_exscan_u32<T>((len + 31) >> 5, &S, warp_tot);
+        if (threadIdx.x < n) {
+          for (uint32_t k = 0; k < len; k += 32, s++) {
+            const uint32_t live = len - k < 32 ? len - k : 32;
+            stab[s] = make_uint2(ys + k, live | (threadIdx.x << 8));
+          }
+        }
+        __syncthreads();
+        for (uint32_t sb = warp; sb < S; sb += NW * U) {
+          uint32_t f[U];
+          double prod[U];
+          bool ok[U];
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            const uint32_t si = sb + u * NW;
+            ok[u] = false;
+            if (si < S) {
+              const uint2 rec = stab[si];
+              ok[u] = lane < (rec.y & 255u);
+              const uint32_t j = rec.x + (ok[u] ? lane : 0u);
+              f[u] = ld_keep_u32(yfk + j, keep) & (seg - 1);
+              prod[u] = __dmul_rn(sx[rec.y >> 8], ld_keep_f64(a.yv + j, keep));
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            if (sb + u * NW < S) {
+              const uint32_t w = f[u] >> 5, bit = 1u << (f[u] & 31);
+              bool first = false;
+              if (ok[u]) {
+                first = (atomicOr(bits + w, bit) & bit) == 0;
+                if (!first) atomicOr(rbits + w, bit);
+              }
+              const uint32_t fm = __ballot_sync(0xffffffffu, first);
+              const uint32_t rm = __ballot_sync(0xffffffffu, ok[u] && !first);
+              uint32_t base = 0;
+              if (lane == 0 && fm) base = atomicAdd(&s_nf, (uint32_t)__popc(fm));
+              if (lane == 1 && rm) base = atomicAdd(&s_nr, (uint32_t)__popc(rm));
+              const uint32_t bf = __shfl_sync(0xffffffffu, base, 0);
+              const uint32_t br = __shfl_sync(0xffffffffu, base, 1);
+              if (ok[u]) {
+                const uint32_t at = first ? bf + __popc(fm & lt) : kStashCap - 1 - (br + __popc(rm & lt));
+                pk[at] = (uint16_t)f[u];
+                pv[at] = prod[u];
+              }
+            }
+          }
+        }
+        if (!one_chunk) __syncthreads();
+      }
+      __syncthreads();
+      const uint32_t nkeys = s_nf, reps = s_nr;
+      if (nkeys == 0) continue;
+      // Thread 31 reserves the outputs; the result is published by the barrier before the write.
+      u64 my_base = 0;
+      if (threadIdx.x == 31) my_base = atomicAdd(tg.counter, (u64)nkeys);
+      uint32_t nrep_keys = 0;
+      if (reps) {
+        // Rank the repeated keys; the key marks are no longer needed and hold the ranks.
+        const uint32_t wpt = (nwords + T - 1) / T;
+        const uint32_t w0 = threadIdx.x * wpt, w1 = w0 + wpt < nwords ? w0 + wpt : nwords;
+        uint32_t sum = 0;
+        for (uint32_t w = w0; w < w1; w++) sum += __popc(rbits[w]);
+        uint32_t r = block_exscan_u32<T>(sum, &nrep_keys, warp_tot);
+        for (uint32_t w = w0; w < w1; w++) {
+          bits[w] = r;
+          r += __popc(rbits[w]);
+        }
+      }
+      if (threadIdx.x == 31) s_gbase = my_base;
+      __syncthreads();
+      const u64 gb = s_gbase;
+      const u64 zseg = tg.zrow + (u64)q * seg;
+      const u64 cap = tg.cap;
+      int32_t* const coords = tg.coords;
+      double* const vals = tg.vals;
+      const bool v4 = tg.op.order == 4 && tg.op.pow2 && ((reinterpret_cast<uintptr_t>(coords) & 15u) == 0);
+      const uint32_t s0 = tg.op.shift[0], s1 = tg.op.shift[1], s2 = tg.op.shift[2], s3 = tg.op.shift[3];
+      const uint32_t m0 = (uint32_t)tg.op.mod[0] - 1, m1 = (uint32_t)tg.op.mod[1] - 1,
+                     m2 = (uint32_t)tg.op.mod[2] - 1, m3 = (uint32_t)tg.op.mod[3] - 1;
+      auto write = [&](uint32_t i) {
+        const u64 pos = gb + i;
+        const u64 z = zseg + pk[i];
+        if (pos >= cap) {
+          atomicOr(a.status, kStatOutOverflow);
+        } else if (v4) {
+          // Coordinates are below 2^31: 32-bit masks.
+          const int4 cv = make_int4((int32_t)((uint32_t)(z >> s0) & m0), (int32_t)((uint32_t)(z >> s1) & m1),
+                                    (int32_t)((uint32_t)(z >> s2) & m2), (int32_t)((uint32_t)(z >> s3) & m3));
+          st_stream_v4(coords + pos * 4, cv, pol);
+          st_stream_f64(vals + pos, pv[i], pol);
+        } else {
+          store_output(coords, vals, pos, z, pv[i], tg.op, pol);
+        }
+      };
+      // ---- write the keys met once; record the places of repeated keys' first products.
+      for (uint32_t i = threadIdx.x; i < nkeys; i += T) {
+        if (reps) {
+          const uint32_t f = pk[i], w = f >> 5, bit = 1u << (f & 31), rw = rbits[w];
+          if (rw & bit) {
+            map[bits[w] + __popc(rw & (bit - 1))] = (uint16_t)i;
+            continue;
+          }
+        }
+        write(i);
+      }
+      if (reps) {
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < reps; k += T) {
+          const uint32_t at = kStashCap - 1 - k;
+          const uint32_t f = pk[at], w = f >> 5, bit = 1u << (f & 31);
+          atomicAdd(pv + map[bits[w] + __popc(rbits[w] & (bit - 1))], pv[at]);
+        }
+        __syncthreads();
+        for (uint32_t r = threadIdx.x; r < nrep_keys; r += T) write(map[r]);
+      }
+      // ---- clear the bitmaps for the next segment or group.
+      for (uint32_t i = threadIdx.x; i < nwords / 4; i += T) {
+        reinterpret_cast<uint4*>(bits)[i] = make_uint4(0, 0, 0, 0);
+        reinterpret_cast<uint4*>(rbits)[i] = make_uint4(0, 0, 0, 0);
+      }
+      if (nwords < 4 && threadIdx.x < nwords) bits[threadIdx.x] = rbits[threadIdx.x] = 0;
+      if (threadIdx.x == 0) s_nf = s_nr = 0;
+      __syncthreads();
     }
   }
 }
@@ -1093,22 +1621,45 @@ cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct
   return cudaSuccess;
 }
 
+uint32_t dense_stash_cap() { return kStashCap; }
+
 cudaError_t launch_group_dense(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
-                               const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
-  if (count == 0) return cudaSuccess;
-  constexpr int T = 512, D = 4;
-  const size_t smem = kDenseSeg * (sizeof(double) + sizeof(uint16_t)) + sizeof(DenseChunk<T>);
-  auto kern = group_dense_kernel<T, D>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  const uint32_t cap = (uint32_t)(sms * per_sm);
-  kern<<<count < cap ? count : cap, T, smem, s>>>(a, yoff, nseg, seg, list, count);
-  note_launch();
-  return cudaGetLastError();
+                               const uint32_t* stash_list, uint32_t stash_count, const uint32_t* rank_list,
+                               uint32_t rank_count, int sms, cudaStream_t s) {
+  if (seg < 64 || seg > kDenseSeg) return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  if (stash_count) {
+    constexpr int U = 4;
+    auto kern = group_stash_kernel<U>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStashSmem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStashThreads, kStashSmem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t cap = (uint32_t)(sms * per_sm);
+    kern<<<stash_count < cap ? stash_count : cap, kStashThreads, kStashSmem, s>>>(a, yoff, nseg, seg, stash_list,
+                                                                                  stash_count);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (rank_count) {
+    constexpr int T = 512, U1 = 4, U2 = 2;
+    static_assert(bitmap_smem<T>() <= kBitmapSmemPerCta && bitmap_vcap<T>() >= 4096, "bitmap layout");
+    const size_t smem = bitmap_smem<T>();
+    auto kern = group_bitmap_kernel<T, U1, U2>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t cap = (uint32_t)(sms * per_sm);
+    kern<<<rank_count < cap ? rank_count : cap, T, smem, s>>>(a, yoff, nseg, seg, rank_list, rank_count);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s) {

@@ -102,6 +102,7 @@ struct GroupedX {
 // Output of the binning pass.
 struct Bins {
   int nclasses;
+  int by_products;            // classify by B_g itself instead of t = min(B_g, F_Y)
   u64 tmax[kMaxClasses];      // a group goes to the first class with t <= tmax
   uint32_t* list[kMaxClasses];
   uint32_t* count;            // [kMaxClasses + 1]; the last entry counts overflow groups
@@ -224,11 +225,16 @@ cudaError_t launch_batch_prepare(const BatchArgs& ba, int sms, cudaStream_t s);
 cudaError_t launch_batch_group(const BatchArgs& ba, GroupedX gx, const Bins& b, uint32_t* gprob, u64* gfk, int sms,
                                cudaStream_t s);
 
-// Dense-row accumulation: each group's outputs are accumulated one free-key segment at a time
-// in a dense shared-memory array indexed by the free key. `yoff` are the per-(contract key,
-// segment) run offsets; seg is the segment width (a power of two, at most kDenseSeg).
-constexpr uint32_t kDenseSeg = 8192;
+// Bitmap-row accumulation: each group's outputs are found one free-key segment at a time
+// through a bitmap over the segment's free keys. `yoff` are the per-(contract key, segment)
+// run offsets; seg is the segment width (a power of two, 64 <= seg <= kDenseSeg). Groups
+// with at most dense_stash_cap() products (per segment) go to the stash kernel, the others
+// to the rank kernel.
+constexpr uint32_t kDenseSeg = 65536;
+constexpr size_t kBitmapSmemPerCta = 112 * 1024;  // two CTAs per SM
+uint32_t dense_stash_cap();
 cudaError_t launch_group_dense(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
-                               const uint32_t* list, uint32_t count, int sms, cudaStream_t s);
+                               const uint32_t* stash_list, uint32_t stash_count, const uint32_t* rank_list,
+                               uint32_t rank_count, int sms, cudaStream_t s);
 
 }  // namespace stc

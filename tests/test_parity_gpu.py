@@ -88,10 +88,10 @@ def test_out_order_and_two_mode_pairing(mode):
     check(W.Problem(X, Y, (3, 1), (0, 2), out_order=(2, 0, 1)), **mode)
 
 
-@pytest.mark.parametrize("fy", [5, 63, 64, 4096, 8192, 10_000, 20_000, 65_536])
+@pytest.mark.parametrize("fy", [5, 63, 64, 4096, 10_000, 65_536, 65_537, 100_000, 300_000, 1_048_576])
 def test_dense_rows_segments(fy):
-    """Dense-row accumulation over Y free key spaces that are below, at and above one
-    segment, including a last segment that is only partly used."""
+    """Bitmap-row accumulation over Y free key spaces that are below, at and above one
+    segment (2^16 free keys), including a last segment that is only partly used."""
     rng = W.rng_for(7000 + fy)
     X = W.uniform_coo(rng, (40, 37), 6_000)
     Y = W.uniform_coo(rng, (37, fy), 30_000)
@@ -102,10 +102,29 @@ def test_dense_rows_segments(fy):
 def test_dense_rows_multi_chunk_groups():
     """Groups with more X entries than one CTA stages at a time (several chunks per segment)."""
     rng = W.rng_for(7100)
-    X = W.uniform_coo(rng, (3, 400), 5_000)
-    Y = W.uniform_coo(rng, (400, 9_000), 20_000)
+    X = W.uniform_coo(rng, (3, 2_000), 5_000)
+    Y = W.uniform_coo(rng, (2_000, 9_000), 20_000)
     res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2, accumulator=2)
     assert res.stats.accumulator == 2
+
+
+def test_dense_rows_rank_windows():
+    """Segments holding more distinct keys than the value array: the accumulation pass is
+    repeated per window of ranks (one chunk per group)."""
+    rng = W.rng_for(7150)
+    X = W.uniform_coo(rng, (4, 60), 200)
+    Y = W.uniform_coo(rng, (60, 65_536), 60_000)
+    res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2, accumulator=2)
+    assert res.stats.accumulator == 2 and res.nnz > 4 * 20_000
+
+
+def test_dense_rows_rank_windows_multi_chunk():
+    """Rank windows in groups of several chunks."""
+    rng = W.rng_for(7160)
+    X = W.uniform_coo(rng, (2, 1200), 2_000)
+    Y = W.uniform_coo(rng, (1200, 30_000), 40_000)
+    res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2, accumulator=2)
+    assert res.stats.accumulator == 2 and res.nnz > 2 * 10_000
 
 
 def test_dense_rows_sparse_survey():
