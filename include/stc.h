@@ -71,8 +71,10 @@ enum { STC_STRATEGY_AUTO = 0, STC_STRATEGY_GLOBAL = 1, STC_STRATEGY_GROUPED = 2 
  * group's bound (Section 4.3); where keys and output positions fit 32 bits, each output is
  * written as soon as its key is first claimed. HASH_SCAN: the same table, accumulated in
  * shared memory and written by a scan of the table after the group. DENSE: the group's output
- * row swept in segments of the Y free key space, each accumulated in a dense array indexed
- * by the free key (F_Y at most 2^20). AUTO = HASH. */
+ * row swept in segments of 2^16 Y free keys; the keys present are found with a bitmap over the
+ * segment (no hashing or probing), products are stashed in shared memory and repeated keys
+ * folded into their first product (F_Y at most 2^20). AUTO: DENSE for the groups larger than
+ * the warp-sized hash tables when F_Y <= 2^20, HASH for the others. */
 enum { STC_ACC_AUTO = 0, STC_ACC_HASH = 1, STC_ACC_DENSE = 2, STC_ACC_HASH_SCAN = 3 };
 
 typedef struct stc_opts {
@@ -96,7 +98,8 @@ typedef struct stc_stats {
   int32_t strategy;       /* STC_STRATEGY_GLOBAL or STC_STRATEGY_GROUPED */
   int32_t nstages;        /* valid entries of stage_ms when record_times was set */
   uint32_t launches;      /* CUDA kernels this call launched (memsets and copies not counted) */
-  int32_t accumulator;    /* STC_ACC_HASH or STC_ACC_DENSE when strategy is GROUPED */
+  int32_t accumulator;    /* GROUPED: STC_ACC_HASH or STC_ACC_DENSE when every group used that
+                             accumulator, STC_ACC_AUTO when both ran */
   float stage_ms[8];      /* 0 group Y, 1 survey X, 2 group X, 3 plan, 4 accumulate, 5 compact/write */
 } stc_stats;
 

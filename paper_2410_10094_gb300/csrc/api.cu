@@ -439,7 +439,7 @@ uint64_t grouped_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t P) {
 
 // Counters of the grouping and binning passes, read back with the first host sync.
 struct GroupCounters {
-  uint32_t count[kMaxClasses + 1];
+  uint32_t count[kMaxClasses + 3];
   uint32_t pad_;
   u64 huge_slots;
   u64 out_cap;
@@ -452,18 +452,15 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
                             const stc_opts& o, cudaStream_t s, StageTimer& tm, stc_result* r) {
   const int64_t nX = X->nnz;
   Plan pl = plan_in;
-  // Dense rows: F_Y is swept in segments of `seg` free keys; Y is grouped per (contract key,
-  // segment). Used on request when F_Y <= 2^20 (on the measured workloads the per-group hash
-  // tables are faster, so AUTO takes those).
+  // Bitmap rows: F_Y is swept in segments of `seg` free keys; Y is grouped per (contract key,
+  // segment). Used when F_Y <= 2^20: for every group with the bitmap accumulator, for the
+  // groups beyond the warp-sized hash classes with AUTO.
   bool dense_rows = false;
   uint32_t seg = 1, nseg = 1;
-  if (pl.FY <= (1ull << 20) && o.accumulator != STC_ACC_HASH) {
-    const double rows = (double)std::max<uint64_t>(1, std::min<uint64_t>(pl.FX, (uint64_t)std::max<int64_t>(nX, 1)));
-    const double est_row = (double)nX * (double)Y->nnz / (double)pl.K / rows;
+  if (pl.FY <= (1ull << 20) && (o.accumulator == STC_ACC_AUTO || o.accumulator == STC_ACC_DENSE)) {
     seg = (uint32_t)std::min<uint64_t>(kDenseSeg, pow2_at_least(std::max<uint64_t>(pl.FY, 64)));
     nseg = (uint32_t)((pl.FY + seg - 1) / seg);
-    dense_rows = o.accumulator == STC_ACC_DENSE && pl.K * nseg <= kMaxDirectBins;
-    (void)est_row;
+    dense_rows = pl.K * nseg <= kMaxDirectBins;
   }
   if (dense_rows) {
     pl.ky.nseg = pl.kx.nseg = nseg;
@@ -494,19 +491,18 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   STC_TRY(ar.alloc(&gx.v, (size_t)nX));
   if (dense_rows) STC_TRY(ar.alloc(&gx.ck, (size_t)nX));
   STC_TRY(ar.alloc(&gc, 1));
+  b.nclasses = ncls;
+  for (int c = 0; c < ncls; c++) {
+    b.tmax[c] = (u64)(ga * shapes[c].slots);
+    STC_TRY(ar.alloc(&b.list[c], maxg));
+  }
   if (dense_rows) {
-    b.nclasses = 2;
-    b.by_products = 1;
-    b.tmax[0] = dense_stash_cap();
-    b.tmax[1] = ~0ull;
-    STC_TRY(ar.alloc(&b.list[0], maxg));
-    STC_TRY(ar.alloc(&b.list[1], maxg));
-  } else {
-    b.nclasses = ncls;
-    for (int c = 0; c < ncls; c++) {
-      b.tmax[c] = (u64)(ga * shapes[c].slots);
-      STC_TRY(ar.alloc(&b.list[c], maxg));
-    }
+    // With AUTO, groups that fit the warp classes keep their hash tables (a bitmap sweep costs
+    // a fixed amount per segment).
+    b.dense_min = o.accumulator == STC_ACC_DENSE ? 0 : (b.tmax[1] + 1) * nseg;
+    b.stash_cap = dense_stash_cap();
+    STC_TRY(ar.alloc(&b.dense_list[0], maxg));
+    STC_TRY(ar.alloc(&b.dense_list[1], maxg));
   }
   STC_TRY(ar.alloc(&b.huge_list, maxg));
   STC_TRY(ar.alloc(&b.huge_off, maxg));
@@ -534,11 +530,12 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   tm.mark(3);
   r->stats.products = h.P;
   r->stats.survivors = h.ns;
-  uint64_t groups = 0;
-  for (int c = 0; c <= kMaxClasses; c++) groups += hg.count[c];
+  uint64_t groups = 0, dense_groups = 0;
+  for (int c = 0; c < kMaxClasses + 3; c++) groups += hg.count[c];
+  dense_groups = hg.count[kMaxClasses + 1] + hg.count[kMaxClasses + 2];
   r->stats.groups = groups;
   r->stats.table_slots = hg.huge_slots;
-  r->stats.accumulator = dense_rows ? STC_ACC_DENSE : STC_ACC_HASH;
+  r->stats.accumulator = dense_groups == 0 ? STC_ACC_HASH : (dense_groups == groups ? STC_ACC_DENSE : STC_ACC_AUTO);
   if (h.P == 0) return STC_OK;
 
   const uint64_t out_cap = hg.out_cap;
@@ -578,13 +575,14 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   a.status = &pr.ctr->status;
   a.bout = dbo;
   a.bnz = &pr.ctr->nz;
-  if (dense_rows) {
-    STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.list[0], hg.count[0], b.list[1], hg.count[1], ctx->sms, s));
-  } else {
+  {
     const bool direct = !wide && out_cap < 0xffffffffull && o.accumulator != STC_ACC_HASH_SCAN;
     STC_CUDA(launch_group_classes(a, wide, direct, b, hg.count, ctx->sms, s));
     STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
   }
+  if (dense_rows)
+    STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.dense_list[0], hg.count[kMaxClasses + 1], b.dense_list[1],
+                                hg.count[kMaxClasses + 2], ctx->sms, s));
   tm.mark(4);
   Counters h2{};
   STC_TRY(read_counters(pr, s, h2));

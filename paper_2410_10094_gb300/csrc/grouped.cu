@@ -64,10 +64,13 @@ __global__ void __launch_bounds__(kThreads) bin_groups_kernel(u64 FX, const uint
     if (lane == 0) {
       const u64 t = bnd < FY ? bnd : FY;
       my_cap += t;
-      const u64 key = b.by_products ? bnd : t;
       int c = 0;
-      while (c < b.nclasses && key > b.tmax[c]) c++;
-      if (c < b.nclasses) {
+      while (c < b.nclasses && t > b.tmax[c]) c++;
+      if (b.dense_list[0] && t >= b.dense_min) {
+        const int d = bnd <= b.stash_cap ? 0 : 1;
+        const uint32_t idx = atomicAdd(b.count + kMaxClasses + 1 + d, 1u);
+        b.dense_list[d][idx] = (uint32_t)g;
+      } else if (c < b.nclasses) {
         const uint32_t idx = atomicAdd(b.count + c, 1u);
         b.list[c][idx] = (uint32_t)g;
       } else if (t > (1ull << 30)) {
@@ -1012,7 +1015,13 @@ __global__ void __launch_bounds__(THREADS, 2) group_bitmap_kernel(GroupArgs a, c
 // those outputs are written last. Products are enumerated in slots of up to 32 consecutive Y
 // entries of one X entry's run (one per lane, coalesced), listed in a slot table.
 
-constexpr int kStashThreads = 512;
+#ifndef STASH_THREADS
+#define STASH_THREADS 512
+#endif
+#ifndef STASH_U
+#define STASH_U 4
+#endif
+constexpr int kStashThreads = STASH_THREADS;
 constexpr uint32_t kStashMaxEntries = kStashThreads;  // X entries staged per chunk
 // Shared memory (widest segment, kBitmapWords words), in order: key bitmap, repeat bitmap,
 // slot table, X values of the chunk, then per product a value, a key and a map byte pair
@@ -1088,8 +1097,9 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
   const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
   for (uint32_t i = threadIdx.x; i < 2 * kBitmapWords; i += T) bits[i] = 0;
   if (threadIdx.x == 0) s_nf = s_nr = 0;
-  // Prefetched staging of the next group (when it fits one chunk).
-  uint32_t pf_g = 0, pf_x0 = 0, pf_x1 = 0, pf_ck = 0;
+  // Prefetched staging of the next group (when it fits one chunk): its X entries' contract
+  // keys and values, and with a single segment their runs.
+  uint32_t pf_g = 0, pf_x0 = 0, pf_x1 = 0, pf_ck = 0, pf_ys = 0, pf_ye = 0;
   double pf_v = 0.0;
   auto prefetch = [&](uint32_t gi) {
     if (gi >= count) return;
@@ -1099,6 +1109,10 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
     if (pf_x1 - pf_x0 <= (uint32_t)T && threadIdx.x < pf_x1 - pf_x0) {
       pf_ck = a.gx.ck[pf_x0 + threadIdx.x];
       pf_v = a.gx.v[pf_x0 + threadIdx.x];
+      if (nseg == 1) {
+        pf_ys = __ldg(yoff + pf_ck);
+        pf_ye = __ldg(yoff + pf_ck + 1);
+      }
     }
   };
   prefetch(blockIdx.x);
@@ -1106,7 +1120,7 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
     const uint32_t g = pf_g, x0 = pf_x0, x1 = pf_x1;
     const bool one_chunk = x1 - x0 <= (uint32_t)T;
     if (threadIdx.x == 0) resolve_target(a, g, 0, tg);
-    const uint32_t my_ck = pf_ck;
+    const uint32_t my_ck = pf_ck, my_ys = pf_ys, my_ye = pf_ye;
     const double my_v = pf_v;
     prefetch(gi + gridDim.x);
     for (uint32_t q = 0; q < nseg; q++) {
@@ -1115,11 +1129,16 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
         const uint32_t n = (x1 - c0 < (uint32_t)T) ? x1 - c0 : (uint32_t)T;
         uint32_t ys = 0, len = 0;
         if (threadIdx.x < n) {
-          const uint32_t ck = one_chunk ? my_ck : a.gx.ck[c0 + threadIdx.x];
           sx[threadIdx.x] = one_chunk ? my_v : a.gx.v[c0 + threadIdx.x];
-          const u64 b = (u64)ck * nseg + q;
-          ys = __ldg(yoff + b);
-          len = __ldg(yoff + b + 1) - ys;
+          if (one_chunk && nseg == 1) {
+            ys = my_ys;
+            len = my_ye - my_ys;
+          } else {
+            const uint32_t ck = one_chunk ? my_ck : a.gx.ck[c0 + threadIdx.x];
+            const u64 b = (u64)ck * nseg + q;
+            ys = __ldg(yoff + b);
+            len = __ldg(yoff + b + 1) - ys;
+          }
         }
         uint32_t S;
         uint32_t s = block_exscan_u32<T>((len + 31) >> 5, &S, warp_tot);
@@ -1629,7 +1648,7 @@ cudaError_t launch_group_dense(const GroupArgs& a, const uint32_t* yoff, uint32_
   if (seg < 64 || seg > kDenseSeg) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (stash_count) {
-    constexpr int U = 4;
+    constexpr int U = STASH_U;
     auto kern = group_stash_kernel<U>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStashSmem);
     if (e != cudaSuccess) return e;

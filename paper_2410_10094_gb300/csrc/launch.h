@@ -102,10 +102,14 @@ struct GroupedX {
 // Output of the binning pass.
 struct Bins {
   int nclasses;
-  int by_products;            // classify by B_g itself instead of t = min(B_g, F_Y)
   u64 tmax[kMaxClasses];      // a group goes to the first class with t <= tmax
   uint32_t* list[kMaxClasses];
-  uint32_t* count;            // [kMaxClasses + 1]; the last entry counts overflow groups
+  uint32_t* count;            // [kMaxClasses + 3]: classes, overflow groups, stash, rank
+  // Bitmap-row accumulation (single contractions with per-segment runs): groups with
+  // t >= dense_min go to the stash list when B_g <= stash_cap, else to the rank list.
+  uint32_t* dense_list[2];    // null when not used
+  u64 dense_min;
+  u64 stash_cap;
   uint32_t* huge_list;        // overflow groups, their table offsets and capacities
   u64* huge_off;
   u64* huge_cap;

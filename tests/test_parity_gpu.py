@@ -11,10 +11,11 @@ from helpers import REL_TOL
 
 pytestmark = pytest.mark.gpu
 
-# one global table; per-X-free-group hash tables; per-X-free-group dense rows
+# one global table; per-X-free-group hash tables (direct output, table scan); bitmap rows for
+# every group; AUTO (bitmap rows for the large groups, hash tables for the small ones)
 MODES = [dict(strategy=1), dict(strategy=2, accumulator=1), dict(strategy=2, accumulator=3),
-         dict(strategy=2, accumulator=2)]
-MODE_IDS = ["global", "grouped-hash", "grouped-hash-scan", "grouped-dense"]
+         dict(strategy=2, accumulator=2), dict(strategy=2, accumulator=0)]
+MODE_IDS = ["global", "grouped-hash", "grouped-hash-scan", "grouped-dense", "grouped-auto"]
 STRATEGIES = [1, 2]
 
 
@@ -125,6 +126,20 @@ def test_dense_rows_rank_windows_multi_chunk():
     Y = W.uniform_coo(rng, (1200, 30_000), 40_000)
     res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2, accumulator=2)
     assert res.stats.accumulator == 2 and res.nnz > 2 * 10_000
+
+
+def test_auto_mixes_hash_and_bitmap_groups():
+    """AUTO on a row space where some groups fit the warp-sized hash tables and others do not:
+    both accumulators run in one call and the result is the oracle's."""
+    rng = W.rng_for(7170)
+    Xa = W.uniform_coo(rng, (60, 40), 300)
+    # a few long rows: every entry of X row 0..3 present
+    xc = np.concatenate([Xa.coords.reshape(-1, 2), np.array([[r, c] for r in range(4) for c in range(40)], np.int32)])
+    xc = np.unique(xc, axis=0)
+    X = W.COO((60, 40), xc.astype(np.int32), rng.uniform(-1, 1, len(xc)))
+    Y = W.uniform_coo(rng, (40, 5_000), 2_000)
+    res, ref = check(W.Problem(X, Y, (1,), (0,)), strategy=2, accumulator=0)
+    assert res.stats.accumulator == 0
 
 
 def test_dense_rows_sparse_survey():
