@@ -13,6 +13,7 @@ divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -70,34 +71,46 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples of SM clock and throttle reasons. Started before the warm-up (the tool
+    takes a moment to start); only samples that arrive inside the marked timed window count."""
 
-    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+    FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
               "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
               "clocks_event_reasons.sw_power_cap"]
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, period_ms: int = 50):
         self.device = device
+        self.period_ms = period_ms
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, line)
+        self.window = None
 
-    def __enter__(self):
+    def start(self, wait_s: float = 5.0):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(min(wait_s, 1.0))  # let the tool start before the warm-up
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
+        # The pipe is block-buffered: each sample's own timestamp (local time) places it.
         for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
+            try:
+                stamp = datetime.datetime.strptime(ln.split(",")[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            self.lines.append((stamp, ln.strip()))
 
-    def __exit__(self, *a):
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
         if self.proc:
             self.proc.terminate()
             try:
@@ -105,13 +118,16 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
             self.t.join(timeout=2)
+            self.proc = None
 
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) != len(self.FIELDS):
+        lo, hi = self.window if self.window else (float("-inf"), float("inf"))
+        inside = [ln for t, ln in self.lines if lo <= t <= hi]
+        for ln in inside:
+            parts = [p.strip() for p in ln.split(",")][1:]
+            if len(parts) != len(self.FIELDS) - 1:
                 continue
             try:
                 sm.append(float(parts[0]))
@@ -122,9 +138,10 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "no nvidia-smi sample inside the timed window"}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "period_ms": self.period_ms}
 
 
 def dist_env():
@@ -132,6 +149,12 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def l2_note(bytes_in, bytes_out, l2=129e6):
+    """How the timed steps relate to the L2 (no flush between steps)."""
+    fits = "working set exceeds" if bytes_in + bytes_out > l2 else "working set fits"
+    return f"inputs {bytes_in / 1e6:.0f} MB, output {bytes_out / 1e6:.0f} MB: {fits} the 129 MB L2; no flush"
 
 
 def alg_bytes(p, nz, oz):
@@ -324,7 +347,8 @@ def main(argv=None):
                 self.nnz = sum(r.nnz for r in rs)
                 self.order = rs[0].order
                 st = rs[0].stats
-                self.stats = type(st)(sum(r.stats.products for r in rs), 0, sum(r.stats.out_capacity for r in rs),
+                self.stats = type(st)(sum(r.stats.products for r in rs), sum(r.stats.survivors for r in rs),
+                                      sum(r.stats.out_capacity for r in rs),
                                       0, 0, st.strategy, st.launches, st.accumulator, st.stage_ms)
 
         def step(record=False):
@@ -338,9 +362,10 @@ def main(argv=None):
                                 group_load_factor=args.group_load_factor, accumulator=args.accumulator,
                                 stream=stream, ctx=ctx)
 
+    clk = ClockSampler(dev).start()
     for _ in range(args.warmup):
         r = step()
-        nz, oz, P, launches = r.nnz, r.order, r.stats.products, r.stats.launches
+        nz, oz, P, launches, ns = r.nnz, r.order, r.stats.products, r.stats.launches, r.stats.survivors
         del r
     torch.cuda.synchronize()
 
@@ -351,17 +376,19 @@ def main(argv=None):
     # ---- timed region: K device-resident steps
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stage = np.zeros(8)
-    with ClockSampler(dev) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            r = step(record=True)
-            stage[: len(r.stats.stage_ms)] += np.asarray(r.stats.stage_ms)
-            del r
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
+    barrier()
+    torch.cuda.synchronize()
+    tw0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        r = step(record=True)
+        stage[: len(r.stats.stage_ms)] += np.asarray(r.stats.stage_ms)
+        del r
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk.mark(tw0, time.time())
+    clk.stop()
+    barrier()
     ms = ev0.elapsed_time(ev1)
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -440,8 +467,8 @@ def main(argv=None):
     bytes_in = (4 * p.X.order + 8) * p.X.nnz + (4 * p.Y.order + 8) * p.Y.nnz
     kernel_bytes = {
         0: (4 * p.Y.order + 8) * p.Y.nnz + 16 * p.Y.nnz,            # read Y, write grouped Y
-        1: (4 * p.X.order + 8) * p.X.nnz,                            # read X once
-        4: 12 * p.X.nnz + 16 * p.Y.nnz + 16 * nz,                    # survivors + Y runs in, distinct outputs out
+        1: 4 * p.X.order * p.X.nnz + 32 * ns,                        # X coordinates in; survivors' values in, records out
+        4: 12 * p.X.nnz + 12 * p.Y.nnz + (4 * oz + 8) * nz,         # grouped X and Y runs in, COO output out
         5: (4 * oz + 8) * nz,                                        # write the COO output
     }.get(dom, bytes_in)
     dom_ms = per_step[dom]
@@ -464,8 +491,7 @@ def main(argv=None):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {DESCRIPTIONS[args.workload]}", "seed": seed,
                    "products_per_step": P, "nnz_out": nz, "parallelism": f"replicas x{world}",
-                   "l2": "inputs 240 MB and output 8.8 GB exceed the 129 MB L2; no flush" if args.workload ==
-                   "plain_large" else "see DESIGN.md", "strategy": args.strategy,
+                   "l2": l2_note(bytes_in, (4 * oz + 8) * nz), "strategy": args.strategy,
                    "group_load_factor": args.group_load_factor, "accumulator": args.accumulator},
         "step_hbm": {"alg_bytes": step_alg, "gbs": step_alg / (step_ms / 1e3) / 1e9,
                      "frac": step_alg / (step_ms / 1e3) / 1e9 / hbm},

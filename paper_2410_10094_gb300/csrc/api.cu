@@ -399,8 +399,10 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
     STC_TRY(ar.alloc(&pr.sv.ystart, (size_t)nX));
     STC_TRY(ar.alloc(&pr.sv.w, (size_t)nX));
     STC_TRY(ar.alloc(&pr.sv.v, (size_t)nX));
-    STC_CUDA(launch_x_survey(X->coords, X->vals, nX, pl.kx, pr.yoff, pr.sv, &pr.ctr->P, pr.gcnt, status, ctx->sms,
-                             s));
+    uint32_t* nonempty = nullptr;
+    if (pl.K <= kNonemptyMaxKeys) STC_TRY(ar.alloc(&nonempty, (size_t)((pl.K + 31) / 32)));
+    STC_CUDA(launch_x_survey(X->coords, X->vals, nX, pl.kx, pr.yoff, pl.K, pr.sv, &pr.ctr->P, pr.gcnt, status,
+                             nonempty, ctx->sms, s));
   }
   tm.mark(1);
   return STC_OK;
@@ -417,7 +419,7 @@ uint64_t global_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t ns, uint6
   const uint64_t target = std::min<uint64_t>(P, pl.F);
   const uint64_t cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)((double)target / alpha) + 1));
   const uint64_t out_cap = std::min(target, cap);
-  uint64_t b = sizeof(Counters) + pl.K * 4 * 3 + (uint64_t)scan_scratch_elems((int64_t)pl.K) * 4;
+  uint64_t b = sizeof(Counters) + pl.K * 4 * 3 + (uint64_t)scan_scratch_elems((int64_t)pl.K) * 4 + (pl.K + 31) / 32 * 4;
   b += (uint64_t)nY * 16 + (uint64_t)nX * 24;
   b += (ns + 1) * 8 + (uint64_t)scan_scratch_elems((int64_t)ns) * 8;
   b += cap * 16 + out_cap * (4ull * pl.oz + 8);
@@ -430,7 +432,7 @@ uint64_t global_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t ns, uint6
 // twice the output bound.
 uint64_t grouped_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t P) {
   const uint64_t out = std::min<uint64_t>(P, pl.F);
-  uint64_t b = sizeof(Counters) + pl.K * 4 * 3 + (uint64_t)scan_scratch_elems((int64_t)pl.K) * 4;
+  uint64_t b = sizeof(Counters) + pl.K * 4 * 3 + (uint64_t)scan_scratch_elems((int64_t)pl.K) * 4 + (pl.K + 31) / 32 * 4;
   b += (uint64_t)nY * 16 + (uint64_t)nX * (24 + 16);
   b += pl.FX * (4 * 3) + std::min<uint64_t>(pl.FX, (uint64_t)nX) * 4 * (kMaxClasses + 5);
   b += out * (4ull * pl.oz + 8);

@@ -81,6 +81,22 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
+// Contract and free keys of one coordinate row. Returns false if any coordinate is outside
+// its mode.
+template <int ORDER>
+__device__ __forceinline__ bool keys_of(const int32_t* c, const KeyPlan& p, uint64_t& ck, uint64_t& fk) {
+  bool ok = true;
+  ck = 0;
+  fk = 0;
+#pragma unroll
+  for (int j = 0; j < ORDER; j++) {
+    ok &= (c[j] >= 0) & ((int64_t)c[j] < p.size[j]);
+    ck += (uint64_t)(uint32_t)c[j] * p.cstride[j];
+    fk += (uint64_t)(uint32_t)c[j] * p.fstride[j];
+  }
+  return ok;
+}
+
 // Reads coordinate row i of a [n][ORDER] int32 array and forms its contract and free
 // keys. Returns false if any coordinate is outside its mode.
 template <int ORDER, bool VEC>
@@ -97,16 +113,7 @@ __device__ __forceinline__ bool row_keys(const int32_t* __restrict__ coords, int
 #pragma unroll
     for (int j = 0; j < ORDER; j++) c[j] = __ldg(coords + i * ORDER + j);
   }
-  bool ok = true;
-  ck = 0;
-  fk = 0;
-#pragma unroll
-  for (int j = 0; j < ORDER; j++) {
-    ok &= (c[j] >= 0) & ((int64_t)c[j] < p.size[j]);
-    ck += (uint64_t)(uint32_t)c[j] * p.cstride[j];
-    fk += (uint64_t)(uint32_t)c[j] * p.fstride[j];
-  }
-  return ok;
+  return keys_of<ORDER>(c, p, ck, fk);
 }
 
 // Output coordinate q of an output key.

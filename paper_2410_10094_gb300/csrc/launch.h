@@ -50,9 +50,13 @@ struct Survivors {
   unsigned* count;  // number of survivors (device counter)
 };
 // With gcnt non-null, also counts survivors per X free key.
+// `nonempty` (K / 32 words of scratch, may be null) is used when K <= kNonemptyMaxKeys: a
+// bitmap of the contract keys that have a Y run, held in shared memory by the survey so that
+// rows without a run skip the lookup.
+constexpr u64 kNonemptyMaxKeys = 1ull << 18;
 cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
-                            const uint32_t* yoff, Survivors sv, u64* P, uint32_t* gcnt, uint32_t* status, int sms,
-                            cudaStream_t s);
+                            const uint32_t* yoff, u64 K, Survivors sv, u64* P, uint32_t* gcnt, uint32_t* status,
+                            uint32_t* nonempty, int sms, cudaStream_t s);
 
 // Dense X (Y runs exist for most contract keys): count entries with a run per X free key
 // and the products, then place them in group order straight from the input, without an

@@ -60,6 +60,15 @@ __global__ void __launch_bounds__(kThreads) key_scatter_kernel(const u64* __rest
 // Row-streaming kernels take R rows per thread per step and issue all of their loads before
 // using any, so each thread keeps R coordinate rows (and their lookups) in flight.
 constexpr int kRows = 4;
+// Row streams over X: at least this many CTAs per SM (keeps enough rows in flight).
+#ifndef STC_X_MIN_BLOCKS
+#define STC_X_MIN_BLOCKS 4
+#endif
+constexpr int kXMinBlocks = STC_X_MIN_BLOCKS;
+#ifndef STC_STAGE_ROWS
+#define STC_STAGE_ROWS 1
+#endif
+constexpr bool kStageRows = STC_STAGE_ROWS != 0;
 
 template <int ORDER, bool VEC>
 __global__ void __launch_bounds__(kThreads) y_count_kernel(const int32_t* __restrict__ coords, int64_t n, KeyPlan p,
@@ -119,19 +128,81 @@ __global__ void __launch_bounds__(kThreads) y_scatter_kernel(const int32_t* __re
 
 // Looks up each row's Y run: lo = first slot, w = length (0 when the key has no run or the
 // row is invalid). Invalid coordinates raise kStatCoordRange.
+// The coordinates of a warp's block of rows [base, base + 32 * kRows), read with 16-byte
+// loads of the whole block (coalesced whatever the order) and handed out through shared
+// memory: lane l receives rows base + l + 32 r.
+template <int ORDER>
+__device__ __forceinline__ void stage_rows(const int32_t* __restrict__ coords, int64_t base, int64_t n,
+                                           int32_t (&c)[kRows][ORDER]) {
+  constexpr int kInts = 32 * kRows * ORDER;
+  __shared__ __align__(16) int32_t buf[kThreads / 32][kInts];
+  int32_t* wb = buf[threadIdx.x >> 5];
+  const int lane = (int)lane_id();
+  const int rows = n - base < 32 * kRows ? (int)(n - base) : 32 * kRows;
+  const int total = rows * ORDER;
+  const int32_t* src = coords + base * ORDER;
+  int k0 = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+    const int nv = total >> 2;
+    int4 t[(kInts / 4 + 31) / 32];
+#pragma unroll
+    for (int it = 0; it < (kInts / 4 + 31) / 32; it++) {
+      const int k = lane + 32 * it;
+      if (k < nv) t[it] = __ldg(reinterpret_cast<const int4*>(src) + k);
+    }
+#pragma unroll
+    for (int it = 0; it < (kInts / 4 + 31) / 32; it++) {
+      const int k = lane + 32 * it;
+      if (k < nv) reinterpret_cast<int4*>(wb)[k] = t[it];
+    }
+    k0 = nv << 2;
+  }
+  for (int k = k0 + lane; k < total; k += 32) wb[k] = __ldg(src + k);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < kRows; r++) {
+    const int row = lane + 32 * r;
+#pragma unroll
+    for (int q = 0; q < ORDER; q++) c[r][q] = row < rows ? wb[row * ORDER + q] : 0;
+  }
+  __syncwarp();
+}
+
+// `nonempty` (shared memory, may be null) has bit c set when contract key c has a Y run: rows
+// whose bit is clear skip the run lookup.
 template <int ORDER, bool VEC>
 __device__ __forceinline__ void rows_runs(const int32_t* __restrict__ coords, int64_t base, int64_t n,
                                           const KeyPlan& p, const uint32_t* __restrict__ yoff, uint64_t* fk,
-                                          uint32_t* lo, uint32_t* w, uint32_t* status, uint64_t* ck) {
+                                          uint32_t* lo, uint32_t* w, uint32_t* status, uint64_t* ck,
+                                          const uint32_t* nonempty = nullptr) {
   bool ok[kRows];
+  if constexpr (kStageRows && !VEC && ORDER >= 3) {
+    int32_t c[kRows][ORDER];
+    stage_rows<ORDER>(coords, base, n, c);
 #pragma unroll
-  for (int r = 0; r < kRows; r++) {
-    const int64_t i = base + lane_id() + 32 * r;
-    ok[r] = false;
-    if (i < n) {
-      ok[r] = row_keys<ORDER, VEC>(coords, i, p, ck[r], fk[r]);
-      if (!ok[r]) atomicOr(status, kStatCoordRange);
+    for (int r = 0; r < kRows; r++) {
+      const int64_t i = base + lane_id() + 32 * r;
+      ok[r] = false;
+      if (i < n) {
+        ok[r] = keys_of<ORDER>(c[r], p, ck[r], fk[r]);
+        if (!ok[r]) atomicOr(status, kStatCoordRange);
+      }
     }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      const int64_t i = base + lane_id() + 32 * r;
+      ok[r] = false;
+      if (i < n) {
+        ok[r] = row_keys<ORDER, VEC>(coords, i, p, ck[r], fk[r]);
+        if (!ok[r]) atomicOr(status, kStatCoordRange);
+      }
+    }
+  }
+  if (nonempty) {
+#pragma unroll
+    for (int r = 0; r < kRows; r++)
+      if (ok[r]) ok[r] = (nonempty[ck[r] >> 5] >> (ck[r] & 31)) & 1u;
   }
 #pragma unroll
   for (int r = 0; r < kRows; r++) {
@@ -146,34 +217,165 @@ __device__ __forceinline__ void rows_runs(const int32_t* __restrict__ coords, in
   for (int r = 0; r < kRows; r++) w[r] -= lo[r];
 }
 
+// Bit c of `bits` is set when contract key c has a Y run (any segment).
+__global__ void __launch_bounds__(kThreads) nonempty_kernel(const uint32_t* __restrict__ yoff, u64 K, uint32_t nseg,
+                                                            uint32_t* __restrict__ bits) {
+  const u64 words = (K + 31) / 32;
+  for (u64 wi = (u64)blockIdx.x * kThreads + threadIdx.x; wi < words; wi += (u64)gridDim.x * kThreads) {
+    uint32_t b = 0;
+    for (int j = 0; j < 32; j++) {
+      const u64 c = wi * 32 + j;
+      if (c < K && yoff[(c + 1) * nseg] > yoff[c * nseg]) b |= 1u << j;
+    }
+    bits[wi] = b;
+  }
+}
+
+// A warp's share of a row stream read as whole blocks of 32 * kRows rows with 16-byte loads
+// (coords 16-byte aligned): load() issues a block's loads, unpack() hands lane l the rows
+// block + l + 32 r. Holding two of these keeps the next block's loads in flight while the
+// current block is processed.
+template <int ORDER>
+struct RowBlock {
+  static constexpr int kVec = 32 * kRows * ORDER / 4;  // int4 per block
+  static constexpr int NV = (kVec + 31) / 32;
+  int4 t[NV];
+  __device__ __forceinline__ void load(const int32_t* __restrict__ coords, int64_t blk) {
+    const int4* src = reinterpret_cast<const int4*>(coords + blk * (32 * kRows * ORDER));
+    const int lane = (int)lane_id();
+#pragma unroll
+    for (int it = 0; it < NV; it++)
+      if (lane + 32 * it < kVec) t[it] = __ldg(src + lane + 32 * it);
+  }
+  __device__ __forceinline__ void unpack(int4* wb, int32_t (&c)[kRows][ORDER]) const {
+    const int lane = (int)lane_id();
+    if constexpr (ORDER == 4) {
+#pragma unroll
+      for (int r = 0; r < kRows; r++) {
+        c[r][0] = t[r].x; c[r][1] = t[r].y; c[r][2] = t[r].z; c[r][3] = t[r].w;
+      }
+    } else {
+#pragma unroll
+      for (int it = 0; it < NV; it++)
+        if (lane + 32 * it < kVec) wb[lane + 32 * it] = t[it];
+      __syncwarp();
+      const int32_t* w32 = reinterpret_cast<const int32_t*>(wb);
+#pragma unroll
+      for (int r = 0; r < kRows; r++)
+#pragma unroll
+        for (int q = 0; q < ORDER; q++) c[r][q] = w32[(lane + 32 * r) * ORDER + q];
+      __syncwarp();
+    }
+  }
+};
+
 template <int ORDER, bool VEC, bool GROUPS>
-__global__ void __launch_bounds__(kThreads) x_survey_kernel(const int32_t* __restrict__ coords,
+__global__ void __launch_bounds__(kThreads, 3) x_survey_kernel(const int32_t* __restrict__ coords,
                                                             const double* __restrict__ vals, int64_t n, KeyPlan p,
                                                             const uint32_t* __restrict__ yoff, Survivors sv,
                                                             u64* __restrict__ P, uint32_t* __restrict__ gcnt,
-                                                            uint32_t* status) {
+                                                            uint32_t* status, const uint32_t* __restrict__ nonempty,
+                                                            uint32_t ne_words) {
+  extern __shared__ __align__(16) uint32_t s_nonempty[];
   __shared__ u64 warp_p[kThreads / 32];
+  if (ne_words) {
+    for (uint32_t i = threadIdx.x; i < ne_words; i += kThreads) s_nonempty[i] = nonempty[i];
+    __syncthreads();
+  }
+  const uint32_t* ne = ne_words ? s_nonempty : nullptr;
+  // Survivors are gathered per warp in shared memory and appended 32 or more at a time: one
+  // atomic on the shared survivor counter per flush instead of one per warp and row step. Their
+  // runs and values are read at the flush, all lanes at once, so that with the bitmap the row
+  // stream itself waits on no lookup.
+  __shared__ u64 b_fk[kThreads / 32][64], b_row[kThreads / 32][64];
+  __shared__ uint32_t b_ck[kThreads / 32][64];
+  constexpr int OD = ORDER > 0 ? ORDER : 1;
+  __shared__ int4 rowbuf[kThreads / 32][ORDER == 4 ? 1 : RowBlock<OD>::kVec];
+  const unsigned lane = lane_id(), wq = threadIdx.x >> 5;
+  uint32_t held = 0;  // warp-uniform
   u64 my_p = 0;
-  STC_WARP_ROWS(base, n) {
+  auto flush = [&]() {
+    __syncwarp();
+    unsigned pos = 0;
+    if (lane == 0) pos = atomicAdd(sv.count, held);
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    for (uint32_t k = lane; k < held; k += 32) {
+      const uint32_t c = b_ck[wq][k];
+      const u64 fk = b_fk[wq][k];
+      const uint32_t lo = __ldg(yoff + (u64)c * p.nseg);
+      const uint32_t w = __ldg(yoff + ((u64)c + 1) * p.nseg) - lo;
+      const double v = __ldg(vals + b_row[wq][k]);
+      sv.fk[pos + k] = fk;
+      if (sv.ck) sv.ck[pos + k] = c;
+      sv.ystart[pos + k] = lo;
+      sv.w[pos + k] = w;
+      sv.v[pos + k] = v;
+      my_p += w;
+      if (GROUPS) atomicAdd(gcnt + fk, 1u);
+    }
+    __syncwarp();
+    held = 0;
+  };
+  // Rows [base, base + 32 * kRows) with their coordinates in c.
+  auto process = [&](int64_t base, int32_t (&c)[kRows][OD]) {
     uint64_t fk[kRows], ck[kRows];
-    uint32_t lo[kRows], w[kRows];
-    rows_runs<ORDER, VEC>(coords, base, n, p, yoff, fk, lo, w, status, ck);
+    bool live[kRows];
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
-      const bool live = w[r] > 0;
-      const unsigned pos = warp_reserve<unsigned>(live, sv.count);
-      if (live) {
-        const int64_t i = base + lane_id() + 32 * r;
-        sv.fk[pos] = fk[r];
-        if (sv.ck) sv.ck[pos] = (uint32_t)ck[r];
-        sv.ystart[pos] = lo[r];
-        sv.w[pos] = w[r];
-        sv.v[pos] = __ldg(vals + i);
-        my_p += w[r];
-        if (GROUPS) atomicAdd(gcnt + fk[r], 1u);
+      live[r] = false;
+      if (base + lane + 32 * r < n) {
+        live[r] = keys_of<ORDER>(c[r], p, ck[r], fk[r]);
+        if (!live[r]) atomicOr(status, kStatCoordRange);
+        else if (ne) live[r] = (ne[ck[r] >> 5] >> (ck[r] & 31)) & 1u;
+      }
+    }
+    if (!ne) {
+#pragma unroll
+      for (int r = 0; r < kRows; r++)
+        if (live[r]) live[r] = __ldg(yoff + (ck[r] + 1) * p.nseg) > __ldg(yoff + ck[r] * p.nseg);
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; r++) {
+      const unsigned m = __ballot_sync(0xffffffffu, live[r]);
+      if (live[r]) {
+        const uint32_t k = held + __popc(m & lanemask_lt());
+        b_fk[wq][k] = fk[r];
+        b_ck[wq][k] = (uint32_t)ck[r];
+        b_row[wq][k] = (u64)(base + lane + 32 * r);
+      }
+      held += __popc(m);
+      if (held >= 32) flush();
+    }
+  };
+  const int64_t nw = (int64_t)gridDim.x * (kThreads / 32);
+  int64_t blk = (int64_t)blockIdx.x * (kThreads / 32) + wq;
+  if constexpr (ORDER > 0) {
+    if ((reinterpret_cast<uintptr_t>(coords) & 15u) == 0) {
+      // Whole blocks, two in flight per warp.
+      const int64_t nfull = n / (32 * kRows);
+      RowBlock<ORDER> cur, nxt;
+      if (blk < nfull) cur.load(coords, blk);
+      for (; blk < nfull; blk += nw) {
+        if (blk + nw < nfull) nxt.load(coords, blk + nw);
+        int32_t c[kRows][OD];
+        cur.unpack(rowbuf[wq], c);
+        process(blk * (32 * kRows), c);
+        cur = nxt;
       }
     }
   }
+  // The last partial block, or every block when the coordinates are not 16-byte aligned.
+  for (; blk * (32 * kRows) < n; blk += nw) {
+    int32_t c[kRows][OD];
+    const int64_t base = blk * (32 * kRows);
+#pragma unroll
+    for (int r = 0; r < kRows; r++)
+#pragma unroll
+      for (int q = 0; q < ORDER; q++)
+        c[r][q] = base + lane + 32 * r < n ? __ldg(coords + (base + lane + 32 * r) * ORDER + q) : 0;
+    process(base, c);
+  }
+  if (held) flush();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_p += __shfl_down_sync(0xffffffffu, my_p, o);
   if (lane_id() == 0) warp_p[threadIdx.x >> 5] = my_p;
@@ -188,7 +390,7 @@ __global__ void __launch_bounds__(kThreads) x_survey_kernel(const int32_t* __res
 // Dense X (most entries have a Y run): count entries per X free key and the products,
 // without writing a survivor list.
 template <int ORDER, bool VEC>
-__global__ void __launch_bounds__(kThreads) x_count_kernel(const int32_t* __restrict__ coords, int64_t n, KeyPlan p,
+__global__ void __launch_bounds__(kThreads, kXMinBlocks) x_count_kernel(const int32_t* __restrict__ coords, int64_t n, KeyPlan p,
                                                            const uint32_t* __restrict__ yoff, u64* __restrict__ P,
                                                            uint32_t* __restrict__ gcnt, uint32_t* status) {
   __shared__ u64 warp_p[kThreads / 32];
@@ -218,7 +420,7 @@ __global__ void __launch_bounds__(kThreads) x_count_kernel(const int32_t* __rest
 
 // Dense X: read X again and place every entry with a Y run at its group's cursor.
 template <int ORDER, bool VEC>
-__global__ void __launch_bounds__(kThreads) x_scatter_dense_kernel(const int32_t* __restrict__ coords,
+__global__ void __launch_bounds__(kThreads, kXMinBlocks) x_scatter_dense_kernel(const int32_t* __restrict__ coords,
                                                                    const double* __restrict__ vals, int64_t n,
                                                                    KeyPlan p, const uint32_t* __restrict__ yoff,
                                                                    uint32_t* __restrict__ gcur, GroupedX gx,
@@ -325,16 +527,25 @@ cudaError_t launch_y_scatter(const int32_t* coords, const double* vals, int64_t 
 }
 
 cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
-                            const uint32_t* yoff, Survivors sv, u64* P, uint32_t* gcnt, uint32_t* status, int sms,
-                            cudaStream_t s) {
+                            const uint32_t* yoff, u64 K, Survivors sv, u64* P, uint32_t* gcnt, uint32_t* status,
+                            uint32_t* nonempty, int sms, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const unsigned g = grid_for((n + kRows - 1) / kRows, sms);
   const bool groups = gcnt != nullptr;
+  const uint32_t ne_words = (nonempty && K <= kNonemptyMaxKeys) ? (uint32_t)((K + 31) / 32) : 0u;
+  if (ne_words) {
+    const unsigned gw = (unsigned)std::min<u64>((ne_words + kThreads - 1) / kThreads, (u64)sms * 8);
+    nonempty_kernel<<<gw, kThreads, 0, s>>>(yoff, K, p.nseg, nonempty);
+    note_launch();
+  }
+  const size_t smem = (size_t)ne_words * 4;
   return dispatch_order(p.order, vec_ok(coords, p.order), [&]<int O, bool V>() {
-    if (groups)
-      x_survey_kernel<O, V, true><<<g, kThreads, 0, s>>>(coords, vals, n, p, yoff, sv, P, gcnt, status);
-    else
-      x_survey_kernel<O, V, false><<<g, kThreads, 0, s>>>(coords, vals, n, p, yoff, sv, P, gcnt, status);
+    auto kern = groups ? x_survey_kernel<O, V, true> : x_survey_kernel<O, V, false>;
+    if (smem) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<g, kThreads, smem, s>>>(coords, vals, n, p, yoff, sv, P, gcnt, status, nonempty, ne_words);
     note_launch();
     return cudaGetLastError();
   });
