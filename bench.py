@@ -82,8 +82,10 @@ class ClockSampler:
         self.device = device
         self.period_ms = period_ms
         self.proc = None
-        self.lines = []  # (arrival time, line)
+        self.lines = []  # (sample time, line)
         self.window = None
+        self.error = None
+        self.raw = []
 
     def start(self, wait_s: float = 5.0):
         try:
@@ -94,13 +96,16 @@ class ClockSampler:
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
             time.sleep(min(wait_s, 1.0))  # let the tool start before the warm-up
-        except Exception:
+        except Exception as e:  # no sampler: reported in the summary
             self.proc = None
+            self.error = repr(e)
         return self
 
     def _read(self):
         # The pipe is block-buffered: each sample's own timestamp (local time) places it.
         for ln in self.proc.stdout:
+            if len(self.raw) < 2:
+                self.raw.append(ln.strip())
             try:
                 stamp = datetime.datetime.strptime(ln.split(",")[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
             except ValueError:
@@ -139,9 +144,32 @@ class ClockSampler:
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
-                    "note": "no nvidia-smi sample inside the timed window"}
+                    "note": "no nvidia-smi sample inside the timed window",
+                    "samples_total": len(self.lines), "error": self.error, "raw": self.raw,
+                    "first": self.lines[0][0] if self.lines else None,
+                    "last": self.lines[-1][0] if self.lines else None, "window": self.window}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm), "period_ms": self.period_ms}
+
+
+def replica_seed(workload: str, rank: int) -> int:
+    """Every rank runs an independent replica: the same shapes with its own seed."""
+    return SEEDS[workload] + 1000 * rank
+
+
+def reduce_over_ranks(ms: float, products: float, world: int, device: str):
+    """Whole-job timing across replicas: the slowest rank's time and the products of all
+    ranks (rank 0 reports value = products / time)."""
+    if world <= 1:
+        return ms, products
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    pt = torch.tensor([products], device=device, dtype=torch.float64)
+    dist.all_reduce(pt)
+    return float(t.item()), float(pt.item())
 
 
 def dist_env():
@@ -322,6 +350,8 @@ def main(argv=None):
     import paper_2410_10094_gb300 as stc
 
     world, rank, local = dist_env()
+    # Sample clocks from before the first CUDA call in this process.
+    clk = ClockSampler(local).start()
     if world > 1:
         import torch.distributed as dist
 
@@ -333,7 +363,7 @@ def main(argv=None):
     stc.load()
     ctx = stc.default_context(dev)
 
-    seed = SEEDS[args.workload] + 1000 * rank
+    seed = replica_seed(args.workload, rank)
     p = WORKLOADS[args.workload](seed)
     workload_problem = p
     stream = torch.cuda.current_stream()
@@ -362,7 +392,6 @@ def main(argv=None):
                                 group_load_factor=args.group_load_factor, accumulator=args.accumulator,
                                 stream=stream, ctx=ctx)
 
-    clk = ClockSampler(dev).start()
     for _ in range(args.warmup):
         r = step()
         nz, oz, P, launches, ns = r.nnz, r.order, r.stats.products, r.stats.launches, r.stats.survivors
@@ -389,16 +418,7 @@ def main(argv=None):
     clk.mark(tw0, time.time())
     clk.stop()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        pt = torch.tensor([float(P)], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(pt)
-        total_products = float(pt.item())
-    else:
-        total_products = float(P)
+    ms, total_products = reduce_over_ranks(ev0.elapsed_time(ev1), float(P), world, "cuda")
     value = total_products * args.steps / (ms / 1e3)
 
     # ---- e2e: the public API call with host buffers, copies inside the timed region

@@ -26,12 +26,16 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Requests with more products than this run as plain contractions even in batched mode.
+constexpr uint64_t kServerAloneProducts = 1ull << 24;
+
 struct Ticket {
   stc_problem req{};
   std::vector<int64_t> xshape, yshape;
   std::vector<int32_t> cx, cy, oo;
   bool has_oo = false;
   uint64_t bytes = 0;  // admission bound
+  uint64_t products = 0;  // exact product count
   bool done = false;
   stc_status status = STC_OK;
   std::string error;
@@ -119,17 +123,44 @@ void worker_main(stc_server* sv, int w) {
       for (uint64_t id : batch) probs.push_back(sv->tickets[id].req);
     }
     std::vector<stc_result*> outs(batch.size(), nullptr);
-    stc_status st;
+    stc_status st = STC_OK;
     std::string err;
-    if (sv->opts.plain) {
-      const stc_problem& q = probs[0];
-      st = stc_contract(sv->ctx, &q.X, &q.Y, q.ncontract, q.cx, q.cy, q.out_order, nullptr, s, &outs[0]);
-    } else {
+    // Requests large enough to fill the GPU alone (and a request that is alone in its batch)
+    // run as plain contractions; the others share one batched launch sequence.
+    std::vector<uint64_t> prods(batch.size());
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (size_t k = 0; k < batch.size(); k++) prods[k] = sv->tickets[batch[k]].products;
+    }
+    std::vector<size_t> small, alone;
+    for (size_t k = 0; k < batch.size(); k++)
+      (sv->opts.plain || prods[k] > kServerAloneProducts ? alone : small).push_back(k);
+    if (small.size() == 1) {
+      alone.insert(alone.begin(), small[0]);
+      small.clear();
+    }
+    if (!small.empty()) {
+      std::vector<stc_problem> sp;
+      std::vector<stc_result*> so(small.size(), nullptr);
+      for (size_t k : small) sp.push_back(probs[k]);
       stc_opts o{};
       o.strategy = STC_STRATEGY_GROUPED;
-      st = stc_contract_batch(sv->ctx, (int32_t)probs.size(), probs.data(), &o, s, outs.data());
+      st = stc_contract_batch(sv->ctx, (int32_t)sp.size(), sp.data(), &o, s, so.data());
+      for (size_t i = 0; i < small.size(); i++) outs[small[i]] = so[i];
     }
-    if (st != STC_OK) err = stc_last_error();
+    for (size_t k : alone) {
+      if (st != STC_OK) break;
+      const stc_problem& q = probs[k];
+      st = stc_contract(sv->ctx, &q.X, &q.Y, q.ncontract, q.cx, q.cy, q.out_order, nullptr, s, &outs[k]);
+    }
+    if (st != STC_OK) {
+      // The whole take fails together; results already made are returned.
+      err = stc_last_error();
+      for (stc_result*& r : outs) {
+        if (r) stc_result_free(r);
+        r = nullptr;
+      }
+    }
     for (stc_result* r : outs) result_release_on_default_stream(r);
     {
       std::lock_guard<std::mutex> lk(sv->mu);
@@ -197,6 +228,7 @@ stc_status stc_server_submit(stc_server* sv, const stc_problem* req, uint64_t* t
                                     sv->count_stream, &P, &bytes);
     if (st != STC_OK) return st;
     t.bytes = bytes;
+    t.products = P;
   }
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->stopping) return report_error(STC_ERR_INVALID_ARG, "server is shutting down");
