@@ -1019,8 +1019,12 @@ __global__ void __launch_bounds__(THREADS, 2) group_bitmap_kernel(GroupArgs a, c
 #define STASH_THREADS 512
 #endif
 #ifndef STASH_U
-#define STASH_U 4
+#define STASH_U 3
 #endif
+#ifndef STASH_PIPE
+#define STASH_PIPE 1
+#endif
+constexpr bool kStashPipe = STASH_PIPE != 0;
 constexpr int kStashThreads = STASH_THREADS;
 constexpr uint32_t kStashMaxEntries = kStashThreads;  // X entries staged per chunk
 // Shared memory (widest segment, kBitmapWords words), in order: key bitmap, repeat bitmap,
@@ -1089,14 +1093,14 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
   __shared__ u64 warp_tot[NW + 1];
   __shared__ OutTarget tg;
   __shared__ u64 s_gbase;
-  __shared__ uint32_t s_nf, s_nr;
+  __shared__ uint32_t s_cnt;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   const uint64_t keep = policy_evict_last();
   const uint64_t pol = policy_evict_first();
   const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
   for (uint32_t i = threadIdx.x; i < 2 * kBitmapWords; i += T) bits[i] = 0;
-  if (threadIdx.x == 0) s_nf = s_nr = 0;
+  if (threadIdx.x == 0) s_cnt = 0;
   // Prefetched staging of the next group (when it fits one chunk): its X entries' contract
   // keys and values, and with a single segment their runs.
   uint32_t pf_g = 0, pf_x0 = 0, pf_x1 = 0, pf_ck = 0, pf_ys = 0, pf_ye = 0;
@@ -1149,50 +1153,75 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
           }
         }
         __syncthreads();
-        for (uint32_t sb = warp; sb < S; sb += NW * U) {
-          uint32_t f[U];
-          double prod[U];
-          bool ok[U];
+        // Slot batches of U per warp; the next batch's Y loads are issued before the current
+        // batch is claimed, so two batches of loads are in flight per warp.
+        uint32_t fA[U], eA[U];
+        double yA[U];
+        bool okA[U], inA[U];
+        auto issue = [&](uint32_t sbase, uint32_t (&f)[U], uint32_t (&e)[U], double (&y)[U], bool (&ok)[U],
+                         bool (&in)[U]) {
 #pragma unroll
           for (int u = 0; u < U; u++) {
-            const uint32_t si = sb + u * NW;
+            const uint32_t si = sbase + u * NW;
+            in[u] = si < S;
             ok[u] = false;
-            if (si < S) {
+            if (in[u]) {
               const uint2 rec = stab[si];
               ok[u] = lane < (rec.y & 255u);
               const uint32_t j = rec.x + (ok[u] ? lane : 0u);
-              f[u] = ld_keep_u32(yfk + j, keep) & (seg - 1);
-              prod[u] = __dmul_rn(sx[rec.y >> 8], ld_keep_f64(a.yv + j, keep));
+              e[u] = rec.y >> 8;
+              f[u] = ld_keep_u32(yfk + j, keep);
+              y[u] = ld_keep_f64(a.yv + j, keep);
             }
           }
+        };
+        issue(warp, fA, eA, yA, okA, inA);
+        for (uint32_t sb = warp; sb < S; sb += NW * U) {
+          uint32_t fB[U], eB[U];
+          double yB[U];
+          bool okB[U], inB[U];
+          if (kStashPipe) issue(sb + NW * U, fB, eB, yB, okB, inB);
 #pragma unroll
           for (int u = 0; u < U; u++) {
-            if (sb + u * NW < S) {
-              const uint32_t w = f[u] >> 5, bit = 1u << (f[u] & 31);
+            if (inA[u]) {
+              const uint32_t f = fA[u] & (seg - 1);
+              const double prod = __dmul_rn(sx[eA[u]], yA[u]);
+              const uint32_t w = f >> 5, bit = 1u << (f & 31);
               bool first = false;
-              if (ok[u]) {
+              if (okA[u]) {
                 first = (atomicOr(bits + w, bit) & bit) == 0;
                 if (!first) atomicOr(rbits + w, bit);
               }
               const uint32_t fm = __ballot_sync(0xffffffffu, first);
-              const uint32_t rm = __ballot_sync(0xffffffffu, ok[u] && !first);
+              const uint32_t rm = __ballot_sync(0xffffffffu, okA[u] && !first);
+              // One packed counter: first products in the low half, repeats in the high half.
               uint32_t base = 0;
-              if (lane == 0 && fm) base = atomicAdd(&s_nf, (uint32_t)__popc(fm));
-              if (lane == 1 && rm) base = atomicAdd(&s_nr, (uint32_t)__popc(rm));
-              const uint32_t bf = __shfl_sync(0xffffffffu, base, 0);
-              const uint32_t br = __shfl_sync(0xffffffffu, base, 1);
-              if (ok[u]) {
-                const uint32_t at = first ? bf + __popc(fm & lt) : kStashCap - 1 - (br + __popc(rm & lt));
-                pk[at] = (uint16_t)f[u];
-                pv[at] = prod[u];
+              if (lane == 0) base = atomicAdd(&s_cnt, (uint32_t)__popc(fm) | ((uint32_t)__popc(rm) << 16));
+              base = __shfl_sync(0xffffffffu, base, 0);
+              if (okA[u]) {
+                const uint32_t at = first ? (base & 0xffffu) + __popc(fm & lt)
+                                          : kStashCap - 1 - ((base >> 16) + __popc(rm & lt));
+                pk[at] = (uint16_t)f;
+                pv[at] = prod;
               }
             }
+          }
+          if (!kStashPipe) {
+            issue(sb + NW * U, fB, eB, yB, okB, inB);
+          }
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            fA[u] = fB[u];
+            eA[u] = eB[u];
+            yA[u] = yB[u];
+            okA[u] = okB[u];
+            inA[u] = inB[u];
           }
         }
         if (!one_chunk) __syncthreads();
       }
       __syncthreads();
-      const uint32_t nkeys = s_nf, reps = s_nr;
+      const uint32_t nkeys = s_cnt & 0xffffu, reps = s_cnt >> 16;
       if (nkeys == 0) continue;
       // Thread 31 reserves the outputs; the result is published by the barrier before the write.
       u64 my_base = 0;
@@ -1263,7 +1292,7 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
         reinterpret_cast<uint4*>(rbits)[i] = make_uint4(0, 0, 0, 0);
       }
       if (nwords < 4 && threadIdx.x < nwords) bits[threadIdx.x] = rbits[threadIdx.x] = 0;
-      if (threadIdx.x == 0) s_nf = s_nr = 0;
+      if (threadIdx.x == 0) s_cnt = 0;
       __syncthreads();
     }
   }
