@@ -186,25 +186,37 @@ def stc_contract(ctx: int, X, Y, cx: Sequence[int], cy: Sequence[int], out_order
     return r.value
 
 
+class BatchProblems:
+    """The stc_problem array of a batch, built once (the inputs' device memory must stay
+    alive and unchanged while it is used). problems: sequence of (X, Y, cx, cy[, out_order])
+    with X and Y as (shape, coords, vals) CUDA tensors."""
+
+    def __init__(self, problems):
+        probs = [tuple(p) + (None,) * (5 - len(p)) for p in problems]
+        self.n = len(probs)
+        self._keep = []
+        self.arr = (stc_problem * max(self.n, 1))()
+        for i, (X, Y, cx, cy, out_order) in enumerate(probs):
+            xa, ya = _CooArg(*X), _CooArg(*Y)
+            acx, acy = _mode_array(cx), _mode_array(cy)
+            oo = _mode_array(out_order) if out_order is not None else None
+            self._keep.extend([X, Y, xa, ya, acx, acy, oo])
+            self.arr[i].X = xa.coo
+            self.arr[i].Y = ya.coo
+            self.arr[i].ncontract = len(cx)
+            self.arr[i].cx = C.cast(acx, C.POINTER(C.c_int32))
+            self.arr[i].cy = C.cast(acy, C.POINTER(C.c_int32))
+            self.arr[i].out_order = C.cast(oo, C.POINTER(C.c_int32)) if oo is not None else None
+
+
 def stc_contract_batch(ctx: int, problems, opts: stc_opts = None, stream=None):
-    """Calls stc_contract_batch; problems is a sequence of (X, Y, cx, cy, out_order) with X and Y
-    as (shape, coords, vals) CUDA tensors. Returns the list of stc_result handles."""
-    n = len(problems)
-    keep = []
-    arr = (stc_problem * max(n, 1))()
-    for i, (X, Y, cx, cy, out_order) in enumerate(problems):
-        xa, ya = _CooArg(*X), _CooArg(*Y)
-        acx, acy = _mode_array(cx), _mode_array(cy)
-        oo = _mode_array(out_order) if out_order is not None else None
-        keep.extend([xa, ya, acx, acy, oo])
-        arr[i].X = xa.coo
-        arr[i].Y = ya.coo
-        arr[i].ncontract = len(cx)
-        arr[i].cx = C.cast(acx, C.POINTER(C.c_int32))
-        arr[i].cy = C.cast(acy, C.POINTER(C.c_int32))
-        arr[i].out_order = C.cast(oo, C.POINTER(C.c_int32)) if oo is not None else None
+    """Calls stc_contract_batch; problems is a BatchProblems or a sequence of (X, Y, cx, cy,
+    out_order) with X and Y as (shape, coords, vals) CUDA tensors. Returns the list of
+    stc_result handles."""
+    bp = problems if isinstance(problems, BatchProblems) else BatchProblems(problems)
+    n = bp.n
     outs = (C.c_void_p * max(n, 1))()
-    check(load().stc_contract_batch(C.c_void_p(ctx), n, arr, C.byref(opts) if opts is not None else None,
+    check(load().stc_contract_batch(C.c_void_p(ctx), n, bp.arr, C.byref(opts) if opts is not None else None,
                                     C.c_void_p(_stream_handle(stream)), outs))
     return [outs[i] for i in range(n)]
 
@@ -331,26 +343,42 @@ class Stats:
 
 class Result:
     """A finished contraction. ``coords`` (int32 [nnz, order]) and ``vals`` (float64 [nnz])
-    are zero-copy CUDA tensors over the library's memory; they keep it alive."""
+    are zero-copy CUDA tensors over the library's memory, made on first access; they keep it
+    alive."""
 
     def __init__(self, handle: int):
-        import torch
-
         self._h = _Handle(handle)
         self.handle = handle
         self.nnz, self.order, self.shape = stc_result_info(handle)
-        cp, vp = stc_result_data(handle)
         st = stc_result_stats(handle)
         self.stats = Stats(st.products, st.survivors, st.out_capacity, st.table_slots, st.groups, st.strategy,
                            st.launches, st.accumulator, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))))
-        if self.nnz and self.order:
-            self.coords = torch.as_tensor(_DeviceArray(self._h, cp, (self.nnz, self.order), "<i4"), device="cuda")
-        else:
-            self.coords = torch.empty((self.nnz, self.order), dtype=torch.int32, device="cuda")
-        if self.nnz:
-            self.vals = torch.as_tensor(_DeviceArray(self._h, vp, (self.nnz,), "<f8"), device="cuda")
-        else:
-            self.vals = torch.empty((0,), dtype=torch.float64, device="cuda")
+        self._coords = self._vals = None
+
+    @property
+    def coords(self):
+        if self._coords is None:
+            import torch
+
+            if self.nnz and self.order:
+                cp, _ = stc_result_data(self.handle)
+                self._coords = torch.as_tensor(_DeviceArray(self._h, cp, (self.nnz, self.order), "<i4"),
+                                               device="cuda")
+            else:
+                self._coords = torch.empty((self.nnz, self.order), dtype=torch.int32, device="cuda")
+        return self._coords
+
+    @property
+    def vals(self):
+        if self._vals is None:
+            import torch
+
+            if self.nnz:
+                _, vp = stc_result_data(self.handle)
+                self._vals = torch.as_tensor(_DeviceArray(self._h, vp, (self.nnz,), "<f8"), device="cuda")
+            else:
+                self._vals = torch.empty((0,), dtype=torch.float64, device="cuda")
+        return self._vals
 
 
 
@@ -367,12 +395,13 @@ def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, stra
 
 def contract_batch(problems, *, group_load_factor: float = 0.0, record_times: bool = False, stream=None,
                    ctx: Context = None):
-    """Many independent contractions in one batch (shared passes). problems: sequence of
-    (X, Y, cx, cy) or (X, Y, cx, cy, out_order). Returns one Result per problem."""
+    """Many independent contractions in one batch (shared passes). problems: a BatchProblems
+    or a sequence of (X, Y, cx, cy) or (X, Y, cx, cy, out_order). Returns one Result per
+    problem."""
     ctx = ctx or default_context()
-    probs = [tuple(p) + (None,) * (5 - len(p)) for p in problems]
+    bp = problems if isinstance(problems, BatchProblems) else BatchProblems(problems)
     o = stc_opts(STRATEGY_GROUPED, 1 if record_times else 0, 0.0, float(group_load_factor), ACC_HASH, 0)
-    return [Result(h) for h in stc_contract_batch(ctx.handle, probs, o, stream)]
+    return [Result(h) for h in stc_contract_batch(ctx.handle, bp, o, stream)]
 
 
 class Server:
