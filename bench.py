@@ -179,6 +179,13 @@ def dist_env():
     return world, rank, local
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
+# kernel, from an ncu capture of the current kernels with the default strategy and
+# accumulator; workloads without a capture report null.
+NCU_TRAFFIC = {"plain_large": ("group_stash_kernel", 2.100e9 + 8.700e9),
+               "imbalanced": ("x_survey_kernel", 0.2746e9 + 0.0074e9)}
+
+
 def l2_note(bytes_in, bytes_out, l2=129e6):
     """How the timed steps relate to the L2 (no flush between steps)."""
     fits = "working set exceeds" if bytes_in + bytes_out > l2 else "working set fits"
@@ -495,8 +502,10 @@ def main(argv=None):
     dom_ms = per_step[dom]
     achieved = kernel_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
     step_ms = ms / args.steps
+    traffic = NCU_TRAFFIC.get(args.workload) if (args.strategy == 0 and args.accumulator == 0) else None
     roofline = {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": (achieved / hbm) if achieved else None, "traffic": None, "peak_kind": peak_kind,
+                "frac": (achieved / hbm) if achieved else None, "traffic": traffic[1] if traffic else None,
+                "traffic_kernel": traffic[0] if traffic else None, "peak_kind": peak_kind,
                 "kernel_ms": dom_ms, "alg_bytes": kernel_bytes}
     step_alg = alg_bytes(p, nz, oz)
 
