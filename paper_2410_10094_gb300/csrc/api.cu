@@ -439,12 +439,17 @@ uint64_t grouped_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t P) {
   return b;
 }
 
+// Bitmap-row groups that fit are streamed (outputs written during the first pass).
+constexpr bool kStreamGroups = true;
+
 // Counters of the grouping and binning passes, read back with the first host sync.
 struct GroupCounters {
   uint32_t count[kMaxClasses + 3];
-  uint32_t pad_;
+  unsigned stream_nrec;  // streamed segments with repeats
   u64 huge_slots;
   u64 out_cap;
+  u64 stream_holes;      // positions of streamed reservations that hold no output
+  u64 fill_counters[2];
 };
 
 // GROUPED strategy (Sections 4.1 and 4.3): survivors are counting-sorted by X free key,
@@ -502,7 +507,8 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
     // With AUTO, groups that fit the warp classes keep their hash tables (a bitmap sweep costs
     // a fixed amount per segment).
     b.dense_min = o.accumulator == STC_ACC_DENSE ? 0 : (b.tmax[1] + 1) * nseg;
-    b.stash_cap = dense_stash_cap();
+    b.stream = kStreamGroups;
+    b.stash_cap = kStreamGroups ? dense_stream_cap() : dense_stash_cap();
     STC_TRY(ar.alloc(&b.dense_list[0], maxg));
     STC_TRY(ar.alloc(&b.dense_list[1], maxg));
   }
@@ -582,13 +588,32 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
     STC_CUDA(launch_group_classes(a, wide, direct, b, hg.count, ctx->sms, s));
     STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
   }
-  if (dense_rows)
-    STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.dense_list[0], hg.count[kMaxClasses + 1], b.dense_list[1],
-                                hg.count[kMaxClasses + 2], ctx->sms, s));
+  StreamArgs sa{};
+  const uint32_t nstream = dense_rows && kStreamGroups ? hg.count[kMaxClasses + 1] : 0u;
+  if (dense_rows) {
+    // Streamed groups go last: every other kernel's outputs then lie below the final count.
+    STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.dense_list[0], kStreamGroups ? 0u : hg.count[kMaxClasses + 1],
+                                b.dense_list[1], hg.count[kMaxClasses + 2], ctx->sms, s));
+    if (nstream) {
+      STC_TRY(ar.alloc(&sa.rec, (size_t)nstream * nseg));
+      sa.nrec = &gc->stream_nrec;
+      sa.holes = &gc->stream_holes;
+      STC_CUDA(launch_group_stream(a, pr.yoff, nseg, seg, b.dense_list[0], nstream, sa, ctx->sms, s));
+    }
+  }
   tm.mark(4);
+  u64 holes = 0;
+  if (nstream) STC_CUDA(cudaMemcpyAsync(&holes, &gc->stream_holes, sizeof(u64), cudaMemcpyDeviceToHost, s));
   Counters h2{};
   STC_TRY(read_counters(pr, s, h2));
-  r->nnz = (int64_t)h2.nz;
+  r->nnz = (int64_t)(h2.nz - holes);
+  if (holes) {
+    u64* src_pos = nullptr;
+    STC_TRY(ar.alloc(&src_pos, (size_t)holes));
+    STC_CUDA(launch_stream_fill(sa.rec, sa.nrec, (u64)r->nnz, holes, src_pos, gc->fill_counters, r->coords,
+                                r->vals, pl.oz, &pr.ctr->status, ctx->sms, s));
+    tm.mark(5);
+  }
   r->stats.out_capacity = out_cap;
   r->mem = adopt(ar, ctx, s, {r->coords, r->vals});
   return STC_OK;

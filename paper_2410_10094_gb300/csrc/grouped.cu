@@ -63,19 +63,22 @@ __global__ void __launch_bounds__(kThreads) bin_groups_kernel(u64 FX, const uint
     for (int o = 16; o > 0; o >>= 1) bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
     if (lane == 0) {
       const u64 t = bnd < FY ? bnd : FY;
-      my_cap += t;
       int c = 0;
       while (c < b.nclasses && t > b.tmax[c]) c++;
       if (b.dense_list[0] && t >= b.dense_min) {
+        // Streamed groups reserve one output position per product (their repeats' records).
         const int d = bnd <= b.stash_cap ? 0 : 1;
+        my_cap += d == 0 && b.stream ? bnd : t;
         const uint32_t idx = atomicAdd(b.count + kMaxClasses + 1 + d, 1u);
         b.dense_list[d][idx] = (uint32_t)g;
       } else if (c < b.nclasses) {
+        my_cap += t;
         const uint32_t idx = atomicAdd(b.count + c, 1u);
         b.list[c][idx] = (uint32_t)g;
       } else if (t > (1ull << 30)) {
         atomicOr(b.status, kStatTooLarge);
       } else {
+        my_cap += t;
         const uint32_t idx = atomicAdd(b.count + kMaxClasses, 1u);
         u64 cap = 64;
         while (cap < 2 * t) cap <<= 1;
@@ -1299,6 +1302,321 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
 }
 
 
+// ---- output streaming: groups whose product count fits kStreamCap (the common case of the
+// bitmap path). Each group segment reserves as many output positions as it has products.
+// Pass 1 forms every product once and marks its free key in a bitmap over the segment; the
+// first product of a key (the one that finds its bit clear) writes its output entry at once,
+// at the next place from the front of the reservation. A repeat writes its key and value as
+// a temporary record at the next place from the back and marks its key in a second bitmap.
+// After a device-scope fence and a barrier the repeated keys are ranked, their first
+// products' places looked up, and every repeat adds its value to that entry with an L2
+// atomic. The back of the reservation (the repeats' records) becomes a hole; after all
+// groups, holes below the final output count are filled with the entries above it.
+
+#ifndef STREAM_U
+#define STREAM_U 3
+#endif
+#ifndef STREAM_MINB
+#define STREAM_MINB 4
+#endif
+constexpr int kStreamThreads = 256;
+constexpr uint32_t kStreamEntries = 256;  // X entries staged per chunk
+constexpr uint32_t kStreamCap = 8192;     // products of one group segment
+constexpr uint32_t kStreamSlots = kStreamCap / 32 + kStreamEntries;
+// Shared memory: key bitmap, repeat bitmap, slot table, X values, first-product keys, and the
+// rank -> place map of the repeated keys.
+constexpr size_t kStreamSmem = (size_t)kBitmapWords * 8 + (size_t)kStreamSlots * 8 + (size_t)kStreamEntries * 8 +
+                               (size_t)kStreamCap * 2 + (size_t)kStreamCap;
+
+template <int U>
+__global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kernel(GroupArgs a, const uint32_t* __restrict__ yoff,
+                                                                        uint32_t nseg, uint32_t seg,
+                                                                        const uint32_t* __restrict__ list,
+                                                                        uint32_t count, StreamArgs sa) {
+  constexpr int T = kStreamThreads, NW = T / 32;
+  constexpr uint32_t CH = kStreamEntries;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t nwords = seg >> 5;
+  uint32_t* const bits = reinterpret_cast<uint32_t*>(smem);              // key marks, then repeat ranks
+  uint32_t* const rbits = bits + kBitmapWords;                           // keys met again
+  uint2* const stab = reinterpret_cast<uint2*>(rbits + kBitmapWords);   // slot table
+  double* const sx = reinterpret_cast<double*>(stab + kStreamSlots);    // X values of the chunk
+  uint16_t* const pk = reinterpret_cast<uint16_t*>(sx + CH);            // keys of the first products
+  uint16_t* const map = pk + kStreamCap;                                 // repeat rank -> first place
+  __shared__ u64 warp_tot[NW + 1];
+  __shared__ OutTarget tg;
+  __shared__ u64 s_gbase;
+  __shared__ uint32_t s_cnt;
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t lt = lanemask_lt();
+  const uint64_t keep = policy_evict_last();
+  const uint64_t pol = policy_evict_first();
+  const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
+  for (uint32_t i = threadIdx.x; i < 2 * kBitmapWords; i += T) bits[i] = 0;
+  if (threadIdx.x == 0) s_cnt = 0;
+  // Prefetched staging of the next group (when it fits one chunk).
+  uint32_t pf_g = 0, pf_x0 = 0, pf_x1 = 0, pf_ck = 0, pf_ys = 0, pf_ye = 0;
+  double pf_v = 0.0;
+  auto prefetch = [&](uint32_t gi) {
+    if (gi >= count) return;
+    pf_g = list[gi];
+    pf_x0 = a.goff[pf_g];
+    pf_x1 = a.goff[pf_g + 1];
+    if (pf_x1 - pf_x0 <= CH && threadIdx.x < pf_x1 - pf_x0) {
+      pf_ck = a.gx.ck[pf_x0 + threadIdx.x];
+      pf_v = a.gx.v[pf_x0 + threadIdx.x];
+      if (nseg == 1) {
+        pf_ys = __ldg(yoff + pf_ck);
+        pf_ye = __ldg(yoff + pf_ck + 1);
+      }
+    }
+  };
+  prefetch(blockIdx.x);
+  for (uint32_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
+    const uint32_t g = pf_g, x0 = pf_x0, x1 = pf_x1;
+    const bool one_chunk = x1 - x0 <= CH;
+    if (threadIdx.x == 0) resolve_target(a, g, 0, tg);
+    const uint32_t my_ck = pf_ck, my_ys = pf_ys, my_ye = pf_ye;
+    const double my_v = pf_v;
+    prefetch(gi + gridDim.x);
+    for (uint32_t q = 0; q < nseg; q++) {
+      // The segment's products, reserved up front (a separate count pass for long groups).
+      uint32_t Pq = 0;
+      if (!one_chunk) {
+        for (uint32_t c0 = x0; c0 < x1; c0 += CH) {
+          const uint32_t n = (x1 - c0 < CH) ? x1 - c0 : CH;
+          uint32_t len = 0;
+          if (threadIdx.x < n) {
+            const u64 b = (u64)a.gx.ck[c0 + threadIdx.x] * nseg + q;
+            len = __ldg(yoff + b + 1) - __ldg(yoff + b);
+          }
+          uint32_t tot;
+          block_exscan_u32<T>(len, &tot, warp_tot);
+          Pq += tot;
+        }
+        if (Pq == 0) continue;
+        if (threadIdx.x == 0) s_gbase = atomicAdd(tg.counter, (u64)Pq);
+      }
+      // ---- pass 1, one chunk of X entries at a time.
+      for (uint32_t c0 = x0; c0 < x1; c0 += CH) {
+        const uint32_t n = (x1 - c0 < CH) ? x1 - c0 : CH;
+        uint32_t ys = 0, len = 0;
+        if (threadIdx.x < n) {
+          sx[threadIdx.x] = one_chunk ? my_v : a.gx.v[c0 + threadIdx.x];
+          if (one_chunk && nseg == 1) {
+            ys = my_ys;
+            len = my_ye - my_ys;
+          } else {
+            const uint32_t ck = one_chunk ? my_ck : a.gx.ck[c0 + threadIdx.x];
+            const u64 b = (u64)ck * nseg + q;
+            ys = __ldg(yoff + b);
+            len = __ldg(yoff + b + 1) - ys;
+          }
+        }
+        // Products (high bits) and slots (low 12 bits) before each entry, in one scan; a
+        // one-chunk group reserves its outputs between the scan's two barriers.
+        const uint32_t nslot = (len + 31) >> 5;
+        uint32_t x = (len << 12) | nslot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          const uint32_t t = (int)lane < NW ? (uint32_t)warp_tot[lane] : 0u;
+          uint32_t inc = t;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if ((int)lane >= o) inc += y;
+          }
+          if ((int)lane < NW) warp_tot[lane] = inc - t;
+          if (lane == 31) {
+            warp_tot[NW] = inc;
+            if (one_chunk && (inc >> 12)) s_gbase = atomicAdd(tg.counter, (u64)(inc >> 12));
+          }
+        }
+        __syncthreads();
+        const uint32_t tot = (uint32_t)warp_tot[NW], S = tot & 4095u;
+        if (one_chunk) Pq = tot >> 12;
+        {
+          uint32_t s = ((uint32_t)warp_tot[warp] + x - ((len << 12) | nslot)) & 4095u;
+          if (threadIdx.x < n) {
+            for (uint32_t k = 0; k < len; k += 32, s++) {
+              const uint32_t live = len - k < 32 ? len - k : 32;
+              stab[s] = make_uint2(ys + k, live | (threadIdx.x << 8));
+            }
+          }
+        }
+        __syncthreads();
+        if (Pq == 0) continue;
+        const u64 gbase = s_gbase;
+        const u64 zseg = tg.zrow + (u64)q * seg;
+        int32_t* const coords = tg.coords;
+        double* const vals = tg.vals;
+        const int oz = tg.op.order;
+        const bool v4 = oz == 4 && tg.op.pow2 && ((reinterpret_cast<uintptr_t>(coords) & 15u) == 0);
+        for (uint32_t sb = warp; sb < S; sb += NW * U) {
+          uint32_t f[U], e[U];
+          double y[U];
+          bool ok[U], in[U];
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            const uint32_t si = sb + u * NW;
+            in[u] = si < S;
+            ok[u] = false;
+            if (in[u]) {
+              const uint2 rec = stab[si];
+              ok[u] = lane < (rec.y & 255u);
+              const uint32_t j = rec.x + (ok[u] ? lane : 0u);
+              e[u] = rec.y >> 8;
+              f[u] = ld_keep_u32(yfk + j, keep);
+              y[u] = ld_keep_f64(a.yv + j, keep);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            if (in[u]) {
+              const uint32_t fk = f[u] & (seg - 1);
+              const double prod = __dmul_rn(sx[e[u]], y[u]);
+              const uint32_t w = fk >> 5, bit = 1u << (fk & 31);
+              bool first = false;
+              if (ok[u]) {
+                first = (atomicOr(bits + w, bit) & bit) == 0;
+                if (!first) atomicOr(rbits + w, bit);
+              }
+              const uint32_t fm = __ballot_sync(0xffffffffu, first);
+              const uint32_t rm = __ballot_sync(0xffffffffu, ok[u] && !first);
+              uint32_t base = 0;
+              if (lane == 0) base = atomicAdd(&s_cnt, (uint32_t)__popc(fm) | ((uint32_t)__popc(rm) << 16));
+              base = __shfl_sync(0xffffffffu, base, 0);
+              if (ok[u]) {
+                if (first) {
+                  const uint32_t place = (base & 0xffffu) + __popc(fm & lt);
+                  pk[place] = (uint16_t)fk;
+                  const u64 pos = gbase + place;
+                  const u64 z = zseg + fk;
+                  if (v4) {
+                    const int4 cv = make_int4((int32_t)((uint32_t)(z >> tg.op.shift[0]) & ((uint32_t)tg.op.mod[0] - 1)),
+                                              (int32_t)((uint32_t)(z >> tg.op.shift[1]) & ((uint32_t)tg.op.mod[1] - 1)),
+                                              (int32_t)((uint32_t)(z >> tg.op.shift[2]) & ((uint32_t)tg.op.mod[2] - 1)),
+                                              (int32_t)((uint32_t)(z >> tg.op.shift[3]) & ((uint32_t)tg.op.mod[3] - 1)));
+                    st_stream_v4(coords + pos * 4, cv, pol);
+                    st_stream_f64(vals + pos, prod, pol);
+                  } else {
+                    store_output(coords, vals, pos, z, prod, tg.op, pol);
+                  }
+                } else {
+                  const u64 pos = gbase + Pq - 1 - ((base >> 16) + __popc(rm & lt));
+                  if (oz) coords[pos * oz] = (int32_t)fk;
+                  vals[pos] = prod;
+                }
+              }
+            }
+          }
+        }
+        if (!one_chunk) __syncthreads();
+      }
+      if (Pq == 0) continue;
+      // First products' stores and repeats' records are visible device-wide past this point.
+      __threadfence();
+      __syncthreads();
+      const uint32_t nkeys = s_cnt & 0xffffu, reps = s_cnt >> 16;
+      if (reps) {
+        const u64 gbase = s_gbase;
+        // Rank the repeated keys; the key marks are no longer needed and hold the ranks.
+        const uint32_t wpt = (nwords + T - 1) / T;
+        const uint32_t w0 = threadIdx.x * wpt, w1 = w0 + wpt < nwords ? w0 + wpt : nwords;
+        uint32_t sum = 0;
+        for (uint32_t w = w0; w < w1; w++) sum += __popc(rbits[w]);
+        uint32_t nrk;
+        uint32_t r = block_exscan_u32<T>(sum, &nrk, warp_tot);
+        for (uint32_t w = w0; w < w1; w++) {
+          bits[w] = r;
+          r += __popc(rbits[w]);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nkeys; i += T) {
+          const uint32_t fk = pk[i], w = fk >> 5, bit = 1u << (fk & 31), rw = rbits[w];
+          if (rw & bit) map[bits[w] + __popc(rw & (bit - 1))] = (uint16_t)i;
+        }
+        __syncthreads();
+        const int oz = tg.op.order;
+        for (uint32_t k = threadIdx.x; k < reps; k += T) {
+          const u64 pos = gbase + Pq - 1 - k;
+          const uint32_t fk = oz ? (uint32_t)__ldcg(tg.coords + pos * oz) : 0u;
+          const double v = __ldcg(tg.vals + pos);
+          const uint32_t w = fk >> 5, bit = 1u << (fk & 31);
+          atomicAdd(tg.vals + gbase + map[bits[w] + __popc(rbits[w] & (bit - 1))], v);
+        }
+        if (threadIdx.x == 0) atomicAdd(sa.holes, (u64)reps);
+        __syncthreads();  // the lookups above read the bitmaps cleared below
+      }
+      // Every streamed segment is recorded: those whose outputs end above the final count are
+      // the sources of the hole filling, whatever their repeats.
+      if (threadIdx.x == 0) sa.rec[atomicAdd(sa.nrec, 1u)] = StreamRec{s_gbase, nkeys, Pq};
+      // ---- clear the bitmaps for the next segment or group.
+      for (uint32_t i = threadIdx.x; i < nwords / 4; i += T) {
+        reinterpret_cast<uint4*>(bits)[i] = make_uint4(0, 0, 0, 0);
+        reinterpret_cast<uint4*>(rbits)[i] = make_uint4(0, 0, 0, 0);
+      }
+      if (nwords < 4 && threadIdx.x < nwords) bits[threadIdx.x] = rbits[threadIdx.x] = 0;
+      if (threadIdx.x == 0) s_cnt = 0;
+      __syncthreads();
+    }
+  }
+}
+
+// Hole filling after the streaming kernel (its reservations are the last ones, so every
+// other kernel's outputs lie below the final count). Sources: the entries of streamed
+// segments at positions >= nnz; holes: the repeats' records below nnz. Both are numbered
+// through atomic counters; hole k receives source k.
+__global__ void __launch_bounds__(256) stream_sources_kernel(const StreamRec* __restrict__ rec,
+                                                             const unsigned* __restrict__ nrec, u64 nnz,
+                                                             u64* __restrict__ src_pos, u64* __restrict__ src_count) {
+  const unsigned lane = lane_id();
+  const unsigned nr = *nrec;
+  for (unsigned i = blockIdx.x * 8 + (threadIdx.x >> 5); i < nr; i += gridDim.x * 8) {
+    const StreamRec r = rec[i];
+    const u64 lo = r.base > nnz ? r.base : nnz, hi = r.base + r.firsts;
+    if (lo >= hi) continue;
+    u64 k0 = 0;
+    if (lane == 0) k0 = atomicAdd(src_count, hi - lo);
+    k0 = __shfl_sync(0xffffffffu, k0, 0);
+    for (u64 p = lo + lane; p < hi; p += 32) src_pos[k0 + (p - lo)] = p;
+  }
+}
+
+__global__ void __launch_bounds__(256) stream_fill_kernel(const StreamRec* __restrict__ rec,
+                                                          const unsigned* __restrict__ nrec, u64 nnz,
+                                                          const u64* __restrict__ src_pos, u64 nsrc,
+                                                          u64* __restrict__ hole_count, int32_t* __restrict__ coords,
+                                                          double* __restrict__ vals, int oz, uint32_t* status) {
+  const unsigned lane = lane_id();
+  const unsigned nr = *nrec;
+  for (unsigned i = blockIdx.x * 8 + (threadIdx.x >> 5); i < nr; i += gridDim.x * 8) {
+    const StreamRec r = rec[i];
+    const u64 lo = r.base + r.firsts, hi0 = r.base + r.products, hi = hi0 < nnz ? hi0 : nnz;
+    if (lo >= hi) continue;
+    u64 k0 = 0;
+    if (lane == 0) k0 = atomicAdd(hole_count, hi - lo);
+    k0 = __shfl_sync(0xffffffffu, k0, 0);
+    for (u64 h = lo + lane; h < hi; h += 32) {
+      const u64 k = k0 + (h - lo);
+      if (k >= nsrc) {
+        atomicOr(status, kStatOutOverflow);
+        continue;
+      }
+      const u64 s = src_pos[k];
+      for (int q = 0; q < oz; q++) coords[h * oz + q] = coords[s * oz + q];
+      vals[h] = vals[s];
+    }
+  }
+}
+
+
 // ---- small groups: one warp per group, each warp with its own table (group-per-warp
 // granularity). Everything a group needs stays inside its warp, so warp-level
 // synchronisation replaces block barriers and warps progress independently.
@@ -1670,6 +1988,38 @@ cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct
 }
 
 uint32_t dense_stash_cap() { return kStashCap; }
+uint32_t dense_stream_cap() { return kStreamCap; }
+
+cudaError_t launch_group_stream(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
+                                const uint32_t* list, uint32_t count, StreamArgs sa, int sms, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  if (seg < 64 || seg > kDenseSeg) return cudaErrorInvalidValue;
+  constexpr int U = STREAM_U;
+  auto kern = group_stream_kernel<U>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStreamThreads, kStreamSmem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const uint32_t cap = (uint32_t)(sms * per_sm);
+  kern<<<count < cap ? count : cap, kStreamThreads, kStreamSmem, s>>>(a, yoff, nseg, seg, list, count, sa);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream_fill(const StreamRec* rec, const unsigned* nrec, u64 nnz, u64 holes_total, u64* src_pos,
+                               u64* counters2, int32_t* coords, double* vals, int oz, uint32_t* status, int sms,
+                               cudaStream_t s) {
+  if (holes_total == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counters2, 0, 2 * sizeof(u64), s);
+  if (e != cudaSuccess) return e;
+  const unsigned g = (unsigned)sms * 8;
+  stream_sources_kernel<<<g, 256, 0, s>>>(rec, nrec, nnz, src_pos, counters2);
+  stream_fill_kernel<<<g, 256, 0, s>>>(rec, nrec, nnz, src_pos, holes_total, counters2 + 1, coords, vals, oz, status);
+  note_launch(2);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_group_dense(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
                                const uint32_t* stash_list, uint32_t stash_count, const uint32_t* rank_list,

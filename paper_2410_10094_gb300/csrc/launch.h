@@ -114,6 +114,7 @@ struct Bins {
   uint32_t* dense_list[2];    // null when not used
   u64 dense_min;
   u64 stash_cap;
+  int stream;                 // list 0 is streamed: its groups' output bound is B_g itself
   uint32_t* huge_list;        // overflow groups, their table offsets and capacities
   u64* huge_off;
   u64* huge_cap;
@@ -241,6 +242,27 @@ cudaError_t launch_batch_group(const BatchArgs& ba, GroupedX gx, const Bins& b, 
 constexpr uint32_t kDenseSeg = 65536;
 constexpr size_t kBitmapSmemPerCta = 112 * 1024;  // two CTAs per SM
 uint32_t dense_stash_cap();
+
+// Streamed bitmap rows: per group segment, its reservation and counts, for the hole filling
+// that follows.
+struct StreamRec {
+  u64 base;           // first reserved position
+  uint32_t firsts;    // outputs (first products), at [base, base + firsts)
+  uint32_t products;  // reserved positions
+};
+struct StreamArgs {
+  StreamRec* rec;
+  unsigned* nrec;  // segments recorded
+  u64* holes;      // total repeats (positions that hold no output at the end)
+};
+uint32_t dense_stream_cap();
+// Streamed groups (B_g <= dense_stream_cap()); launched after every other accumulation kernel.
+cudaError_t launch_group_stream(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
+                                const uint32_t* list, uint32_t count, StreamArgs sa, int sms, cudaStream_t s);
+// Moves the entries above nnz into the holes below it.
+cudaError_t launch_stream_fill(const StreamRec* rec, const unsigned* nrec, u64 nnz, u64 holes_total, u64* src_pos,
+                               u64* counters2, int32_t* coords, double* vals, int oz, uint32_t* status, int sms,
+                               cudaStream_t s);
 cudaError_t launch_group_dense(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
                                const uint32_t* stash_list, uint32_t stash_count, const uint32_t* rank_list,
                                uint32_t rank_count, int sms, cudaStream_t s);
