@@ -317,6 +317,7 @@ struct StageTimer {
   }
   void collect(stc_stats& stats) {
     if (!on) return;
+    if (!ev.empty()) cudaEventSynchronize(ev.back());  // stage times are a diagnostic: wait for them
     for (size_t i = 1; i < ev.size(); i++) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
@@ -608,7 +609,8 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   STC_TRY(read_counters(pr, s, h2));
   r->nnz = (int64_t)(h2.nz - holes);
   if (holes) {
-    u64* src_pos = nullptr;
+    if (holes >= (1ull << 32)) return fail(STC_ERR_UNSUPPORTED, "more than 2^32 repeated products in streamed groups");
+    uint32_t* src_pos = nullptr;
     STC_TRY(ar.alloc(&src_pos, (size_t)holes));
     STC_CUDA(launch_stream_fill(sa.rec, sa.nrec, (u64)r->nnz, holes, src_pos, gc->fill_counters, r->coords,
                                 r->vals, pl.oz, &pr.ctr->status, ctx->sms, s));

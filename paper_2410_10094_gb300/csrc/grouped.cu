@@ -1504,7 +1504,7 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
                                               (int32_t)((uint32_t)(z >> tg.op.shift[2]) & ((uint32_t)tg.op.mod[2] - 1)),
                                               (int32_t)((uint32_t)(z >> tg.op.shift[3]) & ((uint32_t)tg.op.mod[3] - 1)));
                     st_stream_v4(coords + pos * 4, cv, pol);
-                    st_stream_f64(vals + pos, prod, pol);
+                    vals[pos] = prod;  // default policy: a repeat may still add to it
                   } else {
                     store_output(coords, vals, pos, z, prod, tg.op, pol);
                   }
@@ -1575,7 +1575,7 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
 // through atomic counters; hole k receives source k.
 __global__ void __launch_bounds__(256) stream_sources_kernel(const StreamRec* __restrict__ rec,
                                                              const unsigned* __restrict__ nrec, u64 nnz,
-                                                             u64* __restrict__ src_pos, u64* __restrict__ src_count) {
+                                                             uint32_t* __restrict__ src_pos, u64* __restrict__ src_count) {
   const unsigned lane = lane_id();
   const unsigned nr = *nrec;
   for (unsigned i = blockIdx.x * 8 + (threadIdx.x >> 5); i < nr; i += gridDim.x * 8) {
@@ -1585,13 +1585,13 @@ __global__ void __launch_bounds__(256) stream_sources_kernel(const StreamRec* __
     u64 k0 = 0;
     if (lane == 0) k0 = atomicAdd(src_count, hi - lo);
     k0 = __shfl_sync(0xffffffffu, k0, 0);
-    for (u64 p = lo + lane; p < hi; p += 32) src_pos[k0 + (p - lo)] = p;
+    for (u64 p = lo + lane; p < hi; p += 32) src_pos[k0 + (p - lo)] = (uint32_t)(p - nnz);
   }
 }
 
 __global__ void __launch_bounds__(256) stream_fill_kernel(const StreamRec* __restrict__ rec,
                                                           const unsigned* __restrict__ nrec, u64 nnz,
-                                                          const u64* __restrict__ src_pos, u64 nsrc,
+                                                          const uint32_t* __restrict__ src_pos, u64 nsrc,
                                                           u64* __restrict__ hole_count, int32_t* __restrict__ coords,
                                                           double* __restrict__ vals, int oz, uint32_t* status) {
   const unsigned lane = lane_id();
@@ -1609,8 +1609,12 @@ __global__ void __launch_bounds__(256) stream_fill_kernel(const StreamRec* __res
         atomicOr(status, kStatOutOverflow);
         continue;
       }
-      const u64 s = src_pos[k];
-      for (int q = 0; q < oz; q++) coords[h * oz + q] = coords[s * oz + q];
+      const u64 s = nnz + src_pos[k];
+      if (oz == 4 && ((reinterpret_cast<uintptr_t>(coords) & 15u) == 0)) {
+        reinterpret_cast<int4*>(coords)[h] = reinterpret_cast<const int4*>(coords)[s];
+      } else {
+        for (int q = 0; q < oz; q++) coords[h * oz + q] = coords[s * oz + q];
+      }
       vals[h] = vals[s];
     }
   }
@@ -2008,7 +2012,7 @@ cudaError_t launch_group_stream(const GroupArgs& a, const uint32_t* yoff, uint32
   return cudaGetLastError();
 }
 
-cudaError_t launch_stream_fill(const StreamRec* rec, const unsigned* nrec, u64 nnz, u64 holes_total, u64* src_pos,
+cudaError_t launch_stream_fill(const StreamRec* rec, const unsigned* nrec, u64 nnz, u64 holes_total, uint32_t* src_pos,
                                u64* counters2, int32_t* coords, double* vals, int oz, uint32_t* status, int sms,
                                cudaStream_t s) {
   if (holes_total == 0) return cudaSuccess;

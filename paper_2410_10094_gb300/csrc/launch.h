@@ -260,7 +260,8 @@ uint32_t dense_stream_cap();
 cudaError_t launch_group_stream(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
                                 const uint32_t* list, uint32_t count, StreamArgs sa, int sms, cudaStream_t s);
 // Moves the entries above nnz into the holes below it.
-cudaError_t launch_stream_fill(const StreamRec* rec, const unsigned* nrec, u64 nnz, u64 holes_total, u64* src_pos,
+// holes_total < 2^32 (positions above nnz are kept as 32-bit offsets).
+cudaError_t launch_stream_fill(const StreamRec* rec, const unsigned* nrec, u64 nnz, u64 holes_total, uint32_t* src_pos,
                                u64* counters2, int32_t* coords, double* vals, int oz, uint32_t* status, int sms,
                                cudaStream_t s);
 cudaError_t launch_group_dense(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
