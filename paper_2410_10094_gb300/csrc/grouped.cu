@@ -105,6 +105,7 @@ __device__ __forceinline__ void resolve_target(const GroupArgs& a, u64 g, unsign
   const uint32_t p = a.gprob ? a.gprob[g] : 0u;
   const BatchOut* bo = a.bout + p;
   const u64 FY = bo->FY;
+  t.FY = FY;
   t.zrow = (a.gfk ? a.gfk[g] : g) * FY;
   t.counter = a.bnz + p;
   t.base = n ? atomicAdd(a.bnz + p, (u64)n) : 0;
@@ -1347,6 +1348,10 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
   __shared__ OutTarget tg;
   __shared__ u64 s_gbase;
   __shared__ uint32_t s_cnt;
+  // Order-4 power-of-two outputs: each coordinate is either constant over the segment or a bit
+  // field of the segment-relative free key fy = q * seg + fk; coordinate = cst | (fy >> sh) & mk.
+  __shared__ int4 s_cst;
+  __shared__ uint4 s_sh, s_mk;
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   const uint64_t keep = policy_evict_last();
@@ -1380,6 +1385,22 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
     const double my_v = pf_v;
     prefetch(gi + gridDim.x);
     for (uint32_t q = 0; q < nseg; q++) {
+      if (threadIdx.x == 0 && tg.op.order == 4 && tg.op.pow2) {
+        // Published by the staging scan's barriers below.
+        const uint32_t b = 63 - __clzll(tg.FY);
+        uint32_t c[4], sh[4], mk[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const uint32_t sk = tg.op.shift[k], mkk = (uint32_t)tg.op.mod[k] - 1;
+          const bool cst = sk >= b;
+          c[k] = cst ? (uint32_t)(tg.zrow >> sk) & mkk : 0u;
+          sh[k] = cst ? 0u : sk;
+          mk[k] = cst ? 0u : mkk;
+        }
+        s_cst = make_int4((int32_t)c[0], (int32_t)c[1], (int32_t)c[2], (int32_t)c[3]);
+        s_sh = make_uint4(sh[0], sh[1], sh[2], sh[3]);
+        s_mk = make_uint4(mk[0], mk[1], mk[2], mk[3]);
+      }
       // The segment's products, reserved up front (a separate count pass for long groups).
       uint32_t Pq = 0;
       if (!one_chunk) {
@@ -1497,16 +1518,16 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
                   const uint32_t place = (base & 0xffffu) + __popc(fm & lt);
                   pk[place] = (uint16_t)fk;
                   const u64 pos = gbase + place;
-                  const u64 z = zseg + fk;
                   if (v4) {
-                    const int4 cv = make_int4((int32_t)((uint32_t)(z >> tg.op.shift[0]) & ((uint32_t)tg.op.mod[0] - 1)),
-                                              (int32_t)((uint32_t)(z >> tg.op.shift[1]) & ((uint32_t)tg.op.mod[1] - 1)),
-                                              (int32_t)((uint32_t)(z >> tg.op.shift[2]) & ((uint32_t)tg.op.mod[2] - 1)),
-                                              (int32_t)((uint32_t)(z >> tg.op.shift[3]) & ((uint32_t)tg.op.mod[3] - 1)));
+                    const uint32_t fy = q * seg + fk;
+                    const int4 cb = s_cst;
+                    const uint4 sh = s_sh, mk = s_mk;
+                    const int4 cv = make_int4(cb.x | (int32_t)((fy >> sh.x) & mk.x), cb.y | (int32_t)((fy >> sh.y) & mk.y),
+                                              cb.z | (int32_t)((fy >> sh.z) & mk.z), cb.w | (int32_t)((fy >> sh.w) & mk.w));
                     st_stream_v4(coords + pos * 4, cv, pol);
                     vals[pos] = prod;  // default policy: a repeat may still add to it
                   } else {
-                    store_output(coords, vals, pos, z, prod, tg.op, pol);
+                    store_output(coords, vals, pos, zseg + fk, prod, tg.op, pol);
                   }
                 } else {
                   const u64 pos = gbase + Pq - 1 - ((base >> 16) + __popc(rm & lt));

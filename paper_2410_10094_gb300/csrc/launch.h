@@ -156,6 +156,7 @@ struct GroupArgs {
 
 // Where one group's outputs go, resolved once per group.
 struct OutTarget {
+  u64 FY;        // Y free key space of the group's problem
   u64 zrow;      // output key of the group's row: fX * F_Y
   u64 base;      // first output position reserved for the group
   u64 cap;       // output capacity of the group's problem
