@@ -440,12 +440,9 @@ uint64_t grouped_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t P) {
   return b;
 }
 
-// Bitmap-row groups that fit are streamed (outputs written during the first pass).
-constexpr bool kStreamGroups = true;
-
 // Counters of the grouping and binning passes, read back with the first host sync.
 struct GroupCounters {
-  uint32_t count[kMaxClasses + 3];
+  uint32_t count[kMaxClasses + 4];
   unsigned stream_nrec;  // streamed segments with repeats
   u64 huge_slots;
   u64 out_cap;
@@ -508,10 +505,9 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
     // With AUTO, groups that fit the warp classes keep their hash tables (a bitmap sweep costs
     // a fixed amount per segment).
     b.dense_min = o.accumulator == STC_ACC_DENSE ? 0 : (b.tmax[1] + 1) * nseg;
-    b.stream = kStreamGroups;
-    b.stash_cap = kStreamGroups ? dense_stream_cap() : dense_stash_cap();
-    STC_TRY(ar.alloc(&b.dense_list[0], maxg));
-    STC_TRY(ar.alloc(&b.dense_list[1], maxg));
+    b.stream_cap = dense_stream_cap();
+    b.stash_cap = dense_stash_cap();
+    for (int d = 0; d < 3; d++) STC_TRY(ar.alloc(&b.dense_list[d], maxg));
   }
   STC_TRY(ar.alloc(&b.huge_list, maxg));
   STC_TRY(ar.alloc(&b.huge_off, maxg));
@@ -540,8 +536,8 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   r->stats.products = h.P;
   r->stats.survivors = h.ns;
   uint64_t groups = 0, dense_groups = 0;
-  for (int c = 0; c < kMaxClasses + 3; c++) groups += hg.count[c];
-  dense_groups = hg.count[kMaxClasses + 1] + hg.count[kMaxClasses + 2];
+  for (int c = 0; c < kMaxClasses + 4; c++) groups += hg.count[c];
+  dense_groups = hg.count[kMaxClasses + 1] + hg.count[kMaxClasses + 2] + hg.count[kMaxClasses + 3];
   r->stats.groups = groups;
   r->stats.table_slots = hg.huge_slots;
   r->stats.accumulator = dense_groups == 0 ? STC_ACC_HASH : (dense_groups == groups ? STC_ACC_DENSE : STC_ACC_AUTO);
@@ -590,11 +586,11 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
     STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
   }
   StreamArgs sa{};
-  const uint32_t nstream = dense_rows && kStreamGroups ? hg.count[kMaxClasses + 1] : 0u;
+  const uint32_t nstream = dense_rows ? hg.count[kMaxClasses + 1] : 0u;
   if (dense_rows) {
     // Streamed groups go last: every other kernel's outputs then lie below the final count.
-    STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.dense_list[0], kStreamGroups ? 0u : hg.count[kMaxClasses + 1],
-                                b.dense_list[1], hg.count[kMaxClasses + 2], ctx->sms, s));
+    STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.dense_list[2], hg.count[kMaxClasses + 3], b.dense_list[1],
+                                hg.count[kMaxClasses + 2], ctx->sms, s));
     if (nstream) {
       STC_TRY(ar.alloc(&sa.rec, (size_t)nstream * nseg));
       sa.nrec = &gc->stream_nrec;

@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(kThreads) bin_groups_kernel(u64 FX, const uint
       while (c < b.nclasses && t > b.tmax[c]) c++;
       if (b.dense_list[0] && t >= b.dense_min) {
         // Streamed groups reserve one output position per product (their repeats' records).
-        const int d = bnd <= b.stash_cap ? 0 : 1;
-        my_cap += d == 0 && b.stream ? bnd : t;
+        const int d = (bnd <= b.stream_cap && 2 * bnd <= FY) ? 0 : (bnd <= b.stash_cap ? 2 : 1);
+        my_cap += d == 0 ? bnd : t;
         const uint32_t idx = atomicAdd(b.count + kMaxClasses + 1 + d, 1u);
         b.dense_list[d][idx] = (uint32_t)g;
       } else if (c < b.nclasses) {

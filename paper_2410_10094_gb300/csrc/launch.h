@@ -108,13 +108,15 @@ struct Bins {
   int nclasses;
   u64 tmax[kMaxClasses];      // a group goes to the first class with t <= tmax
   uint32_t* list[kMaxClasses];
-  uint32_t* count;            // [kMaxClasses + 3]: classes, overflow groups, stash, rank
+  uint32_t* count;            // [kMaxClasses + 4]: classes, overflow groups, stream, rank, stash
   // Bitmap-row accumulation (single contractions with per-segment runs): groups with
-  // t >= dense_min go to the stash list when B_g <= stash_cap, else to the rank list.
-  uint32_t* dense_list[2];    // null when not used
+  // t >= dense_min go to the stream list (0) when B_g <= stream_cap and repeats are expected
+  // to be few (2 B_g <= F_Y), else to the stash list (2) when B_g <= stash_cap, else to the
+  // rank list (1). A streamed group's output bound is B_g itself.
+  uint32_t* dense_list[3];    // null when not used
   u64 dense_min;
+  u64 stream_cap;
   u64 stash_cap;
-  int stream;                 // list 0 is streamed: its groups' output bound is B_g itself
   uint32_t* huge_list;        // overflow groups, their table offsets and capacities
   u64* huge_off;
   u64* huge_cap;
