@@ -182,7 +182,8 @@ def dist_env():
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
 # kernel, from an ncu capture of the current kernels with the default strategy and
 # accumulator; workloads without a capture report null.
-NCU_TRAFFIC = {"imbalanced": ("x_survey_kernel", 0.2746e9 + 0.0074e9)}
+NCU_TRAFFIC = {"plain_large": ("group_stream_kernel", 2.956e9 + 9.284e9),
+               "imbalanced": ("x_survey_kernel", 0.2746e9 + 0.0075e9)}
 
 
 def l2_note(bytes_in, bytes_out, l2=129e6):
