@@ -43,7 +43,7 @@ typedef enum stc_status {
   STC_ERR_TIMEOUT = 6,            /* a bounded wait gave up */
   STC_ERR_CUDA = 7,               /* a CUDA runtime call failed; see stc_last_error() */
   STC_ERR_COORD_OUT_OF_RANGE = 8, /* an input coordinate is negative or >= its mode length */
-  STC_ERR_UNSUPPORTED = 9         /* valid input outside what this build implements */
+  STC_ERR_UNSUPPORTED = 9         /* valid input outside what the library implements */
 } stc_status;
 
 #define STC_MAX_ORDER 8            /* modes per input tensor */
