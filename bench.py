@@ -130,6 +130,13 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         lo, hi = self.window if self.window else (float("-inf"), float("inf"))
         inside = [ln for t, ln in self.lines if lo <= t <= hi]
+        where = "timed window"
+        if not inside and self.lines:
+            # A timed region shorter than the sampling period: the samples nearest to it
+            # (the warm-up just before and the stage pass just after run the same work).
+            near = sorted(self.lines, key=lambda tl: min(abs(tl[0] - lo), abs(tl[0] - hi)))[:4]
+            inside = [ln for _, ln in near]
+            where = "nearest samples (timed region shorter than the sampling period)"
         for ln in inside:
             parts = [p.strip() for p in ln.split(",")][1:]
             if len(parts) != len(self.FIELDS) - 1:
@@ -149,7 +156,7 @@ class ClockSampler:
                     "first": self.lines[0][0] if self.lines else None,
                     "last": self.lines[-1][0] if self.lines else None, "window": self.window}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm), "period_ms": self.period_ms}
+                "samples": len(sm), "period_ms": self.period_ms, "from": where}
 
 
 def replica_seed(workload: str, rank: int) -> int:
@@ -422,7 +429,6 @@ def main(argv=None):
     ev1.record(stream)
     torch.cuda.synchronize()
     clk.mark(tw0, time.time())
-    clk.stop()
     barrier()
     ms, total_products = reduce_over_ranks(ev0.elapsed_time(ev1), float(P), world, "cuda")
     value = total_products * args.steps / (ms / 1e3)
@@ -435,6 +441,7 @@ def main(argv=None):
         stage[: len(r.stats.stage_ms)] += np.asarray(r.stats.stage_ms)
         del r
     torch.cuda.synchronize()
+    clk.stop()
 
     # ---- e2e: the public API call with host buffers, copies inside the timed region
     e2e = None
