@@ -6,12 +6,28 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "launch.h"
 
 using namespace stc;
+
+// Autotuning of batches (group load factor, which also decides which groups get a warp of
+// their own): per size bucket, each candidate is timed once with CUDA events around the
+// accumulation kernels, read back without a sync on a later call of the same bucket; then
+// the fastest is kept.
+constexpr double kTuneAlpha[] = {0.5, 0.75, 0.9};
+constexpr int kTuneCand = 3;
+struct TuneEntry {
+  int best = -1;
+  float ms[kTuneCand] = {};
+  bool done[kTuneCand] = {};
+  bool pending[kTuneCand] = {};
+  cudaEvent_t ev0[kTuneCand] = {}, ev1[kTuneCand] = {};
+};
 
 struct stc_ctx {
   int device = 0;
@@ -20,7 +36,60 @@ struct stc_ctx {
   std::atomic<size_t> held{0};
   std::atomic<int64_t> live_results{0};
   int sms = 0;
+  std::mutex tune_mu;
+  std::map<int, TuneEntry> tune;
 };
+
+namespace {
+// Picks the load factor for a batch of this bucket; *measure is the candidate to time (or -1).
+double tune_pick(stc_ctx* ctx, int bucket, int* measure) {
+  std::lock_guard<std::mutex> lk(ctx->tune_mu);
+  TuneEntry& te = ctx->tune[bucket];
+  *measure = -1;
+  if (te.best >= 0) return kTuneAlpha[te.best];
+  for (int c = 0; c < kTuneCand; c++) {
+    if (te.pending[c] && cudaEventQuery(te.ev1[c]) == cudaSuccess) {
+      cudaEventElapsedTime(&te.ms[c], te.ev0[c], te.ev1[c]);
+      te.pending[c] = false;
+      te.done[c] = true;
+    }
+  }
+  int best = 0;
+  bool all = true;
+  for (int c = 0; c < kTuneCand; c++) {
+    all = all && te.done[c];
+    if (te.done[c] && te.ms[c] < te.ms[best]) best = c;
+    if (te.done[c] && !te.done[best]) best = c;
+  }
+  if (all) {
+    te.best = best;
+    return kTuneAlpha[best];
+  }
+  for (int c = 0; c < kTuneCand; c++) {
+    if (!te.done[c] && !te.pending[c]) {
+      if (!te.ev0[c] && (cudaEventCreate(&te.ev0[c]) != cudaSuccess || cudaEventCreate(&te.ev1[c]) != cudaSuccess))
+        return 0.75;
+      *measure = c;
+      te.pending[c] = true;
+      return kTuneAlpha[c];
+    }
+  }
+  return 0.75;  // every remaining candidate is still being timed
+}
+void tune_mark(stc_ctx* ctx, int bucket, int cand, bool end, cudaStream_t s) {
+  if (cand < 0) return;
+  std::lock_guard<std::mutex> lk(ctx->tune_mu);
+  TuneEntry& te = ctx->tune[bucket];
+  cudaEventRecord(end ? te.ev1[cand] : te.ev0[cand], s);
+}
+// A batch that failed after picking a candidate gives it back.
+void tune_abort(stc_ctx* ctx, int bucket, int cand) {
+  if (cand < 0) return;
+  std::lock_guard<std::mutex> lk(ctx->tune_mu);
+  ctx->tune[bucket].pending[cand] = false;
+}
+int log2_floor(uint64_t v) { return v ? 63 - __builtin_clzll(v) : 0; }
+}  // namespace
 
 // Device memory owned by one or more results (a batch's results share one block); returned to
 // the context's pool, in the order of the stream it was made on, when the last owner goes.
@@ -706,6 +775,11 @@ stc_status stc_destroy(stc_ctx* ctx) {
                 (long long)ctx->live_results.load());
   DeviceGuard g(ctx->device);
   cudaDeviceSynchronize();
+  for (auto& kv : ctx->tune)
+    for (int c = 0; c < kTuneCand; c++) {
+      if (kv.second.ev0[c]) cudaEventDestroy(kv.second.ev0[c]);
+      if (kv.second.ev1[c]) cudaEventDestroy(kv.second.ev1[c]);
+    }
   cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return STC_OK;
@@ -829,8 +903,8 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
   for (int32_t i = 0; i < n; i++) outs[i] = nullptr;
   if (n == 0) return STC_OK;
   const stc_opts o = opts ? *opts : stc_opts{};
-  const double ga = (o.group_load_factor > 0.0) ? o.group_load_factor : 0.75;
-  if (!(ga > 0.0 && ga <= 0.9)) return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", ga);
+  if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
+    return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
 
   std::vector<Plan> plans(n);
   std::vector<BatchProb> hb(n);
@@ -865,6 +939,18 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
       return fail(STC_ERR_INVALID_ARG, "the batch holds more than STC_MAX_NNZ entries of X or of Y");
   }
   const int64_t total_x = xrow[n], total_y = yrow[n];
+  // Load factor: given, or picked by the autotuner for this size bucket (entries, problems).
+  int tune_cand = -1;
+  const int tune_bucket = log2_floor((uint64_t)(total_x + total_y)) * 32 + std::min(31, log2_floor((uint64_t)n));
+  const double ga = o.group_load_factor > 0.0 ? o.group_load_factor : tune_pick(ctx, tune_bucket, &tune_cand);
+  struct TuneGuard {  // gives a picked candidate back if the batch fails before it is timed
+    stc_ctx* c;
+    int b, k;
+    bool armed = true;
+    ~TuneGuard() {
+      if (armed) tune_abort(c, b, k);
+    }
+  } tune_guard{ctx, tune_bucket, tune_cand};
 
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
@@ -1027,8 +1113,11 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
     u64 maxcap = 0;
     for (int32_t i = 0; i < n; i++) maxcap = std::max<u64>(maxcap, hper[n + i]);
     const bool direct = !wide && maxcap < 0xffffffffull && o.accumulator != STC_ACC_HASH_SCAN;
+    tune_mark(ctx, tune_bucket, tune_cand, false, s);
     STC_CUDA(launch_group_classes(a, wide, direct, b, hg.count, ctx->sms, s));
     STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
+    tune_mark(ctx, tune_bucket, tune_cand, true, s);
+    tune_guard.armed = false;
   }
   tm.mark(4);
   STC_CUDA(cudaMemcpyAsync(hper.data() + 2 * n, per + 2 * n, n * sizeof(u64), cudaMemcpyDeviceToHost, s));

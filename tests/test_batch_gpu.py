@@ -124,3 +124,21 @@ def test_batched_workload_full():
         assert torch.equal(ka, kb)
         assert torch.allclose(vb, va, rtol=1e-9, atol=1e-12)
         del alone, ka, va, kb, vb
+
+
+def test_batch_autotuned_calls_agree():
+    """Repeated calls on one size bucket: the autotuner tries each load factor once and then
+    keeps the fastest; every call's results match the oracle."""
+    rng = W.rng_for(8400)
+    probs = [W.small_pair(rng, nnz_hi=2e3) for _ in range(48)]
+    refs = [oracle.contract(p.X, p.Y, p.cx, p.cy) for p in probs]
+    import paper_2410_10094_gb300 as stc
+
+    ctx = stc.Context(0)
+    bp = stc.BatchProblems([(to_dev(p.X), to_dev(p.Y), p.cx, p.cy, p.out_order) for p in probs])
+    for _ in range(5):
+        res = stc.contract_batch(bp, ctx=ctx)
+        for ref, r in zip(refs, res):
+            c, v = host(r)
+            assert_matches_oracle(c, v, ref)
+        del res
