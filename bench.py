@@ -46,9 +46,10 @@ WORKLOADS = {
     "imbalanced": lambda seed: W.imbalanced(seed=seed),
     "imbalanced_both": lambda seed: W.imbalanced(seed=seed, both_zipf=True),
     "plain_small": lambda seed: W.plain_small(seed=seed),
+    "wide_keys": lambda seed: W.wide_keys(seed=seed),
 }
 SEEDS = {"batched": W.SEED_BASE + 4, "plain_large": W.SEED_BASE + 2, "plain_large_slice": W.SEED_BASE + 2, "imbalanced": W.SEED_BASE + 3, "imbalanced_both": W.SEED_BASE + 3,
-         "plain_small": W.SEED_BASE + 1}
+         "plain_small": W.SEED_BASE + 1, "wide_keys": W.SEED_BASE + 6}
 DESCRIPTIONS = {
     "batched": "2,048 order-3 pairs, lengths 16..512, one paired mode, nnz log-uniform 1e2..1e5 each, one batch call",
     "plain_large_slice": "X 16x256^3 3.125e5 nnz, Y 256^4 5e6 nnz, X modes (2,3) x Y modes (0,1) (profiling slice)",
@@ -56,9 +57,12 @@ DESCRIPTIONS = {
     "imbalanced": "X 4096x512x512 2e7 nnz, Y 512x512x64 2e4 nnz with Zipf(1.2) contract keys, X (1,2) x Y (0,1)",
     "imbalanced_both": "as imbalanced, X contract keys also Zipf(1.2)",
     "plain_small": "X,Y order-3 64^3 COO, 5e3 distinct nnz each, X mode 2 x Y mode 0",
+    "wide_keys": "X 256x256x65536x65536, Y 65536x65536x256x256, 5e6 nnz each, X modes (2,3) x Y modes (0,1) "
+                 "(2^32 contract keys, renumbered to dense ids); paired cells from one pool of 65,536",
 }
 # Rows of X (first coordinate < bound) that make the oracle's bounded CPU sample.
-CPU_SAMPLE_X0 = {"batched": 0, "plain_large": 7, "plain_large_slice": 1, "imbalanced": 4096, "imbalanced_both": 64, "plain_small": 64}
+CPU_SAMPLE_X0 = {"batched": 0, "plain_large": 7, "plain_large_slice": 1, "imbalanced": 4096, "imbalanced_both": 64, "plain_small": 64,
+                 "wide_keys": 7}
 
 
 def peaks():
@@ -410,6 +414,7 @@ def main(argv=None):
     for _ in range(args.warmup):
         r = step()
         nz, oz, P, launches, ns = r.nnz, r.order, r.stats.products, r.stats.launches, r.stats.survivors
+        cids = r.stats.contract_ids
         del r
     torch.cuda.synchronize()
 
@@ -539,7 +544,8 @@ def main(argv=None):
         "config": {"workload": f"{args.workload}: {DESCRIPTIONS[args.workload]}", "seed": seed,
                    "products_per_step": P, "nnz_out": nz, "parallelism": f"replicas x{world}",
                    "l2": l2_note(bytes_in, (4 * oz + 8) * nz), "strategy": args.strategy,
-                   "group_load_factor": args.group_load_factor, "accumulator": args.accumulator},
+                   "group_load_factor": args.group_load_factor, "accumulator": args.accumulator,
+                   "contract_ids": int(cids)},
         "step_hbm": {"alg_bytes": step_alg, "gbs": step_alg / (step_ms / 1e3) / 1e9,
                      "frac": step_alg / (step_ms / 1e3) / 1e9 / hbm},
         "stage_ms": {n: float(per_step[i]) for i, n in enumerate(stage_names)},

@@ -101,6 +101,8 @@ typedef struct stc_stats {
   int32_t accumulator;    /* GROUPED: STC_ACC_HASH or STC_ACC_DENSE when every group used that
                              accumulator, STC_ACC_AUTO when both ran */
   float stage_ms[8];      /* 0 group Y, 1 survey X, 2 group X, 3 plan, 4 accumulate, 5 compact/write */
+  uint64_t contract_ids;  /* distinct contract keys of Y when the contract key space was renumbered
+                             to dense ids (key space > 2^26), else 0 */
 } stc_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -130,6 +132,9 @@ stc_status stc_destroy(stc_ctx* ctx);
  *   out         receives the result
  * Output: every coordinate that received at least one product, once, with the sum of its
  * products (a structural nonzero is kept even if it sums to 0.0), in unspecified order.
+ * Contract key spaces above 2^26 are first renumbered to dense ids (Section 4.1.2, as
+ * stc_dense_ids does): stats.contract_ids then holds the number of distinct contract keys
+ * of Y, which must stay below 2^26 (else UNSUPPORTED).
  * Errors: INVALID_ARG, SHAPE_MISMATCH, KEY_OVERFLOW (output key space > 2^64 - 2),
  * COORD_OUT_OF_RANGE (checked on the device), OUT_OF_MEMORY, UNSUPPORTED, CUDA. */
 stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t ncontract,
@@ -222,6 +227,19 @@ stc_status stc_linearize(stc_ctx* ctx, const stc_coo* T, int32_t nmodes, const i
  * n <= STC_MAX_NNZ and k <= 2^26. */
 stc_status stc_group_keys(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t k,
                           uint32_t* offsets_out, uint32_t* perm_out, void* stream);
+
+/* Small numbers for large keys (Section 4.1.2, Fig. 6): ids_out[i] = the dense id of
+ * keys[i], with ids in [0, D), equal keys sharing one id and distinct keys distinct ids,
+ * where D = the number of distinct keys, written to *ndistinct. Every 64-bit value is a
+ * valid key. Which key gets which id is unspecified (the paper numbers keys in order of
+ * first sight; here they are numbered in the order of their hash-table slots), so ids
+ * feed stc_group_keys with k = D.
+ *   keys: device, [n], read only; ids_out: device, [n], written; ndistinct: host.
+ *   n <= STC_MAX_NNZ; the call allocates a table of about 64 n bytes from the context and
+ *   returns after its device work completes (it reads D back).
+ * Errors: INVALID_ARG (NULL pointer, n out of range), OUT_OF_MEMORY, CUDA. */
+stc_status stc_dense_ids(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint32_t* ids_out,
+                         uint64_t* ndistinct, void* stream);
 
 /* stc_group_keys without allocation. The paper has no counterpart: this entry point exists
  * for callers that must not allocate device memory, for example a process whose device memory

@@ -52,7 +52,7 @@ class stc_stats(C.Structure):
     _fields_ = [("products", C.c_uint64), ("survivors", C.c_uint64), ("out_capacity", C.c_uint64),
                 ("table_slots", C.c_uint64), ("groups", C.c_uint64), ("strategy", C.c_int32),
                 ("nstages", C.c_int32), ("launches", C.c_uint32), ("accumulator", C.c_int32),
-                ("stage_ms", C.c_float * 8)]
+                ("stage_ms", C.c_float * 8), ("contract_ids", C.c_uint64)]
 
 
 EXPORTS = {
@@ -76,6 +76,7 @@ EXPORTS = {
     "stc_group_keys": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p],
                        C.c_int),
     "stc_group_keys_static": ([C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "stc_dense_ids": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_uint64), C.c_void_p], C.c_int),
     "stc_result_info": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                          C.POINTER(C.POINTER(C.c_int64))], C.c_int),
     "stc_result_data": ([C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)], C.c_int),
@@ -245,6 +246,16 @@ def stc_group_keys(ctx: int, keys, k: int, offsets_out, perm_out, stream=None):
                                 C.c_void_p(_stream_handle(stream))))
 
 
+def stc_dense_ids(ctx: int, keys, ids_out, stream=None) -> int:
+    """Dense ids of device uint64/int64 keys into int32/uint32 ids_out; returns D."""
+    n = int(keys.numel())
+    d = C.c_uint64()
+    check(load().stc_dense_ids(C.c_void_p(ctx), C.c_void_p(keys.data_ptr() if n else 0), n,
+                               C.c_void_p(ids_out.data_ptr() if n else 0), C.byref(d),
+                               C.c_void_p(_stream_handle(stream))))
+    return d.value
+
+
 def stc_group_keys_static(keys, k: int, offsets_out, perm_out, stream=None):
     """stc_group_keys without allocation (fixed device scratch; k <= 262144). Runs on the
     current device; calls that overlap on the GPU race on the shared scratch."""
@@ -339,6 +350,7 @@ class Stats:
     launches: int
     accumulator: int
     stage_ms: tuple
+    contract_ids: int = 0
 
 
 class Result:
@@ -352,7 +364,8 @@ class Result:
         self.nnz, self.order, self.shape = stc_result_info(handle)
         st = stc_result_stats(handle)
         self.stats = Stats(st.products, st.survivors, st.out_capacity, st.table_slots, st.groups, st.strategy,
-                           st.launches, st.accumulator, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))))
+                           st.launches, st.accumulator, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))),
+                           st.contract_ids)
         self._coords = self._vals = None
 
     @property
@@ -467,6 +480,16 @@ def linearize(T, modes, *, stream=None, ctx: Context = None):
     out = torch.empty(n, dtype=torch.int64, device="cuda")
     stc_linearize(ctx.handle, T, modes, out, stream)
     return out
+
+
+def dense_ids(keys, *, stream=None, ctx: Context = None):
+    """Small numbers for large keys (Section 4.1.2): returns (ids int32 [n], D)."""
+    import torch
+
+    ctx = ctx or default_context()
+    ids = torch.empty(int(keys.numel()), dtype=torch.int32, device="cuda")
+    d = stc_dense_ids(ctx.handle, keys, ids, stream)
+    return ids, d
 
 
 def group_keys(keys, k: int, *, stream=None, ctx: Context = None):

@@ -695,6 +695,74 @@ int pick_strategy(const Plan& pl, const stc_coo* X, int requested) {
   return STC_STRATEGY_GLOBAL;
 }
 
+// A contraction whose contract key space is too large to count directly, restated over
+// dense ids (Section 4.1.2): the distinct contract keys of Y are numbered 0..D-1, and X and
+// Y are rewritten with their free modes (ascending, lengths unchanged) followed by one
+// paired mode of length D + 1 holding the id. X entries whose key Y lacks take the id D,
+// which no Y entry has, so they form no products, as in Eq. 2. The free modes keep their
+// order, so the output modes and out_order mean the same for the rewritten pair.
+struct Relabelled {
+  Arena ar;  // the rewritten coordinates
+  StageTimer tm;
+  std::vector<int64_t> xs, ys;
+  stc_coo X{}, Y{};
+  int32_t cx = 0, cy = 0;
+  uint64_t ids = 0;  // D
+  unsigned launches = 0;
+  Relabelled(stc_ctx* c, cudaStream_t s) : ar(c, s) {}
+};
+
+stc_status relabel(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, const Plan& pl, bool record,
+                   cudaStream_t s, Relabelled& rl) {
+  rl.tm.start(record, s);
+  const uint64_t slots = id_table_slots(Y->nnz);
+  uint32_t fx = 0, fy = 0;
+  int nfx = 0, nfy = 0;
+  for (int j = 0; j < X->order; j++)
+    if (pl.kx.cstride[j] == 0) fx |= 1u << j, rl.xs.push_back(X->shape[j]), nfx++;
+  for (int j = 0; j < Y->order; j++)
+    if (pl.ky.cstride[j] == 0) fy |= 1u << j, rl.ys.push_back(Y->shape[j]), nfy++;
+  int32_t *xc = nullptr, *yc = nullptr;
+  STC_TRY(rl.ar.alloc(&xc, (size_t)X->nnz * (nfx + 1)));
+  STC_TRY(rl.ar.alloc(&yc, (size_t)Y->nnz * (nfy + 1)));
+  uint32_t h[2] = {0, 0};
+  {
+    Arena tab(ctx, s);  // released (stream-ordered) once the rewrites are queued
+    IdTable t{};
+    uint32_t *scr = nullptr, *status = nullptr;
+    t.slots = slots;
+    STC_TRY(tab.alloc(&t.keys, slots));
+    STC_TRY(tab.alloc(&t.flags, slots + 1));
+    STC_TRY(tab.alloc(&t.prefix, slots + 2));
+    STC_TRY(tab.alloc(&scr, (size_t)scan_scratch_elems((int64_t)slots + 1)));
+    STC_TRY(tab.alloc(&status, 1));
+    STC_CUDA(cudaMemsetAsync(t.keys, 0xff, slots * sizeof(u64), s));
+    STC_CUDA(cudaMemsetAsync(t.flags + slots, 0, sizeof(uint32_t), s));
+    STC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+    STC_CUDA(launch_id_insert_rows(Y->coords, Y->nnz, pl.ky, t, status, ctx->sms, s));
+    STC_CUDA(launch_id_number(t, scr, ctx->sms, s));
+    STC_CUDA(launch_id_rewrite_rows(X->coords, X->nnz, pl.kx, fx, nfx, t, xc, status, ctx->sms, s));
+    STC_CUDA(launch_id_rewrite_rows(Y->coords, Y->nnz, pl.ky, fy, nfy, t, yc, status, ctx->sms, s));
+    STC_CUDA(cudaMemcpyAsync(&h[0], status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    STC_CUDA(cudaMemcpyAsync(&h[1], t.prefix + slots + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    STC_CUDA(cudaStreamSynchronize(s));
+  }
+  rl.tm.mark(0);
+  STC_TRY(status_word(h[0]));
+  rl.ids = h[1];
+  if (rl.ids + 1 > kMaxDirectBins)
+    return fail(STC_ERR_UNSUPPORTED, "Y has %llu distinct contract keys; at most 2^26 - 1 are supported",
+                (unsigned long long)rl.ids);
+  rl.xs.push_back((int64_t)rl.ids + 1);
+  rl.ys.push_back((int64_t)rl.ids + 1);
+  rl.X = stc_coo{nfx + 1, rl.xs.data(), X->nnz, xc, X->vals};
+  rl.Y = stc_coo{nfy + 1, rl.ys.data(), Y->nnz, yc, Y->vals};
+  rl.cx = nfx;
+  rl.cy = nfy;
+  rl.launches = take_launches();
+  return STC_OK;
+}
+
 }  // namespace
 
 DeviceBlock::~DeviceBlock() {
@@ -801,6 +869,18 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
     return fail(STC_ERR_INVALID_ARG, "unknown accumulator %d", o.accumulator);
   if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
     return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
+  if (pl.K > kMaxDirectBins) {
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+    Relabelled rl(ctx, static_cast<cudaStream_t>(stream));
+    take_launches();
+    STC_TRY(relabel(ctx, X, Y, pl, o.record_times != 0, static_cast<cudaStream_t>(stream), rl));
+    STC_TRY(stc_contract(ctx, &rl.X, &rl.Y, 1, &rl.cx, &rl.cy, out_order, opts, stream, out));
+    (*out)->stats.launches += rl.launches;
+    (*out)->stats.contract_ids = rl.ids;
+    rl.tm.collect((*out)->stats);
+    return STC_OK;
+  }
   const int strategy = pick_strategy(pl, X, o.strategy);
   if (strategy == STC_STRATEGY_GROUPED && pl.FX > kMaxDirectBins)
     return fail(STC_ERR_UNSUPPORTED, "X free key space %llu exceeds %llu bins", (unsigned long long)pl.FX,
@@ -1166,6 +1246,18 @@ stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (pl.K > kMaxDirectBins) {
+    Relabelled rl(ctx, s);
+    STC_TRY(relabel(ctx, X, Y, pl, false, s, rl));
+    uint64_t b = 0;
+    STC_TRY(stc_count(ctx, &rl.X, &rl.Y, 1, &rl.cx, &rl.cy, stream, products, bytes_bound ? &b : nullptr));
+    // The rewritten coordinates stay held beside the id table, then beside the contraction.
+    const uint64_t slots = id_table_slots(Y->nnz);
+    const uint64_t table = 16 * slots + 4 * (uint64_t)scan_scratch_elems((int64_t)slots + 1) + 16;
+    if (bytes_bound)
+      *bytes_bound = std::max(b, table) + 4ull * (uint64_t)(rl.X.order * X->nnz + rl.Y.order * Y->nnz);
+    return STC_OK;
+  }
   Arena ar(ctx, s);
   StageTimer tm;
   Prepared pr;
@@ -1240,6 +1332,38 @@ stc_status stc_group_keys(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint64_
   STC_CUDA(cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, s));
   STC_CUDA(cudaStreamSynchronize(s));
   return status_word(h);
+}
+
+stc_status stc_dense_ids(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint32_t* ids_out, uint64_t* ndistinct,
+                         void* stream) {
+  if (!ctx) return fail(STC_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0 || n > STC_MAX_NNZ) return fail(STC_ERR_INVALID_ARG, "n = %lld out of range", (long long)n);
+  if (!ndistinct || (n > 0 && (!keys || !ids_out))) return fail(STC_ERR_INVALID_ARG, "NULL pointer");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(ctx, s);
+  IdTable t{};
+  uint32_t *scr = nullptr, *status = nullptr;
+  t.slots = id_table_slots(n);
+  STC_TRY(ar.alloc(&t.keys, t.slots));
+  STC_TRY(ar.alloc(&t.flags, t.slots + 1));
+  STC_TRY(ar.alloc(&t.prefix, t.slots + 2));
+  STC_TRY(ar.alloc(&scr, (size_t)scan_scratch_elems((int64_t)t.slots + 1)));
+  STC_TRY(ar.alloc(&status, 1));
+  STC_CUDA(cudaMemsetAsync(t.keys, 0xff, t.slots * sizeof(u64), s));
+  STC_CUDA(cudaMemsetAsync(t.flags + t.slots, 0, sizeof(uint32_t), s));
+  STC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  const u64* kk = reinterpret_cast<const u64*>(keys);
+  STC_CUDA(launch_id_insert_keys(kk, n, t, status, ctx->sms, s));
+  STC_CUDA(launch_id_number(t, scr, ctx->sms, s));
+  STC_CUDA(launch_id_lookup_keys(kk, n, t, ids_out, ctx->sms, s));
+  uint32_t h[2] = {0, 0};
+  STC_CUDA(cudaMemcpyAsync(&h[0], status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaMemcpyAsync(&h[1], t.prefix + t.slots + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaStreamSynchronize(s));
+  *ndistinct = h[1];
+  return status_word(h[0]);
 }
 
 stc_status stc_result_info(const stc_result* r, int64_t* nnz, int32_t* order, const int64_t** shape) {

@@ -68,6 +68,33 @@ cudaError_t launch_x_scatter_dense(const int32_t* coords, const double* vals, in
                                    const uint32_t* yoff, uint32_t* gcur, GroupedX gx, uint32_t* status, int sms,
                                    cudaStream_t s);
 
+// ------------------------------------------------------------------ dense ids (ids.cu)
+// Distinct keys collected in an open-addressing table and numbered densely (Section 4.1.2).
+// keys[slots] (all-ones = empty), flags[slots + 1] (flags[slots] = the all-ones key was
+// seen), prefix[slots + 2] = exclusive scan of flags: the id of the key in slot h is
+// prefix[h], the all-ones key's is prefix[slots], and prefix[slots + 1] = D, the number of
+// distinct keys, which is also the id given to a key the table lacks.
+struct IdTable {
+  u64* keys;
+  uint32_t* flags;
+  uint32_t* prefix;
+  u64 slots;  // a power of two >= 2n
+};
+uint64_t id_table_slots(int64_t n);
+cudaError_t launch_id_insert_keys(const u64* keys, int64_t n, const IdTable& t, uint32_t* status, int sms,
+                                  cudaStream_t s);
+// Inserts the contract key of every coordinate row.
+cudaError_t launch_id_insert_rows(const int32_t* coords, int64_t n, const KeyPlan& p, const IdTable& t,
+                                  uint32_t* status, int sms, cudaStream_t s);
+// Flags the occupied slots and scans them into prefix (scratch: scan_scratch_elems(slots + 1)).
+cudaError_t launch_id_number(const IdTable& t, uint32_t* scratch, int sms, cudaStream_t s);
+cudaError_t launch_id_lookup_keys(const u64* keys, int64_t n, const IdTable& t, uint32_t* ids, int sms,
+                                  cudaStream_t s);
+// out[i] = (free coordinates of row i, ascending mode order; id of its contract key), nf + 1
+// int32 per row. fmask has bit j set for each free mode j.
+cudaError_t launch_id_rewrite_rows(const int32_t* coords, int64_t n, const KeyPlan& p, uint32_t fmask, int nf,
+                                   const IdTable& t, int32_t* out, uint32_t* status, int sms, cudaStream_t s);
+
 // ------------------------------------------------------------------ one global table (global.cu)
 struct GlobalTable {
   u64* keys;    // [cap], kEmpty64 when free

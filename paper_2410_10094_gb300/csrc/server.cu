@@ -36,6 +36,7 @@ struct Ticket {
   bool has_oo = false;
   uint64_t bytes = 0;  // admission bound
   uint64_t products = 0;  // exact product count
+  bool alone = false;     // runs as a plain contraction (its contract keys need renumbering)
   bool done = false;
   stc_status status = STC_OK;
   std::string error;
@@ -128,13 +129,17 @@ void worker_main(stc_server* sv, int w) {
     // Requests large enough to fill the GPU alone (and a request that is alone in its batch)
     // run as plain contractions; the others share one batched launch sequence.
     std::vector<uint64_t> prods(batch.size());
+    std::vector<char> lone(batch.size());
     {
       std::lock_guard<std::mutex> lk(sv->mu);
-      for (size_t k = 0; k < batch.size(); k++) prods[k] = sv->tickets[batch[k]].products;
+      for (size_t k = 0; k < batch.size(); k++) {
+        prods[k] = sv->tickets[batch[k]].products;
+        lone[k] = sv->tickets[batch[k]].alone;
+      }
     }
     std::vector<size_t> small, alone;
     for (size_t k = 0; k < batch.size(); k++)
-      (sv->opts.plain || prods[k] > kServerAloneProducts ? alone : small).push_back(k);
+      (sv->opts.plain || lone[k] || prods[k] > kServerAloneProducts ? alone : small).push_back(k);
     if (small.size() == 1) {
       alone.insert(alone.begin(), small[0]);
       small.clear();
@@ -230,6 +235,14 @@ stc_status stc_server_submit(stc_server* sv, const stc_problem* req, uint64_t* t
     t.bytes = bytes;
     t.products = P;
   }
+  // The batched launch groups Y by contract key directly; a key space above 2^26 is
+  // renumbered to dense ids by the plain path only.
+  unsigned __int128 K = 1;
+  for (int32_t i = 0; i < t.req.ncontract; i++) {
+    K *= (unsigned __int128)t.req.X.shape[t.req.cx[i]];
+    if (K > ((unsigned __int128)1 << 26)) break;
+  }
+  t.alone = K > ((unsigned __int128)1 << 26);
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->stopping) return report_error(STC_ERR_INVALID_ARG, "server is shutting down");
   const uint64_t id = sv->next_ticket++;

@@ -7,7 +7,7 @@ CPU oracle and the CUDA path can be fed from it without sharing method code.
 Recipe (stated once, used everywhere):
 
 * Random numbers come from NumPy's ``PCG64`` bit generator. The named
-  workloads use seed ``20241010 + k`` for workload k (1..5); 3Z uses the seed
+  workloads use seed ``20241010 + k`` for workload k (1..5; 6 for wide_keys); 3Z uses the seed
   of workload 3.
 * Values are uniform in [-1, 1]; an exact 0.0 is redrawn, because COO lists
   only nonzeros (Section 2.1.2).
@@ -162,6 +162,37 @@ def imbalanced(seed: int = SEED_BASE + 3, nx: int = 20_000_000, ny: int = 20_000
     yv = nonzero_values(rng, ny)
     name = "imbalanced_zipf_both" if both_zipf else "imbalanced_zipf_y"
     return Problem(COO((4096, 512, 512), X, xv), COO((512, 512, 64), Y, yv), (1, 2), (0, 1), name=name)
+
+
+def wide_keys(seed: int = SEED_BASE + 6, nnz: int = 5_000_000, n: int = 256, length: int = 65536,
+              pool: int = 65536, nnz_y: Optional[int] = None) -> Problem:
+    """plain_large with its paired modes stretched to ``length`` each: X is n x n x L x L, Y
+    is L x L x n x n, X modes (2,3) with Y modes (0,1), a L^2 (2^32) contract key space.
+
+    Both tensors draw their paired (i, j) coordinates uniformly from one shared pool of
+    ``pool`` cells, themselves uniform over L x L: a very sparse tensor whose entries sit on
+    a few fibres, like the network-traffic tensors of Table 2 (LBNL, 65K^3). Free
+    coordinates are uniform; with the defaults the products and output match plain_large's
+    in distribution.
+    """
+    rng = rng_for(seed)
+    cells = rng.choice(length * length, size=pool, replace=False)
+    ci, cj = np.unravel_index(cells, (length, length))
+    ny = nnz if nnz_y is None else nnz_y
+
+    def draw(count, paired_first):
+        c = np.empty((count, 4), dtype=np.int32)
+        pick = rng.integers(0, pool, size=count)
+        a, b = (0, 1) if paired_first else (2, 3)
+        f, g = (2, 3) if paired_first else (0, 1)
+        c[:, a], c[:, b] = ci[pick], cj[pick]
+        c[:, f] = rng.integers(0, n, size=count).astype(np.int32)
+        c[:, g] = rng.integers(0, n, size=count).astype(np.int32)
+        return c
+
+    X = COO((n, n, length, length), draw(nnz, False), nonzero_values(rng, nnz))
+    Y = COO((length, length, n, n), draw(ny, True), nonzero_values(rng, ny))
+    return Problem(X, Y, (2, 3), (0, 1), name=f"wide_keys_{length}^2_pool{pool}_{nnz:.0e}")
 
 
 def small_pair(rng: np.random.Generator, nnz_lo: float = 1e2, nnz_hi: float = 1e5,
