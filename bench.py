@@ -238,6 +238,10 @@ def reference_arm(args):
     import oracle
 
     oracle.build()
+    if args.workload not in WORKLOADS:
+        ap_err = f"--impl reference times single contractions; '{args.workload}' is reported by our arm only"
+        print(json.dumps({"impl": "reference", "unavailable": ap_err}), flush=True)
+        return 0
     p = WORKLOADS[args.workload](SEEDS[args.workload])
     for _ in range(args.warmup):
         run_oracle_sample(p, args.workload)
@@ -339,16 +343,91 @@ def serve_bench(args):
     return 0
 
 
+SWEEP_NNZ = (50_000, 100_000, 200_000, 300_000, 500_000)
+
+
+def sweep_problems():
+    """Table 1's Set 1 and Set 2 (A: order 5, B: order 4; A with A, B with B, A with B) at
+    each entry count, then Table 2's shapes as random self-contractions."""
+    probs = [W.set_sweep(s, pair, n) for s in (1, 2) for pair in ("AA", "BB", "AB") for n in SWEEP_NNZ]
+    return probs + [W.table2(name) for name in W.TABLE2]
+
+
+def sweep_bench(args):
+    """Every sweep problem timed alone (CUDA events over --steps calls after --warmup), then
+    the oracle on the 50K cases of Set 1 and Set 2 as the CPU baseline."""
+    import torch
+
+    import paper_2410_10094_gb300 as stc
+
+    clk = ClockSampler(0).start()
+    torch.cuda.set_device(0)
+    stc.load()
+    ctx = stc.default_context(0)
+    stream = torch.cuda.current_stream()
+    dev = lambda t: (t.shape, torch.from_numpy(t.coords).cuda(), torch.from_numpy(t.vals).cuda())
+    rows, tot_p, tot_ms = [], 0, 0.0
+    tw0 = time.time()
+    for p in sweep_problems():
+        X = dev(p.X)
+        Y = X if p.Y is p.X else dev(p.Y)
+        step = lambda: stc.contract(X, Y, p.cx, p.cy, p.out_order, stream=stream, ctx=ctx)
+        for _ in range(args.warmup):
+            r = step()
+            P, nz, cids = r.stats.products, r.nnz, r.stats.contract_ids
+            del r
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+            del r
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        rows.append({"name": p.name, "shape_x": list(p.X.shape), "shape_y": list(p.Y.shape), "nnz_x": p.X.nnz,
+                     "nnz_y": p.Y.nnz, "products": int(P), "nnz_out": int(nz), "contract_ids": int(cids),
+                     "ms": ms, "products_per_s": P / (ms / 1e3)})
+        tot_p += P
+        tot_ms += ms
+        del X, Y
+    clk.mark(tw0, time.time())
+    clk.stop()
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        t0 = time.perf_counter()
+        prods = sum(oracle.contract(q.X, q.Y, q.cx, q.cy).products
+                    for q in (W.set_sweep(s, pair, SWEEP_NNZ[0]) for s in (1, 2) for pair in ("AA", "BB", "AB")))
+        dt = time.perf_counter() - t0
+        cpu = {"value": prods / dt, "unit": "products/s", "cores": 1, "kind": "oracle",
+               "sample": "the six 50K cases of Set 1 and Set 2", "seconds": dt}
+    line = {
+        "metric": "products/s", "value": tot_p / (tot_ms / 1e3), "unit": "products/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "sweep: Table 1 Sets 1-2 (A 5-order, B 4-order; AA, BB, AB; 50K-500K entries) and "
+                               "Table 2 shapes as random self-contractions; second and third modes paired",
+                   "problems": len(rows), "l2": "no flush; each problem's inputs stay resident"},
+        "sweep": rows, "cpu_baseline": cpu, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain_large", choices=sorted(WORKLOADS) + ["served"])
+    ap.add_argument("--workload", default="plain_large", choices=sorted(WORKLOADS) + ["served", "sweep"])
     ap.add_argument("--strategy", type=int, default=0, help="0 auto, 1 global table, 2 grouped")
     ap.add_argument("--group-load-factor", type=float, default=0.0, help="0 = library default")
     ap.add_argument("--accumulator", type=int, default=0, help="0 auto, 1 hash tables, 2 dense rows")
+    ap.add_argument("--contract-ids", type=int, default=0, help="0 auto, 1 direct contract keys, 2 dense ids")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -362,6 +441,8 @@ def main(argv=None):
         return reference_arm(args)
     if args.workload == "served":
         return serve_bench(args)
+    if args.workload == "sweep":
+        return sweep_bench(args)
 
     import torch
 
@@ -409,7 +490,7 @@ def main(argv=None):
         def step(record=False):
             return stc.contract(X, Y, p.cx, p.cy, p.out_order, strategy=args.strategy, record_times=record,
                                 group_load_factor=args.group_load_factor, accumulator=args.accumulator,
-                                stream=stream, ctx=ctx)
+                                contract_ids=args.contract_ids, stream=stream, ctx=ctx)
 
     for _ in range(args.warmup):
         r = step()
@@ -479,8 +560,8 @@ def main(argv=None):
             Xd = (p.X.shape, hx[0].to("cuda", non_blocking=True), hx[1].to("cuda", non_blocking=True))
             Yd = (p.Y.shape, hy[0].to("cuda", non_blocking=True), hy[1].to("cuda", non_blocking=True))
             r = stc.contract(Xd, Yd, p.cx, p.cy, p.out_order, strategy=args.strategy,
-                             group_load_factor=args.group_load_factor, accumulator=args.accumulator, stream=stream,
-                            ctx=ctx)
+                             group_load_factor=args.group_load_factor, accumulator=args.accumulator,
+                             contract_ids=args.contract_ids, stream=stream, ctx=ctx)
             hc[: r.nnz].copy_(r.coords, non_blocking=True)
             hv[: r.nnz].copy_(r.vals, non_blocking=True)
             torch.cuda.synchronize()
@@ -524,7 +605,8 @@ def main(argv=None):
     dom_ms = per_step[dom]
     achieved = kernel_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
     step_ms = ms / args.steps
-    traffic = NCU_TRAFFIC.get(args.workload) if (args.strategy == 0 and args.accumulator == 0) else None
+    default_opts = args.strategy == 0 and args.accumulator == 0 and args.contract_ids == 0
+    traffic = NCU_TRAFFIC.get(args.workload) if default_opts else None
     roofline = {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic[1] if traffic else None,
                 "traffic_kernel": traffic[0] if traffic else None, "peak_kind": peak_kind,
@@ -545,7 +627,7 @@ def main(argv=None):
                    "products_per_step": P, "nnz_out": nz, "parallelism": f"replicas x{world}",
                    "l2": l2_note(bytes_in, (4 * oz + 8) * nz), "strategy": args.strategy,
                    "group_load_factor": args.group_load_factor, "accumulator": args.accumulator,
-                   "contract_ids": int(cids)},
+                   "contract_ids_mode": args.contract_ids, "contract_ids": int(cids)},
         "step_hbm": {"alg_bytes": step_alg, "gbs": step_alg / (step_ms / 1e3) / 1e9,
                      "frac": step_alg / (step_ms / 1e3) / 1e9 / hbm},
         "stage_ms": {n: float(per_step[i]) for i, n in enumerate(stage_names)},

@@ -62,9 +62,10 @@ typedef struct stc_coo {
   const double* vals;     /* device, [nnz]; may be NULL when nnz == 0 */
 } stc_coo;
 
-/* Accumulation strategy. AUTO picks from the key spaces: one global table when the output
- * key space is small (the whole table stays in L2), otherwise per-X-free-group tables in
- * shared memory (Section 4.3). */
+/* Accumulation strategy. AUTO picks from the key spaces and sizes: one global table when the
+ * output key space is small (the whole table stays in L2) or when X has far fewer entries than
+ * free keys (more than about two free keys per entry, sixteen when n_Y >= 16 K), otherwise
+ * per-X-free-group tables in shared memory (Section 4.3). */
 enum { STC_STRATEGY_AUTO = 0, STC_STRATEGY_GLOBAL = 1, STC_STRATEGY_GROUPED = 2 };
 
 /* Per-group accumulator of the GROUPED strategy. HASH: a probing table sized from the
@@ -77,6 +78,14 @@ enum { STC_STRATEGY_AUTO = 0, STC_STRATEGY_GLOBAL = 1, STC_STRATEGY_GROUPED = 2 
  * the warp-sized hash tables when F_Y <= 2^20, HASH for the others. */
 enum { STC_ACC_AUTO = 0, STC_ACC_HASH = 1, STC_ACC_DENSE = 2, STC_ACC_HASH_SCAN = 3 };
 
+/* Contract keys (Section 4.1.2). DIRECT: Y is grouped over the K = prod(paired lengths)
+ * contract keys themselves (counting sort over K bins). DENSE: the contract keys of Y are
+ * first renumbered 0..D-1 and X and Y are rewritten with the id in place of their paired modes
+ * (as stc_dense_ids does); stats.contract_ids = D. AUTO: DENSE when K > 2^26 (always, since
+ * direct counting stops there) or when K exceeds both 2^22 and 8 (nX + nY); DIRECT otherwise.
+ * A DIRECT request with K > 2^26 is renumbered too. */
+enum { STC_IDS_AUTO = 0, STC_IDS_DIRECT = 1, STC_IDS_DENSE = 2 };
+
 typedef struct stc_opts {
   int32_t strategy;       /* STC_STRATEGY_*; 0 = AUTO */
   int32_t record_times;   /* nonzero: time each stage with CUDA events (stc_result_stats) */
@@ -85,7 +94,7 @@ typedef struct stc_opts {
                                0 = default 0.75. A group of bound t goes to the smallest table
                                class with t <= group_load_factor * slots. */
   int32_t accumulator;    /* STC_ACC_*; 0 = AUTO */
-  int32_t reserved_;
+  int32_t contract_ids;   /* STC_IDS_*; 0 = AUTO */
 } stc_opts;
 
 /* Per-call statistics of a finished contraction. */
@@ -101,8 +110,8 @@ typedef struct stc_stats {
   int32_t accumulator;    /* GROUPED: STC_ACC_HASH or STC_ACC_DENSE when every group used that
                              accumulator, STC_ACC_AUTO when both ran */
   float stage_ms[8];      /* 0 group Y, 1 survey X, 2 group X, 3 plan, 4 accumulate, 5 compact/write */
-  uint64_t contract_ids;  /* distinct contract keys of Y when the contract key space was renumbered
-                             to dense ids (key space > 2^26), else 0 */
+  uint64_t contract_ids;  /* distinct contract keys of Y when the contract keys were renumbered
+                             to dense ids (STC_IDS_DENSE), else 0 */
 } stc_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -132,9 +141,9 @@ stc_status stc_destroy(stc_ctx* ctx);
  *   out         receives the result
  * Output: every coordinate that received at least one product, once, with the sum of its
  * products (a structural nonzero is kept even if it sums to 0.0), in unspecified order.
- * Contract key spaces above 2^26 are first renumbered to dense ids (Section 4.1.2, as
- * stc_dense_ids does): stats.contract_ids then holds the number of distinct contract keys
- * of Y, which must stay below 2^26 (else UNSUPPORTED).
+ * Large contract key spaces are first renumbered to dense ids (opts.contract_ids, Section
+ * 4.1.2): stats.contract_ids then holds the number of distinct contract keys of Y, which
+ * must stay below 2^26 (else UNSUPPORTED).
  * Errors: INVALID_ARG, SHAPE_MISMATCH, KEY_OVERFLOW (output key space > 2^64 - 2),
  * COORD_OUT_OF_RANGE (checked on the device), OUT_OF_MEMORY, UNSUPPORTED, CUDA. */
 stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t ncontract,

@@ -19,6 +19,7 @@ STATUS_NAMES = {
 }
 STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_GROUPED = 0, 1, 2
 ACC_AUTO, ACC_HASH, ACC_DENSE, ACC_HASH_SCAN = 0, 1, 2, 3
+IDS_AUTO, IDS_DIRECT, IDS_DENSE = 0, 1, 2
 STC_MAX_ORDER = 8
 
 
@@ -45,7 +46,7 @@ class stc_server_opts(C.Structure):
 
 class stc_opts(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double),
-                ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("reserved_", C.c_int32)]
+                ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("contract_ids", C.c_int32)]
 
 
 class stc_stats(C.Structure):
@@ -397,12 +398,13 @@ class Result:
 
 def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, strategy: int = STRATEGY_AUTO,
              load_factor: float = 0.0, group_load_factor: float = 0.0, accumulator: int = ACC_AUTO,
-             record_times: bool = False, stream=None, ctx: Context = None) -> Result:
+             contract_ids: int = IDS_AUTO, record_times: bool = False, stream=None,
+             ctx: Context = None) -> Result:
     """Z = X (x) Y (Eq. 2) on the GPU. X and Y are (shape, coords, vals) with coords a CUDA
     int32 [nnz, order] tensor and vals a CUDA float64 [nnz] tensor."""
     ctx = ctx or default_context()
     o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor), float(group_load_factor),
-                 int(accumulator), 0)
+                 int(accumulator), int(contract_ids))
     return Result(stc_contract(ctx.handle, X, Y, cx, cy, out_order, o, stream))
 
 

@@ -329,15 +329,32 @@ stc_status make_plan(const stc_coo* X, const stc_coo* Y, int32_t m, const int32_
   pl.op = OutPlan{};
   pl.op.order = pl.oz;
   pl.op.pow2 = 1;
+  pl.op.z32 = pl.F <= (1ull << 32);
   pl.zshape.assign(pl.oz, 0);
+  std::vector<int> pos_of(pl.oz);  // output position of concatenated mode t
   for (int q = 0; q < pl.oz; q++) {
     const int t = out_order ? out_order[q] : q;
-    pl.op.div[q] = cstr[t];
+    pos_of[t] = q;
     pl.op.mod[q] = csize[t];
     pl.zshape[q] = (int64_t)csize[t];
     if (!is_pow2(csize[t])) pl.op.pow2 = 0;
   }
-  for (int q = 0; q < pl.oz; q++) pl.op.shift[q] = pl.op.pow2 ? log2_u64(pl.op.div[q]) : 0;
+  for (int q = 0; q < pl.oz; q++) {
+    const int t = out_order ? out_order[q] : q;
+    pl.op.shift[q] = pl.op.pow2 ? log2_u64(cstr[t]) : 0;
+  }
+  // Digits least significant first: the last concatenated mode is the lowest digit.
+  for (int j = 0; j < pl.oz; j++) {
+    const int t = pl.oz - 1 - j;
+    const uint64_t d = csize[t];
+    const uint32_t l = d <= 1 ? 0 : 64 - (uint32_t)__builtin_clzll(d - 1);  // ceil(log2 d)
+    const unsigned N = pl.op.z32 ? 32 : 64;
+    const unsigned __int128 num = ((unsigned __int128)(((unsigned __int128)1 << l) - d)) << N;
+    pl.op.magic[j] = (uint64_t)(num / d + 1);
+    pl.op.dpos[j] = (uint8_t)pos_of[t];
+    pl.op.dsh1[j] = (uint8_t)(l < 1 ? l : 1);
+    pl.op.dsh2[j] = (uint8_t)(l > 1 ? l - 1 : 0);
+  }
   return STC_OK;
 }
 
@@ -688,11 +705,27 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
 
 // AUTO: one global table when the output key space is small (the table stays in L2),
 // per-group shared-memory tables when X's free keys can be counted directly.
-int pick_strategy(const Plan& pl, const stc_coo* X, int requested) {
+// GROUPED pays per X free key (a counting sort over F_X bins) and per group (a table and an
+// output reservation), so it needs groups with work in them: at most about two free keys per
+// X entry, or up to sixteen when each X entry meets many Y entries (n_Y >= 16 K).
+int pick_strategy(const Plan& pl, const stc_coo* X, const stc_coo* Y, int requested) {
   if (requested != STC_STRATEGY_AUTO) return requested;
   if (pl.F <= (1ull << 22)) return STC_STRATEGY_GLOBAL;
-  if (pl.FX <= kMaxDirectBins && pl.FX <= 16ull * (uint64_t)X->nnz + (1ull << 20)) return STC_STRATEGY_GROUPED;
+  if (pl.FX > kMaxDirectBins) return STC_STRATEGY_GLOBAL;
+  const uint64_t nX = (uint64_t)X->nnz, nY = (uint64_t)Y->nnz;
+  if (pl.FX <= 2 * nX + (1ull << 20)) return STC_STRATEGY_GROUPED;
+  if (nY >= 16 * pl.K && pl.FX <= 16 * nX + (1ull << 20)) return STC_STRATEGY_GROUPED;
   return STC_STRATEGY_GLOBAL;
+}
+
+// Whether the contract keys are renumbered to dense ids before grouping (Section 4.1.2):
+// always past the direct-counting limit, and under AUTO when the key space dwarfs the inputs
+// (the K-bin histogram and scan would cost more than the renumbering).
+bool use_dense_ids(const Plan& pl, const stc_coo* X, const stc_coo* Y, int mode) {
+  if (pl.K > kMaxDirectBins) return true;
+  if (pl.K <= 1 || mode == STC_IDS_DIRECT) return false;
+  if (mode == STC_IDS_DENSE) return true;
+  return pl.K > (1ull << 22) && pl.K > 8ull * (uint64_t)(X->nnz + Y->nnz);
 }
 
 // A contraction whose contract key space is too large to count directly, restated over
@@ -869,19 +902,23 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
     return fail(STC_ERR_INVALID_ARG, "unknown accumulator %d", o.accumulator);
   if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
     return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
-  if (pl.K > kMaxDirectBins) {
+  if (o.contract_ids < 0 || o.contract_ids > STC_IDS_DENSE)
+    return fail(STC_ERR_INVALID_ARG, "unknown contract_ids %d", o.contract_ids);
+  if (use_dense_ids(pl, X, Y, o.contract_ids)) {
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
     Relabelled rl(ctx, static_cast<cudaStream_t>(stream));
     take_launches();
     STC_TRY(relabel(ctx, X, Y, pl, o.record_times != 0, static_cast<cudaStream_t>(stream), rl));
-    STC_TRY(stc_contract(ctx, &rl.X, &rl.Y, 1, &rl.cx, &rl.cy, out_order, opts, stream, out));
+    stc_opts inner = o;
+    inner.contract_ids = STC_IDS_DIRECT;
+    STC_TRY(stc_contract(ctx, &rl.X, &rl.Y, 1, &rl.cx, &rl.cy, out_order, &inner, stream, out));
     (*out)->stats.launches += rl.launches;
     (*out)->stats.contract_ids = rl.ids;
     rl.tm.collect((*out)->stats);
     return STC_OK;
   }
-  const int strategy = pick_strategy(pl, X, o.strategy);
+  const int strategy = pick_strategy(pl, X, Y, o.strategy);
   if (strategy == STC_STRATEGY_GROUPED && pl.FX > kMaxDirectBins)
     return fail(STC_ERR_UNSUPPORTED, "X free key space %llu exceeds %llu bins", (unsigned long long)pl.FX,
                 (unsigned long long)kMaxDirectBins);
@@ -1246,7 +1283,7 @@ stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (pl.K > kMaxDirectBins) {
+  if (use_dense_ids(pl, X, Y, STC_IDS_AUTO)) {
     Relabelled rl(ctx, s);
     STC_TRY(relabel(ctx, X, Y, pl, false, s, rl));
     uint64_t b = 0;
@@ -1261,7 +1298,7 @@ stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m
   Arena ar(ctx, s);
   StageTimer tm;
   Prepared pr;
-  const int strategy = pick_strategy(pl, X, STC_STRATEGY_AUTO);
+  const int strategy = pick_strategy(pl, X, Y, STC_STRATEGY_AUTO);
   const bool dense = strategy == STC_STRATEGY_GROUPED && (uint64_t)Y->nnz >= pl.K;
   STC_TRY(prepare(ctx, ar, X, Y, pl, dense ? Survey::kDenseGroups : Survey::kSurvivors, s, tm, pr));
   Counters h{};

@@ -42,14 +42,27 @@ struct KeyPlan {
   uint64_t fstride[kMaxOrder];
 };
 
-// How an output key zkey = fX * F_Y + fY decodes into output coordinates. Output mode q is
-// (zkey / div[q]) % mod[q]; when every length is a power of two, (zkey >> shift[q]) & (mod[q]-1).
+// How an output key zkey = fX * F_Y + fY decodes into output coordinates. zkey is a
+// mixed-radix number whose digits, least significant first, are the output coordinates at
+// positions dpos[0], dpos[1], ...; digit j has radix mod[dpos[j]]. When every length is a
+// power of two, output mode q is simply (zkey >> shift[q]) & (mod[q] - 1). Otherwise the
+// digits are peeled off by repeated division, each division by an invariant radix done with
+// a multiply-high (Granlund and Montgomery, PLDI 1994, Section 4): with l = ceil(log2 d),
+// m = floor(2^N (2^l - d) / d) + 1 and t = mulhi(m, n), n / d = (t + ((n - t) >> sh1)) >> sh2
+// where sh1 = min(l, 1), sh2 = max(l - 1, 0), for every N-bit n. N = 32 when z32 (every
+// output key below 2^32), else 64.
 struct OutPlan {
   int32_t order;
   int32_t pow2;
-  uint64_t div[kMaxOutOrder];
-  uint64_t mod[kMaxOutOrder];
-  uint32_t shift[kMaxOutOrder];
+  int32_t z32;
+  int32_t pad_;
+  uint64_t mod[kMaxOutOrder];    // length of output mode q
+  uint32_t shift[kMaxOutOrder];  // power-of-two plans: bit offset of output mode q
+  uint64_t magic[kMaxOutOrder];  // multiplier m of digit j
+  uint8_t dpos[kMaxOutOrder];    // output position of digit j
+  uint8_t dsh1[kMaxOutOrder];
+  uint8_t dsh2[kMaxOutOrder];
+  uint8_t pad2_[kMaxOutOrder];
 };
 
 // MurmurHash3's 64-bit finaliser (fmix64, Austin Appleby, public domain): a bijective
@@ -116,12 +129,36 @@ __device__ __forceinline__ bool row_keys(const int32_t* __restrict__ coords, int
   return keys_of<ORDER>(c, p, ck, fk);
 }
 
-// Output coordinate q of an output key.
-__device__ __forceinline__ int32_t out_coord(uint64_t zkey, const OutPlan& op, int q) {
-  if (op.pow2) return (int32_t)((zkey >> op.shift[q]) & (op.mod[q] - 1));
-  if (zkey <= 0xffffffffull && op.div[q] <= 0xffffffffull)
-    return (int32_t)(((uint32_t)zkey / (uint32_t)op.div[q]) % (uint32_t)op.mod[q]);
-  return (int32_t)((zkey / op.div[q]) % op.mod[q]);
+// Peels the digits of zkey off (least significant first) and hands each output coordinate
+// to put(q, c). Used when the plan is not all powers of two.
+template <typename Put>
+__device__ __forceinline__ void decode_digits(uint64_t zkey, const OutPlan& op, Put&& put) {
+  if (op.z32) {
+    uint32_t z = (uint32_t)zkey;
+#pragma unroll 1
+    for (int j = 0; j < op.order; j++) {
+      const uint32_t t = __umulhi(z, (uint32_t)op.magic[j]);
+      const uint32_t q = (t + ((z - t) >> op.dsh1[j])) >> op.dsh2[j];
+      const int p = op.dpos[j];
+      put(p, (int32_t)(z - q * (uint32_t)op.mod[p]));
+      z = q;
+    }
+  } else {
+    uint64_t z = zkey;
+#pragma unroll 1
+    for (int j = 0; j < op.order; j++) {
+      const uint64_t t = __umul64hi(z, op.magic[j]);
+      const uint64_t q = (t + ((z - t) >> op.dsh1[j])) >> op.dsh2[j];
+      const int p = op.dpos[j];
+      put(p, (int32_t)(z - q * op.mod[p]));
+      z = q;
+    }
+  }
+}
+
+// Output coordinate q of an output key (power-of-two plans).
+__device__ __forceinline__ int32_t out_coord_pow2(uint64_t zkey, const OutPlan& op, int q) {
+  return (int32_t)((zkey >> op.shift[q]) & (op.mod[q] - 1));
 }
 
 // Writes the output coordinates of zkey to dst[0..order).
@@ -135,8 +172,12 @@ __device__ __forceinline__ void store_coords(uint64_t zkey, const OutPlan& op, i
     *reinterpret_cast<int4*>(dst) = v;
     return;
   }
+  if (op.pow2) {
 #pragma unroll 1
-  for (int q = 0; q < op.order; q++) dst[q] = out_coord(zkey, op, q);
+    for (int q = 0; q < op.order; q++) dst[q] = out_coord_pow2(zkey, op, q);
+    return;
+  }
+  decode_digits(zkey, op, [&](int q, int32_t c) { dst[q] = c; });
 }
 
 // L2 cache policies (PTX createpolicy): data read again soon (Y runs) is kept with
@@ -189,8 +230,10 @@ __device__ __forceinline__ void store_output(int32_t* __restrict__ coords, doubl
     cv.z = (int32_t)((zkey >> op.shift[2]) & (op.mod[2] - 1));
     cv.w = (int32_t)((zkey >> op.shift[3]) & (op.mod[3] - 1));
     st_stream_v4(dst, cv, pol);
+  } else if (op.pow2) {
+    for (int q = 0; q < op.order; q++) st_stream_s32(dst + q, out_coord_pow2(zkey, op, q), pol);
   } else {
-    for (int q = 0; q < op.order; q++) st_stream_s32(dst + q, out_coord(zkey, op, q), pol);
+    decode_digits(zkey, op, [&](int q, int32_t c) { st_stream_s32(dst + q, c, pol); });
   }
   st_stream_f64(vals + pos, v, pol);
 }

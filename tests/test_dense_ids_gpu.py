@@ -104,8 +104,11 @@ def test_wide_keys_parity(mode, pool, nx, ny):
 
 
 def test_wide_keys_boundary():
-    """2^26 bins exactly are counted directly; 2^26 + 2^14 are renumbered. Non-power-of-two
-    lengths, three paired modes, an output permutation."""
+    """2^26 bins exactly can be counted directly (and are renumbered under AUTO, being sparse);
+    2^26 + 2^14 are always renumbered. Non-power-of-two lengths, three paired modes, an output
+    permutation."""
+    import paper_2410_10094_gb300 as stc
+
     rng = W.rng_for(7101)
     for shape, renum in [((4096, 8192), False), ((4097, 8192), True)]:
         xs = (shape[0], 5, shape[1], 2)
@@ -118,10 +121,10 @@ def test_wide_keys_boundary():
         X.coords[:, [0, 2, 3]] = cells[rng.integers(0, 40, X.nnz)]
         Y.coords[:, [2, 1, 3]] = cells[rng.integers(0, 40, Y.nnz)]
         p = W.Problem(X, Y, (0, 2, 3), (2, 1, 3), out_order=(1, 0))
-        res, ref = check(p)
+        res, ref = check(p, contract_ids=stc.IDS_DIRECT)
         assert (res.stats.contract_ids > 0) == renum
-        if renum:
-            assert res.stats.contract_ids == distinct_y_cells(p)
+        res, ref = check(p)
+        assert res.stats.contract_ids == distinct_y_cells(p)
 
 
 def test_wide_keys_degenerate():
@@ -215,3 +218,26 @@ def test_server_routes_wide_keys_alone():
     sv.close()
     for p, (c, v) in zip(probs, got):
         assert_matches_oracle(c, v, oracle.contract(p.X, p.Y, p.cx, p.cy, p.out_order))
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_random_cases_renumbered(seed):
+    """Tiny random problems (orders 1-5, repeated coordinates, any number of paired modes)
+    with the contract keys renumbered even where direct counting applies."""
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(7200 + seed)
+    p = W.random_case(rng, max_order=5, max_size=6, max_nnz=120)
+    for mode in (dict(strategy=1), dict(strategy=2, accumulator=0)):
+        res, ref = check(p, contract_ids=stc.IDS_DENSE, **mode)
+        K = int(np.prod([p.X.shape[j] for j in p.cx], dtype=object))
+        if K > 1 and p.Y.nnz:
+            assert res.stats.contract_ids == distinct_y_cells(p)
+
+
+def test_direct_request_above_limit_is_renumbered():
+    import paper_2410_10094_gb300 as stc
+
+    p = W.wide_keys(nnz=5_000, n=8, pool=50)
+    res, _ = check(p, contract_ids=stc.IDS_DIRECT)
+    assert res.stats.contract_ids == distinct_y_cells(p)

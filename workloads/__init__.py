@@ -7,7 +7,8 @@ CPU oracle and the CUDA path can be fed from it without sharing method code.
 Recipe (stated once, used everywhere):
 
 * Random numbers come from NumPy's ``PCG64`` bit generator. The named
-  workloads use seed ``20241010 + k`` for workload k (1..5; 6 for wide_keys); 3Z uses the seed
+  workloads use seed ``20241010 + k`` for workload k (1..5; 6 for wide_keys, 7 for the
+  Table 2 shapes, 8 for the Set 1/2 sweeps); 3Z uses the seed
   of workload 3.
 * Values are uniform in [-1, 1]; an exact 0.0 is redrawn, because COO lists
   only nonzeros (Section 2.1.2).
@@ -193,6 +194,42 @@ def wide_keys(seed: int = SEED_BASE + 6, nnz: int = 5_000_000, n: int = 256, len
     X = COO((n, n, length, length), draw(nnz, False), nonzero_values(rng, nnz))
     Y = COO((length, length, n, n), draw(ny, True), nonzero_values(rng, ny))
     return Problem(X, Y, (2, 3), (0, 1), name=f"wide_keys_{length}^2_pool{pool}_{nnz:.0e}")
+
+
+# Table 2 shapes and entry counts. The paper generated these tensors at random (all but
+# NIPS); "65K", "2K" and the like are read as 65,536 and 2,000.
+TABLE2 = {
+    "enron": ((186, 186, 44), 9_838),
+    "lbnl": ((65_536, 65_536, 65_536), 27_269),
+    "facebook": ((63_891, 63_890, 1_847), 738_000),
+    "hubbard_1d_p": ((4, 4, 93, 36, 432), 300_000),
+    "hubbard_1d_t": ((131, 4, 413, 36, 4), 400_000),
+    "hubbard_1d_z": ((4, 129, 184, 24, 4), 100_000),
+    "hubbard_2d": ((4, 4, 111, 24, 528), 300_000),
+    "nips": ((2_000, 3_000, 14_000, 17_000), 3_000_000),
+}
+
+
+def table2(name: str, seed: int = SEED_BASE + 7, nnz: Optional[int] = None) -> Problem:
+    """Self-contraction of a random tensor with one of Table 2's shapes over its second and
+    third modes (0-based 1 and 2), the paper's stated convention for its experiments.
+    ``nnz`` overrides the table's entry count (smaller copies for the oracle)."""
+    shape, n0 = TABLE2[name]
+    rng = rng_for(seed + sorted(TABLE2).index(name))
+    T = uniform_coo(rng, shape, n0 if nnz is None else nnz)
+    return Problem(T, T, (1, 2), (1, 2), name=f"table2_{name}")
+
+
+def set_sweep(set_no: int, pair: str, nnz: int, seed: int = SEED_BASE + 8) -> Problem:
+    """A Set 1 (mode length 50) or Set 2 (length 100) case of Table 1: A is order 5, B order 4,
+    each with ``nnz`` uniform entries. ``pair`` is "AA" or "BB" (a tensor with itself) or "AB";
+    the second and third modes (0-based 1 and 2) of both are paired."""
+    length = {1: 50, 2: 100}[set_no]
+    rng = rng_for(seed + 10 * set_no + {"AA": 0, "BB": 1, "AB": 2}[pair])
+    A = uniform_coo(rng, (length,) * 5, nnz) if pair in ("AA", "AB") else None
+    B = uniform_coo(rng, (length,) * 4, nnz) if pair in ("BB", "AB") else None
+    X, Y = {"AA": (A, A), "BB": (B, B), "AB": (A, B)}[pair]
+    return Problem(X, Y, (1, 2), (1, 2), name=f"set{set_no}_{pair}_{nnz // 1000}K")
 
 
 def small_pair(rng: np.random.Generator, nnz_lo: float = 1e2, nnz_hi: float = 1e5,
