@@ -45,10 +45,13 @@ WORKLOADS = {
     "plain_large_slice": plain_large_slice,
     "imbalanced": lambda seed: W.imbalanced(seed=seed),
     "imbalanced_both": lambda seed: W.imbalanced(seed=seed, both_zipf=True),
+    "imbalanced_small_first": lambda seed: (lambda p: W.Problem(p.Y, p.X, p.cy, p.cx, out_order=(1, 0)))(
+        W.imbalanced(seed=seed)),
     "plain_small": lambda seed: W.plain_small(seed=seed),
     "wide_keys": lambda seed: W.wide_keys(seed=seed),
 }
 SEEDS = {"batched": W.SEED_BASE + 4, "plain_large": W.SEED_BASE + 2, "plain_large_slice": W.SEED_BASE + 2, "imbalanced": W.SEED_BASE + 3, "imbalanced_both": W.SEED_BASE + 3,
+         "imbalanced_small_first": W.SEED_BASE + 3,
          "plain_small": W.SEED_BASE + 1, "wide_keys": W.SEED_BASE + 6}
 DESCRIPTIONS = {
     "batched": "2,048 order-3 pairs, lengths 16..512, one paired mode, nnz log-uniform 1e2..1e5 each, one batch call",
@@ -56,12 +59,15 @@ DESCRIPTIONS = {
     "plain_large": "X,Y order-4 256^4 COO, 5e6 uniform nnz each, X modes (2,3) x Y modes (0,1), FP64",
     "imbalanced": "X 4096x512x512 2e7 nnz, Y 512x512x64 2e4 nnz with Zipf(1.2) contract keys, X (1,2) x Y (0,1)",
     "imbalanced_both": "as imbalanced, X contract keys also Zipf(1.2)",
+    "imbalanced_small_first": "as imbalanced with the operands given the other way round (Y (x) X, output modes "
+                              "permuted back)",
     "plain_small": "X,Y order-3 64^3 COO, 5e3 distinct nnz each, X mode 2 x Y mode 0",
     "wide_keys": "X 256x256x65536x65536, Y 65536x65536x256x256, 5e6 nnz each, X modes (2,3) x Y modes (0,1) "
                  "(2^32 contract keys, renumbered to dense ids); paired cells from one pool of 65,536",
 }
 # Rows of X (first coordinate < bound) that make the oracle's bounded CPU sample.
-CPU_SAMPLE_X0 = {"batched": 0, "plain_large": 7, "plain_large_slice": 1, "imbalanced": 4096, "imbalanced_both": 64, "plain_small": 64,
+CPU_SAMPLE_X0 = {"batched": 0, "plain_large": 7, "plain_large_slice": 1, "imbalanced": 4096, "imbalanced_both": 64,
+                 "imbalanced_small_first": 4096, "plain_small": 64,
                  "wide_keys": 7}
 
 
@@ -193,7 +199,7 @@ def dist_env():
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
 # kernel, from an ncu capture of the current kernels with the default strategy and
 # accumulator; workloads without a capture report null.
-NCU_TRAFFIC = {"plain_large": ("group_stream_kernel", 2.956e9 + 9.284e9),
+NCU_TRAFFIC = {"plain_large": ("group_stream_kernel", 2.876e9 + 9.198e9),
                "imbalanced": ("x_survey_kernel", 0.2746e9 + 0.0075e9)}
 
 
@@ -428,6 +434,7 @@ def main(argv=None):
     ap.add_argument("--group-load-factor", type=float, default=0.0, help="0 = library default")
     ap.add_argument("--accumulator", type=int, default=0, help="0 auto, 1 hash tables, 2 dense rows")
     ap.add_argument("--contract-ids", type=int, default=0, help="0 auto, 1 direct contract keys, 2 dense ids")
+    ap.add_argument("--operands", type=int, default=0, help="0 auto, 1 as given, 2 swapped")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -490,12 +497,12 @@ def main(argv=None):
         def step(record=False):
             return stc.contract(X, Y, p.cx, p.cy, p.out_order, strategy=args.strategy, record_times=record,
                                 group_load_factor=args.group_load_factor, accumulator=args.accumulator,
-                                contract_ids=args.contract_ids, stream=stream, ctx=ctx)
+                                contract_ids=args.contract_ids, operands=args.operands, stream=stream, ctx=ctx)
 
     for _ in range(args.warmup):
         r = step()
         nz, oz, P, launches, ns = r.nnz, r.order, r.stats.products, r.stats.launches, r.stats.survivors
-        cids = r.stats.contract_ids
+        cids, swp = r.stats.contract_ids, r.stats.swapped
         del r
     torch.cuda.synchronize()
 
@@ -561,7 +568,7 @@ def main(argv=None):
             Yd = (p.Y.shape, hy[0].to("cuda", non_blocking=True), hy[1].to("cuda", non_blocking=True))
             r = stc.contract(Xd, Yd, p.cx, p.cy, p.out_order, strategy=args.strategy,
                              group_load_factor=args.group_load_factor, accumulator=args.accumulator,
-                             contract_ids=args.contract_ids, stream=stream, ctx=ctx)
+                             contract_ids=args.contract_ids, operands=args.operands, stream=stream, ctx=ctx)
             hc[: r.nnz].copy_(r.coords, non_blocking=True)
             hv[: r.nnz].copy_(r.vals, non_blocking=True)
             torch.cuda.synchronize()
@@ -605,7 +612,7 @@ def main(argv=None):
     dom_ms = per_step[dom]
     achieved = kernel_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
     step_ms = ms / args.steps
-    default_opts = args.strategy == 0 and args.accumulator == 0 and args.contract_ids == 0
+    default_opts = args.strategy == 0 and args.accumulator == 0 and args.contract_ids == 0 and args.operands == 0
     traffic = NCU_TRAFFIC.get(args.workload) if default_opts else None
     roofline = {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic[1] if traffic else None,
@@ -627,7 +634,8 @@ def main(argv=None):
                    "products_per_step": P, "nnz_out": nz, "parallelism": f"replicas x{world}",
                    "l2": l2_note(bytes_in, (4 * oz + 8) * nz), "strategy": args.strategy,
                    "group_load_factor": args.group_load_factor, "accumulator": args.accumulator,
-                   "contract_ids_mode": args.contract_ids, "contract_ids": int(cids)},
+                   "contract_ids_mode": args.contract_ids, "contract_ids": int(cids),
+                   "operands_mode": args.operands, "swapped": int(swp)},
         "step_hbm": {"alg_bytes": step_alg, "gbs": step_alg / (step_ms / 1e3) / 1e9,
                      "frac": step_alg / (step_ms / 1e3) / 1e9 / hbm},
         "stage_ms": {n: float(per_step[i]) for i, n in enumerate(stage_names)},

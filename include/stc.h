@@ -86,6 +86,15 @@ enum { STC_ACC_AUTO = 0, STC_ACC_HASH = 1, STC_ACC_DENSE = 2, STC_ACC_HASH_SCAN 
  * A DIRECT request with K > 2^26 is renumbered too. */
 enum { STC_IDS_AUTO = 0, STC_IDS_DIRECT = 1, STC_IDS_DENSE = 2 };
 
+/* Operand roles. Y is the tensor grouped by contract key (the array of Section 4.2), X the one
+ * streamed against it and grouped by free key. Eq. 2 gives the same output with the operands
+ * swapped and the output modes permuted back, and the paper's cost (Section 4.4: a processing
+ * term, nnz_X x cmode_Yavg and nnz_Z) is symmetric, as its Set 3 swap experiment shows
+ * (Section 5.4); on the device the grouping of Y costs more per entry than the survey of X. AUTO therefore swaps
+ * when Y has more than four times X's entries; AS_GIVEN never swaps; SWAPPED always does.
+ * stats.swapped records the choice. */
+enum { STC_OPERANDS_AUTO = 0, STC_OPERANDS_AS_GIVEN = 1, STC_OPERANDS_SWAPPED = 2 };
+
 typedef struct stc_opts {
   int32_t strategy;       /* STC_STRATEGY_*; 0 = AUTO */
   int32_t record_times;   /* nonzero: time each stage with CUDA events (stc_result_stats) */
@@ -95,6 +104,8 @@ typedef struct stc_opts {
                                class with t <= group_load_factor * slots. */
   int32_t accumulator;    /* STC_ACC_*; 0 = AUTO */
   int32_t contract_ids;   /* STC_IDS_*; 0 = AUTO */
+  int32_t operands;       /* STC_OPERANDS_*; 0 = AUTO */
+  int32_t reserved_;      /* set to 0 */
 } stc_opts;
 
 /* Per-call statistics of a finished contraction. */
@@ -112,6 +123,8 @@ typedef struct stc_stats {
   float stage_ms[8];      /* 0 group Y, 1 survey X, 2 group X, 3 plan, 4 accumulate, 5 compact/write */
   uint64_t contract_ids;  /* distinct contract keys of Y when the contract keys were renumbered
                              to dense ids (STC_IDS_DENSE), else 0 */
+  int32_t swapped;        /* 1 when the operands were swapped (STC_OPERANDS_*) */
+  int32_t reserved_;
 } stc_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -275,6 +288,12 @@ stc_status stc_result_info(const stc_result* r, int64_t* nnz, int32_t* order, co
 stc_status stc_result_data(const stc_result* r, const int32_t** coords, const double** vals);
 stc_status stc_result_stats(const stc_result* r, stc_stats* stats);
 stc_status stc_result_free(stc_result* r);
+
+/* A view of a result as an input tensor, for chains of contractions (the output of one
+ * feeding the next, as in Section 5.4's motivation): out->coords, vals and shape point into
+ * the result (device, device and host memory), valid until stc_result_free(r). Nothing is
+ * copied. */
+stc_status stc_result_as_coo(const stc_result* r, stc_coo* out);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,7 @@ STATUS_NAMES = {
 STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_GROUPED = 0, 1, 2
 ACC_AUTO, ACC_HASH, ACC_DENSE, ACC_HASH_SCAN = 0, 1, 2, 3
 IDS_AUTO, IDS_DIRECT, IDS_DENSE = 0, 1, 2
+OPERANDS_AUTO, OPERANDS_AS_GIVEN, OPERANDS_SWAPPED = 0, 1, 2
 STC_MAX_ORDER = 8
 
 
@@ -46,14 +47,16 @@ class stc_server_opts(C.Structure):
 
 class stc_opts(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double),
-                ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("contract_ids", C.c_int32)]
+                ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("contract_ids", C.c_int32),
+                ("operands", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class stc_stats(C.Structure):
     _fields_ = [("products", C.c_uint64), ("survivors", C.c_uint64), ("out_capacity", C.c_uint64),
                 ("table_slots", C.c_uint64), ("groups", C.c_uint64), ("strategy", C.c_int32),
                 ("nstages", C.c_int32), ("launches", C.c_uint32), ("accumulator", C.c_int32),
-                ("stage_ms", C.c_float * 8), ("contract_ids", C.c_uint64)]
+                ("stage_ms", C.c_float * 8), ("contract_ids", C.c_uint64), ("swapped", C.c_int32),
+                ("reserved_", C.c_int32)]
 
 
 EXPORTS = {
@@ -78,6 +81,7 @@ EXPORTS = {
                        C.c_int),
     "stc_group_keys_static": ([C.c_void_p, C.c_int64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "stc_dense_ids": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_uint64), C.c_void_p], C.c_int),
+    "stc_result_as_coo": ([C.c_void_p, C.POINTER(stc_coo)], C.c_int),
     "stc_result_info": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                          C.POINTER(C.POINTER(C.c_int64))], C.c_int),
     "stc_result_data": ([C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)], C.c_int),
@@ -352,6 +356,7 @@ class Stats:
     accumulator: int
     stage_ms: tuple
     contract_ids: int = 0
+    swapped: int = 0
 
 
 class Result:
@@ -366,7 +371,7 @@ class Result:
         st = stc_result_stats(handle)
         self.stats = Stats(st.products, st.survivors, st.out_capacity, st.table_slots, st.groups, st.strategy,
                            st.launches, st.accumulator, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))),
-                           st.contract_ids)
+                           st.contract_ids, st.swapped)
         self._coords = self._vals = None
 
     @property
@@ -394,17 +399,23 @@ class Result:
                 self._vals = torch.empty((0,), dtype=torch.float64, device="cuda")
         return self._vals
 
+    @property
+    def tensor(self):
+        """(shape, coords, vals): the result as the input of a further contraction (a chain),
+        with no copy; the tensors keep the result's memory alive."""
+        return (tuple(self.shape), self.coords, self.vals)
+
 
 
 def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, strategy: int = STRATEGY_AUTO,
              load_factor: float = 0.0, group_load_factor: float = 0.0, accumulator: int = ACC_AUTO,
-             contract_ids: int = IDS_AUTO, record_times: bool = False, stream=None,
-             ctx: Context = None) -> Result:
+             contract_ids: int = IDS_AUTO, operands: int = OPERANDS_AUTO, record_times: bool = False,
+             stream=None, ctx: Context = None) -> Result:
     """Z = X (x) Y (Eq. 2) on the GPU. X and Y are (shape, coords, vals) with coords a CUDA
     int32 [nnz, order] tensor and vals a CUDA float64 [nnz] tensor."""
     ctx = ctx or default_context()
     o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor), float(group_load_factor),
-                 int(accumulator), int(contract_ids))
+                 int(accumulator), int(contract_ids), int(operands), 0)
     return Result(stc_contract(ctx.handle, X, Y, cx, cy, out_order, o, stream))
 
 
@@ -415,7 +426,7 @@ def contract_batch(problems, *, group_load_factor: float = 0.0, record_times: bo
     problem."""
     ctx = ctx or default_context()
     bp = problems if isinstance(problems, BatchProblems) else BatchProblems(problems)
-    o = stc_opts(STRATEGY_GROUPED, 1 if record_times else 0, 0.0, float(group_load_factor), ACC_HASH, 0)
+    o = stc_opts(STRATEGY_GROUPED, 1 if record_times else 0, 0.0, float(group_load_factor), ACC_HASH, 0, 0, 0)
     return [Result(h) for h in stc_contract_batch(ctx.handle, bp, o, stream)]
 
 

@@ -904,6 +904,23 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
     return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
   if (o.contract_ids < 0 || o.contract_ids > STC_IDS_DENSE)
     return fail(STC_ERR_INVALID_ARG, "unknown contract_ids %d", o.contract_ids);
+  if (o.operands < 0 || o.operands > STC_OPERANDS_SWAPPED)
+    return fail(STC_ERR_INVALID_ARG, "unknown operands %d", o.operands);
+  if (o.operands == STC_OPERANDS_SWAPPED ||
+      (o.operands == STC_OPERANDS_AUTO && (uint64_t)Y->nnz > 4 * (uint64_t)X->nnz)) {
+    // Y (x) X has output modes (Y free, X free); map each requested mode onto that order.
+    const int nfx = X->order - m, nfy = Y->order - m;
+    std::vector<int32_t> oo(nfx + nfy);
+    for (int q = 0; q < nfx + nfy; q++) {
+      const int t = out_order ? out_order[q] : q;
+      oo[q] = t < nfx ? nfy + t : t - nfx;
+    }
+    stc_opts inner = o;
+    inner.operands = STC_OPERANDS_AS_GIVEN;
+    STC_TRY(stc_contract(ctx, Y, X, m, cy, cx, oo.data(), &inner, stream, out));
+    (*out)->stats.swapped = 1;
+    return STC_OK;
+  }
   if (use_dense_ids(pl, X, Y, o.contract_ids)) {
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
@@ -1421,6 +1438,16 @@ stc_status stc_result_data(const stc_result* r, const int32_t** coords, const do
 stc_status stc_result_stats(const stc_result* r, stc_stats* stats) {
   if (!r || !stats) return fail(STC_ERR_INVALID_ARG, "NULL argument");
   *stats = r->stats;
+  return STC_OK;
+}
+
+stc_status stc_result_as_coo(const stc_result* r, stc_coo* out) {
+  if (!r || !out) return fail(STC_ERR_INVALID_ARG, "NULL argument");
+  out->order = r->order;
+  out->shape = r->shape.empty() ? nullptr : r->shape.data();
+  out->nnz = r->nnz;
+  out->coords = r->coords;
+  out->vals = r->vals;
   return STC_OK;
 }
 
