@@ -231,7 +231,8 @@ stc_status stc_server_destroy(stc_server* s);
 
 /* The exact product count of the contraction (Section 4.3: each X entry meets exactly
  * count_Y[its contract key] Y entries) and the device bytes a stc_contract of the same
- * inputs would hold at its peak (scratch + result). Used to admit work under a budget. */
+ * inputs with default options would hold at its peak (scratch + result), for the operand
+ * order and contract-key handling AUTO picks. Used to admit work under a budget. */
 stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t ncontract,
                      const int32_t* cx, const int32_t* cy, void* stream, uint64_t* products,
                      uint64_t* bytes_bound);

@@ -25,7 +25,8 @@ struct TuneEntry {
   int best = -1;
   float ms[kTuneCand] = {};
   bool done[kTuneCand] = {};
-  bool pending[kTuneCand] = {};
+  bool pending[kTuneCand] = {};   // handed to a batch, not yet read back
+  bool recorded[kTuneCand] = {};  // that batch has recorded both events
   cudaEvent_t ev0[kTuneCand] = {}, ev1[kTuneCand] = {};
 };
 
@@ -47,12 +48,22 @@ double tune_pick(stc_ctx* ctx, int bucket, int* measure) {
   TuneEntry& te = ctx->tune[bucket];
   *measure = -1;
   if (te.best >= 0) return kTuneAlpha[te.best];
+  // Only candidates whose batch has recorded both events are read: a batch of another thread
+  // may still be between picking a candidate and recording its events (an event never
+  // recorded reads as complete). A failed read is cleared so that it cannot surface as the
+  // error of a later call on this thread, and the candidate is timed again.
   for (int c = 0; c < kTuneCand; c++) {
-    if (te.pending[c] && cudaEventQuery(te.ev1[c]) == cudaSuccess) {
-      cudaEventElapsedTime(&te.ms[c], te.ev0[c], te.ev1[c]);
-      te.pending[c] = false;
-      te.done[c] = true;
+    if (!te.pending[c] || !te.recorded[c]) continue;
+    const cudaError_t q = cudaEventQuery(te.ev1[c]);
+    if (q == cudaErrorNotReady) {
+      cudaGetLastError();
+      continue;
     }
+    const cudaError_t e = q == cudaSuccess ? cudaEventElapsedTime(&te.ms[c], te.ev0[c], te.ev1[c]) : q;
+    if (e != cudaSuccess) cudaGetLastError();
+    te.pending[c] = false;
+    te.recorded[c] = false;
+    te.done[c] = e == cudaSuccess;
   }
   int best = 0;
   bool all = true;
@@ -67,10 +78,19 @@ double tune_pick(stc_ctx* ctx, int bucket, int* measure) {
   }
   for (int c = 0; c < kTuneCand; c++) {
     if (!te.done[c] && !te.pending[c]) {
-      if (!te.ev0[c] && (cudaEventCreate(&te.ev0[c]) != cudaSuccess || cudaEventCreate(&te.ev1[c]) != cudaSuccess))
-        return 0.75;
+      if (!te.ev1[c]) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+          cudaGetLastError();
+          if (a) cudaEventDestroy(a);
+          return 0.75;  // untimed; the default
+        }
+        te.ev0[c] = a;
+        te.ev1[c] = b;
+      }
       *measure = c;
       te.pending[c] = true;
+      te.recorded[c] = false;
       return kTuneAlpha[c];
     }
   }
@@ -80,13 +100,18 @@ void tune_mark(stc_ctx* ctx, int bucket, int cand, bool end, cudaStream_t s) {
   if (cand < 0) return;
   std::lock_guard<std::mutex> lk(ctx->tune_mu);
   TuneEntry& te = ctx->tune[bucket];
-  cudaEventRecord(end ? te.ev1[cand] : te.ev0[cand], s);
+  if (cudaEventRecord(end ? te.ev1[cand] : te.ev0[cand], s) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (end) te.recorded[cand] = true;
 }
 // A batch that failed after picking a candidate gives it back.
 void tune_abort(stc_ctx* ctx, int bucket, int cand) {
   if (cand < 0) return;
   std::lock_guard<std::mutex> lk(ctx->tune_mu);
   ctx->tune[bucket].pending[cand] = false;
+  ctx->tune[bucket].recorded[cand] = false;
 }
 int log2_floor(uint64_t v) { return v ? 63 - __builtin_clzll(v) : 0; }
 }  // namespace
@@ -330,11 +355,13 @@ stc_status make_plan(const stc_coo* X, const stc_coo* Y, int32_t m, const int32_
   pl.op.order = pl.oz;
   pl.op.pow2 = 1;
   pl.op.z32 = pl.F <= (1ull << 32);
+  pl.op.ident = 1;
   pl.zshape.assign(pl.oz, 0);
   std::vector<int> pos_of(pl.oz);  // output position of concatenated mode t
   for (int q = 0; q < pl.oz; q++) {
     const int t = out_order ? out_order[q] : q;
     pos_of[t] = q;
+    if (t != q) pl.op.ident = 0;
     pl.op.mod[q] = csize[t];
     pl.zshape[q] = (int64_t)csize[t];
     if (!is_pow2(csize[t])) pl.op.pow2 = 0;
@@ -681,7 +708,8 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
       STC_TRY(ar.alloc(&sa.rec, (size_t)nstream * nseg));
       sa.nrec = &gc->stream_nrec;
       sa.holes = &gc->stream_holes;
-      STC_CUDA(launch_group_stream(a, pr.yoff, nseg, seg, b.dense_list[0], nstream, sa, ctx->sms, s));
+      const bool fixed_rows = !pl.op.pow2 && pl.op.ident && pl.op.order >= 2 && pl.op.order <= 8;
+      STC_CUDA(launch_group_stream(a, pr.yoff, nseg, seg, b.dense_list[0], nstream, sa, fixed_rows, ctx->sms, s));
     }
   }
   tm.mark(4);
@@ -1297,6 +1325,9 @@ stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m
   if (!ctx) return fail(STC_ERR_INVALID_ARG, "ctx is NULL");
   Plan pl;
   STC_TRY(make_plan(X, Y, m, cx, cy, nullptr, pl));
+  // Bound the orientation stc_contract's AUTO operand order will run (P is the same).
+  if ((uint64_t)Y->nnz > 4 * (uint64_t)X->nnz)
+    return stc_count(ctx, Y, X, m, cy, cx, stream, products, bytes_bound);
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

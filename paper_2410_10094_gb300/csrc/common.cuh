@@ -55,7 +55,7 @@ struct OutPlan {
   int32_t order;
   int32_t pow2;
   int32_t z32;
-  int32_t pad_;
+  int32_t ident;                 // output modes in concatenation order (no permutation)
   uint64_t mod[kMaxOutOrder];    // length of output mode q
   uint32_t shift[kMaxOutOrder];  // power-of-two plans: bit offset of output mode q
   uint64_t magic[kMaxOutOrder];  // multiplier m of digit j
@@ -219,7 +219,51 @@ __device__ __forceinline__ void st_stream_f64(double* ptr, double v, uint64_t po
   asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(ptr), "d"(v), "l"(pol) : "memory");
 }
 
+// Output rows of O coordinates in concatenation order, not all lengths powers of two: the
+// digits are decoded into registers (digit j is coordinate O-1-j) and stored in pairs with
+// 8-byte stores where the row allows.
+template <int O>
+__device__ __forceinline__ void store_row_fixed(int32_t* __restrict__ dst, uint64_t zkey, const OutPlan& op,
+                                                uint64_t pol) {
+  int32_t c[O];
+  if (op.z32) {
+    uint32_t z = (uint32_t)zkey;
+#pragma unroll
+    for (int j = 0; j < O; j++) {
+      const uint32_t t = __umulhi(z, (uint32_t)op.magic[j]);
+      const uint32_t q = (t + ((z - t) >> op.dsh1[j])) >> op.dsh2[j];
+      c[O - 1 - j] = (int32_t)(z - q * (uint32_t)op.mod[O - 1 - j]);
+      z = q;
+    }
+  } else {
+    uint64_t z = zkey;
+#pragma unroll
+    for (int j = 0; j < O; j++) {
+      const uint64_t t = __umul64hi(z, op.magic[j]);
+      const uint64_t q = (t + ((z - t) >> op.dsh1[j])) >> op.dsh2[j];
+      c[O - 1 - j] = (int32_t)(z - q * op.mod[O - 1 - j]);
+      z = q;
+    }
+  }
+  const int first = (reinterpret_cast<uintptr_t>(dst) & 7u) ? 1 : 0;  // 0 or 1 single store first
+  if (first) st_stream_s32(dst, c[0], pol);
+#pragma unroll
+  for (int k = 0; k < O; k++) {
+    if (k < first || ((k - first) & 1)) continue;
+    if (k + 1 < O) {
+      asm volatile("st.global.L2::cache_hint.v2.s32 [%0], {%1, %2}, %3;" ::"l"(dst + k), "r"(c[k]), "r"(c[k + 1]),
+                   "l"(pol)
+                   : "memory");
+    } else {
+      st_stream_s32(dst + k, c[k], pol);
+    }
+  }
+}
+
 // Writes output entry `pos` (coordinates decoded from zkey, and its value) with streaming stores.
+// FIXED = false leaves out the register-decoded rows of store_row_fixed (a smaller body for
+// kernels whose hot path is the power-of-two one).
+template <bool FIXED = true>
 __device__ __forceinline__ void store_output(int32_t* __restrict__ coords, double* __restrict__ vals, unsigned long long pos,
                                              uint64_t zkey, double v, const OutPlan& op, uint64_t pol) {
   int32_t* dst = coords + pos * (uint64_t)op.order;
@@ -232,6 +276,16 @@ __device__ __forceinline__ void store_output(int32_t* __restrict__ coords, doubl
     st_stream_v4(dst, cv, pol);
   } else if (op.pow2) {
     for (int q = 0; q < op.order; q++) st_stream_s32(dst + q, out_coord_pow2(zkey, op, q), pol);
+  } else if (FIXED && op.ident && op.order >= 2 && op.order <= 8) {
+    switch (op.order) {
+      case 2: store_row_fixed<2>(dst, zkey, op, pol); break;
+      case 3: store_row_fixed<3>(dst, zkey, op, pol); break;
+      case 4: store_row_fixed<4>(dst, zkey, op, pol); break;
+      case 5: store_row_fixed<5>(dst, zkey, op, pol); break;
+      case 6: store_row_fixed<6>(dst, zkey, op, pol); break;
+      case 7: store_row_fixed<7>(dst, zkey, op, pol); break;
+      default: store_row_fixed<8>(dst, zkey, op, pol); break;
+    }
   } else {
     decode_digits(zkey, op, [&](int q, int32_t c) { st_stream_s32(dst + q, c, pol); });
   }

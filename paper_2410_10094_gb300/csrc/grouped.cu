@@ -1329,7 +1329,10 @@ constexpr uint32_t kStreamSlots = kStreamCap / 32 + kStreamEntries;
 constexpr size_t kStreamSmem = (size_t)kBitmapWords * 8 + (size_t)kStreamSlots * 8 + (size_t)kStreamEntries * 8 +
                                (size_t)kStreamCap * 2 + (size_t)kStreamCap;
 
-template <int U>
+// FIXED: output rows of 2..8 coordinates in concatenation order with some length not a power
+// of two, decoded into registers and stored in pairs (store_row_fixed); a separate
+// instantiation so that the power-of-two kernel keeps its own code.
+template <int U, bool FIXED>
 __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kernel(GroupArgs a, const uint32_t* __restrict__ yoff,
                                                                         uint32_t nseg, uint32_t seg,
                                                                         const uint32_t* __restrict__ list,
@@ -1527,7 +1530,7 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
                     st_stream_v4(coords + pos * 4, cv, pol);
                     vals[pos] = prod;  // default policy: a repeat may still add to it
                   } else {
-                    store_output(coords, vals, pos, zseg + fk, prod, tg.op, pol);
+                    store_output<FIXED>(coords, vals, pos, zseg + fk, prod, tg.op, pol);
                   }
                 } else {
                   const u64 pos = gbase + Pq - 1 - ((base >> 16) + __popc(rm & lt));
@@ -2016,11 +2019,12 @@ uint32_t dense_stash_cap() { return kStashCap; }
 uint32_t dense_stream_cap() { return kStreamCap; }
 
 cudaError_t launch_group_stream(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
-                                const uint32_t* list, uint32_t count, StreamArgs sa, int sms, cudaStream_t s) {
+                                const uint32_t* list, uint32_t count, StreamArgs sa, bool fixed_rows, int sms,
+                                cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   if (seg < 64 || seg > kDenseSeg) return cudaErrorInvalidValue;
   constexpr int U = STREAM_U;
-  auto kern = group_stream_kernel<U>;
+  auto kern = fixed_rows ? group_stream_kernel<U, true> : group_stream_kernel<U, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStreamSmem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

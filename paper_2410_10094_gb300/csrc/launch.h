@@ -287,8 +287,10 @@ struct StreamArgs {
 };
 uint32_t dense_stream_cap();
 // Streamed groups (B_g <= dense_stream_cap()); launched after every other accumulation kernel.
+// fixed_rows: the output plan has 2..8 modes in concatenation order, not all powers of two.
 cudaError_t launch_group_stream(const GroupArgs& a, const uint32_t* yoff, uint32_t nseg, uint32_t seg,
-                                const uint32_t* list, uint32_t count, StreamArgs sa, int sms, cudaStream_t s);
+                                const uint32_t* list, uint32_t count, StreamArgs sa, bool fixed_rows, int sms,
+                                cudaStream_t s);
 // Moves the entries above nnz into the holes below it.
 // holes_total < 2^32 (positions above nnz are kept as 32-bit offsets).
 cudaError_t launch_stream_fill(const StreamRec* rec, const unsigned* nrec, u64 nnz, u64 holes_total, uint32_t* src_pos,
