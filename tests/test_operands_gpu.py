@@ -62,7 +62,8 @@ def test_auto_swaps_when_y_is_larger():
 
 
 def test_imbalanced_given_small_first():
-    """Config 3's pair written small-first (2e4 entries (x) 2e7): AUTO swaps it back."""
+    """The imbalanced pair (Y 512x512x64 with 2e4 entries, X 4096x512x512 with 2e7) written
+    small-first: AUTO swaps it back."""
     import paper_2410_10094_gb300 as stc
 
     p = W.imbalanced()
