@@ -65,10 +65,6 @@ DESCRIPTIONS = {
     "wide_keys": "X 256x256x65536x65536, Y 65536x65536x256x256, 5e6 nnz each, X modes (2,3) x Y modes (0,1) "
                  "(2^32 contract keys, renumbered to dense ids); paired cells from one pool of 65,536",
 }
-# Rows of X (first coordinate < bound) that make the oracle's bounded CPU sample.
-CPU_SAMPLE_X0 = {"batched": 0, "plain_large": 7, "plain_large_slice": 1, "imbalanced": 4096, "imbalanced_both": 64,
-                 "imbalanced_small_first": 4096, "plain_small": 64,
-                 "wide_keys": 7}
 
 
 def peaks():
@@ -214,27 +210,55 @@ def alg_bytes(p, nz, oz):
     return (4 * p.X.order + 8) * p.X.nnz + (4 * p.Y.order + 8) * p.Y.nnz + (4 * oz + 8) * nz
 
 
-def cpu_sample(p, workload):
-    bound = CPU_SAMPLE_X0[workload]
-    sel = p.X.coords[:, 0] < bound
-    return W.Problem(p.X.take(sel), p.Y, p.cx, p.cy, p.out_order), \
-        f"X entries with first coordinate < {bound} ({int(sel.sum())} of {p.X.nnz}), all of Y"
+def key_sample(p, m):
+    """The sub-contraction over the paired cells whose cell number is a multiple of m: every
+    entry of X and Y on those cells, so every product of the sample is one of the workload's
+    and each cell keeps all its work."""
+    if m <= 1:
+        return p, "the whole workload"
+
+    def cell(t, modes):
+        c = np.zeros(t.nnz, dtype=np.int64)
+        for j in modes:
+            c = (c * 1_000_003 + t.coords[:, j]) % (1 << 40)
+        return c
+
+    xi = np.flatnonzero(cell(p.X, p.cx) % m == 0)
+    yi = np.flatnonzero(cell(p.Y, p.cy) % m == 0)
+    return W.Problem(p.X.take(xi), p.Y.take(yi), p.cx, p.cy, p.out_order), \
+        f"the paired cells with cell number = 0 mod {m}: {xi.size} of {p.X.nnz} X and {yi.size} of {p.Y.nnz} Y entries"
 
 
-def run_oracle_sample(p, workload):
+def run_oracle_sample(p, workload, m=1):
+    """One timed oracle call on key_sample(p, m) (batches: the first 48 // m pairs)."""
     import oracle
 
     if workload == "batched":
+        n = max(1, 48 // max(m, 1))
         t0 = time.perf_counter()
         prods = 0
-        for q in p[:48]:
+        for q in p[:n]:
             prods += oracle.contract(q.X, q.Y, q.cx, q.cy).products
-        return prods, time.perf_counter() - t0, "the first 48 of the 2,048 pairs, one after another"
-    sp, desc = cpu_sample(p, workload)
+        return prods, time.perf_counter() - t0, f"the first {n} of the 2,048 pairs, one after another"
+    sp, desc = key_sample(p, m)
     t0 = time.perf_counter()
     r = oracle.contract(sp.X, sp.Y, sp.cx, sp.cy, sp.out_order)
     dt = time.perf_counter() - t0
     return r.products, dt, desc
+
+
+REF_SECONDS = 120.0  # the reference arm's whole run (warm-up and timed steps) on the host
+CPU_SECONDS = 15.0   # the one timed oracle call of cpu_baseline
+
+
+def sample_fraction(p, workload, seconds):
+    """m such that key_sample(p, m) takes about `seconds` in the oracle, estimated from one
+    untimed call on 1/4096 of the paired cells. The oracle's ordered maps make its time grow
+    about as size^1.1 (measured between 1/4096 and 1/16 of plain_large)."""
+    probe = 4096
+    _, t_probe, _ = run_oracle_sample(p, workload, probe)
+    grow = (seconds / max(t_probe, 1e-6)) ** (1 / 1.1)
+    return max(1, int(np.ceil(probe / grow)))
 
 
 def reference_arm(args):
@@ -249,11 +273,14 @@ def reference_arm(args):
         print(json.dumps({"impl": "reference", "unavailable": ap_err}), flush=True)
         return 0
     p = WORKLOADS[args.workload](SEEDS[args.workload])
+    # Each step is the sub-contraction over 1/m of the paired cells, m chosen so that warm-up
+    # and timed steps together take about REF_SECONDS.
+    m = sample_fraction(p, args.workload, REF_SECONDS / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        run_oracle_sample(p, args.workload)
+        run_oracle_sample(p, args.workload, m)
     prods, times, desc = 0, [], ""
     for _ in range(args.steps):
-        pr, dt, desc = run_oracle_sample(p, args.workload)
+        pr, dt, desc = run_oracle_sample(p, args.workload, m)
         prods += pr
         times.append(dt)
     total = sum(times)
@@ -622,7 +649,8 @@ def main(argv=None):
 
     cpu = None
     if not args.no_cpu_baseline:
-        prods, dt, desc = run_oracle_sample(workload_problem, args.workload)
+        m = sample_fraction(workload_problem, args.workload, CPU_SECONDS) if args.workload != "batched" else 1
+        prods, dt, desc = run_oracle_sample(workload_problem, args.workload, m)
         cpu = {"value": prods / dt, "unit": "products/s", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": dt}
 
