@@ -255,6 +255,17 @@ def sample_fraction(p, workload, seconds):
     """m such that key_sample(p, m) takes about `seconds` in the oracle, estimated from one
     untimed call on 1/4096 of the paired cells. The oracle's ordered maps make its time grow
     about as size^1.1 (measured between 1/4096 and 1/16 of plain_large)."""
+    if workload == "batched":  # m selects the first 48 // m pairs: count how many fit
+        import oracle
+
+        t, n = 0.0, 0
+        while n < 48 and t < seconds:
+            q = p[n]
+            t0 = time.perf_counter()
+            oracle.contract(q.X, q.Y, q.cx, q.cy)
+            t += time.perf_counter() - t0
+            n += 1
+        return max(1, -(-48 // max(1, n - 1)))  # at most the n - 1 pairs that fitted
     probe = 4096
     _, t_probe, _ = run_oracle_sample(p, workload, probe)
     grow = (seconds / max(t_probe, 1e-6)) ** (1 / 1.1)
