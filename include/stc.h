@@ -243,7 +243,7 @@ stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t n
 stc_status stc_linearize(stc_ctx* ctx, const stc_coo* T, int32_t nmodes, const int32_t* modes,
                          uint64_t* keys_out, void* stream);
 
-/* Group n keys in [0, k) with a counting sort (Section 4.1.1, Fig. 5): count, exclusive
+/* Group n keys in [0, k) with a counting sort (Section 4.1.1, Fig. 6): count, exclusive
  * scan, scatter. offsets_out: device, [k+1], offsets_out[v] = first slot of key v and
  * offsets_out[k] = n. perm_out: device, [n], perm_out[s] = index of the key placed in
  * slot s; the order inside one key's run is unspecified. keys: device, [n]. Requires
@@ -251,7 +251,7 @@ stc_status stc_linearize(stc_ctx* ctx, const stc_coo* T, int32_t nmodes, const i
 stc_status stc_group_keys(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t k,
                           uint32_t* offsets_out, uint32_t* perm_out, void* stream);
 
-/* Small numbers for large keys (Section 4.1.2, Fig. 6): ids_out[i] = the dense id of
+/* Small numbers for large keys (Section 4.1.2, Fig. 7): ids_out[i] = the dense id of
  * keys[i], with ids in [0, D), equal keys sharing one id and distinct keys distinct ids,
  * where D = the number of distinct keys, written to *ndistinct. Every 64-bit value is a
  * valid key. Which key gets which id is unspecified (the paper numbers keys in order of

@@ -9,8 +9,8 @@ Functions and the passages they follow (Swift, arXiv 2410.10094):
 
 * :func:`contract`         Eq. 2, the contraction itself (Section 2.1.3)
 * :func:`ln_key`           the LN key of a mode subset (Section 2.3.1, Fig. 3)
-* :func:`counting_sort`    count / cumulative sum / place (Section 4.1.1, Fig. 5)
-* :func:`first_seen_ids`   small numbers for keys (Section 4.1.2, Fig. 6)
+* :func:`counting_sort`    count / cumulative sum / place (Section 4.1.1, Fig. 6)
+* :func:`first_seen_ids`   small numbers for keys (Section 4.1.2, Fig. 7)
 * :func:`group_bounds`     exact per-group table bound (Section 4.3)
 * :func:`table_slots`      the x1.3 probing-table rule (Section 2.2.1, Section 4.3)
 """
@@ -189,7 +189,7 @@ def ln_key(shape: Sequence[int], coords: np.ndarray, modes: Sequence[int]) -> np
 
 
 def counting_sort(keys: np.ndarray, k: int):
-    """Counting sort (Fig. 5): returns (offsets[k+1], perm[n]) with perm stable."""
+    """Counting sort (Fig. 6): returns (offsets[k+1], perm[n]) with perm stable."""
     L = _lib()
     ks = np.ascontiguousarray(keys, dtype=np.uint64)
     off = np.empty(int(k) + 1, dtype=np.int64)
@@ -201,7 +201,7 @@ def counting_sort(keys: np.ndarray, k: int):
 
 
 def first_seen_ids(keys: np.ndarray):
-    """Small numbers (Fig. 6): returns (ids[n], number of distinct keys)."""
+    """Small numbers (Fig. 7): returns (ids[n], number of distinct keys)."""
     L = _lib()
     ks = np.ascontiguousarray(keys, dtype=np.uint64)
     ids = np.empty(ks.shape[0], dtype=np.int64)

@@ -6,8 +6,8 @@
 // Each entry point writes out the definition, or the steps, of one passage of the paper:
 //   oracle_contract        the contraction itself, Eq. 2 (Section 2.1.3)
 //   oracle_ln_key          the "large number" (LN) key of a mode subset (Section 2.3.1, Fig. 3)
-//   oracle_counting_sort   counting sort: count, cumulative sum, place (Section 4.1.1, Fig. 5)
-//   oracle_first_seen_ids  small numbers assigned in order of first sight (Section 4.1.2, Fig. 6)
+//   oracle_counting_sort   counting sort: count, cumulative sum, place (Section 4.1.1, Fig. 6)
+//   oracle_first_seen_ids  small numbers assigned in order of first sight (Section 4.1.2, Fig. 7)
 //   oracle_group_bounds    exact accumulation-table bound per X free group (Section 4.3)
 //   oracle_table_slots     the x1.3 probing-table sizing rule (Section 2.2.1, Section 4.3)
 //
@@ -220,7 +220,7 @@ int oracle_ln_key(int32_t order, const int64_t* shape, int64_t n, const int32_t*
   return OK;
 }
 
-// Counting sort (Section 4.1.1, Fig. 5) of n keys in [0, k): count each value, take the
+// Counting sort (Section 4.1.1, Fig. 6) of n keys in [0, k): count each value, take the
 // cumulative sum so that cum[v] is one past the last slot of value v, then walk the input
 // and place each element at its value's pointer, decrementing the pointer. Walking from
 // the last element to the first keeps equal keys in input order.
@@ -249,7 +249,7 @@ int oracle_counting_sort(int64_t n, const uint64_t* keys, uint64_t k, int64_t* o
   return OK;
 }
 
-// Small numbers (Section 4.1.2, Fig. 6): scan the keys in order; a key already in the
+// Small numbers (Section 4.1.2, Fig. 7): scan the keys in order; a key already in the
 // table gets its stored number, a new key gets the number of keys stored so far.
 int oracle_first_seen_ids(int64_t n, const uint64_t* keys, int64_t* ids_out, int64_t* ndistinct) {
   if (n < 0 || ndistinct == nullptr || (n > 0 && (keys == nullptr || ids_out == nullptr))) return INVALID;

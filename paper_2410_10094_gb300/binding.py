@@ -506,7 +506,7 @@ def dense_ids(keys, *, stream=None, ctx: Context = None):
 
 
 def group_keys(keys, k: int, *, stream=None, ctx: Context = None):
-    """Counting-sort grouping (Fig. 5) of keys in [0, k): returns (offsets[k+1], perm[n])."""
+    """Counting-sort grouping (Fig. 6) of keys in [0, k): returns (offsets[k+1], perm[n])."""
     import torch
 
     ctx = ctx or default_context()

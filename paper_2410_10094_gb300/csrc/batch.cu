@@ -3,7 +3,7 @@
 // row offsets), Y is grouped over the concatenation of all problems' contract-key bins, and
 // X's survivors are grouped by (problem, X free key). Because the problems' X free key spaces
 // together are far too large to count directly, each distinct (problem, free key) pair gets a
-// small number through a probing table, in order of first sight (Section 4.1.2, Fig. 6).
+// small number through a probing table, in order of first sight (Section 4.1.2, Fig. 7).
 // The per-group accumulation then runs in the same class kernels as a single contraction.
 #include "launch.h"
 

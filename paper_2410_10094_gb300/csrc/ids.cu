@@ -1,4 +1,4 @@
-// Dense ids for keys whose space is too large to count directly (Section 4.1.2, Fig. 6).
+// Dense ids for keys whose space is too large to count directly (Section 4.1.2, Fig. 7).
 //
 // The paper gives each distinct key the next unused small number while it scans the keys
 // in order, so that a counting sort over the ids costs O(n). On the device the distinct

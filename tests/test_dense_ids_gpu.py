@@ -1,4 +1,4 @@
-"""GPU parity of dense ids for large contract key spaces (Section 4.1.2, Fig. 6): the
+"""GPU parity of dense ids for large contract key spaces (Section 4.1.2, Fig. 7): the
 stc_dense_ids entry point against the oracle's first-seen numbering, and contractions whose
 contract key space exceeds 2^26 (renumbered before grouping) against the oracle."""
 import numpy as np

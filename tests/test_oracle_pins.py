@@ -67,7 +67,7 @@ def test_golden_ln_key():
 
 
 def test_golden_counting_sort():
-    g = golden("counting_sort_fig5.json")
+    g = golden("counting_sort_fig6.json")
     keys = np.asarray(g["keys"], dtype=np.uint64)
     off, perm = oracle.counting_sort(keys, g["k"])
     assert off.tolist() == g["expect_offsets"]
@@ -79,7 +79,7 @@ def test_golden_counting_sort():
 
 
 def test_golden_first_seen():
-    g = golden("first_seen_fig6.json")
+    g = golden("first_seen_fig7.json")
     ids, nd = oracle.first_seen_ids(np.asarray(g["keys"], dtype=np.uint64))
     assert ids.tolist() == g["expect_ids"]
     assert nd == g["expect_distinct"]

@@ -292,7 +292,7 @@ def test_group_keys_matches_oracle_counting_sort():
         for v in np.unique(keys)[:50]:
             a, b = ref_off[v], ref_off[v + 1]
             assert sorted(perm[a:b]) == sorted(ref_perm[a:b])
-    g = __import__("helpers").golden("counting_sort_fig5.json")
+    g = __import__("helpers").golden("counting_sort_fig6.json")
     off, _ = stc.group_keys(torch.tensor(g["keys"], dtype=torch.int64).cuda(), g["k"])
     assert off.cpu().tolist() == g["expect_offsets"]
 
