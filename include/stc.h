@@ -6,7 +6,7 @@
  *     Z = X (x)_{cy}^{cx} Y,    z[fX, fY] = sum_c x[fX, c] * y[c, fY]     (Eq. 1, Eq. 2)
  *
  * X and Y are COO lists (Section 2.1.2); X mode cx[i] is paired with Y mode cy[i] and the
- * two must have equal lengths (Section 2.1.3). The output's modes are X's free modes in
+ * two must have equal lengths (Section 2.2). The output's modes are X's free modes in
  * ascending order followed by Y's free modes in ascending order (Eq. 4, Fig. 2), unless an
  * explicit output order permutes them.
  *
@@ -36,7 +36,7 @@ extern "C" {
 typedef enum stc_status {
   STC_OK = 0,
   STC_ERR_INVALID_ARG = 1,        /* null pointer, bad order, bad mode list, bad permutation */
-  STC_ERR_SHAPE_MISMATCH = 2,     /* paired modes have different lengths (Section 2.1.3) */
+  STC_ERR_SHAPE_MISMATCH = 2,     /* paired modes have different lengths (Section 2.2) */
   STC_ERR_KEY_OVERFLOW = 3,       /* a key space (product of mode lengths) needs > 64 bits */
   STC_ERR_OUT_OF_MEMORY = 4,      /* device allocation failed or the context budget is exceeded */
   STC_ERR_TABLE_FULL = 5,         /* an accumulation table overflowed (internal; never expected) */
@@ -146,7 +146,7 @@ stc_status stc_destroy(stc_ctx* ctx);
  *   ncontract   number of paired modes m, 0 <= m <= min(X.order, Y.order); m = 0 is the
  *               outer product, m = order of both gives an order-0 (scalar) output
  *   cx, cy      host, [m]; X mode cx[i] pairs with Y mode cy[i]; the lists order the
- *               contract key (first listed mode most significant, Section 2.3.1)
+ *               contract key (first listed mode most significant, Section 2.4.1)
  *   out_order   host, [orderZ] or NULL; output mode q holds entry out_order[q] of the
  *               concatenation (X free modes ascending, Y free modes ascending)
  *   opts        host or NULL (defaults)
@@ -237,7 +237,7 @@ stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t n
                      const int32_t* cx, const int32_t* cy, void* stream, uint64_t* products,
                      uint64_t* bytes_bound);
 
-/* LN keys of the listed modes of every entry of T (Section 2.3.1, Fig. 3): the coordinates
+/* LN keys of the listed modes of every entry of T (Section 2.4.1, Fig. 3): the coordinates
  * of modes[0..nmodes) read as digits of one mixed-radix number, modes[0] most significant,
  * each digit's radix its mode length. keys_out: device, [T.nnz]. */
 stc_status stc_linearize(stc_ctx* ctx, const stc_coo* T, int32_t nmodes, const int32_t* modes,

@@ -7,12 +7,12 @@ the library on linearised 64-bit keys in GPU hash tables.
 
 Functions and the passages they follow (Swift, arXiv 2410.10094):
 
-* :func:`contract`         Eq. 2, the contraction itself (Section 2.1.3)
-* :func:`ln_key`           the LN key of a mode subset (Section 2.3.1, Fig. 3)
+* :func:`contract`         Eq. 2, the contraction itself (Section 2.2)
+* :func:`ln_key`           the LN key of a mode subset (Section 2.4.1, Fig. 3)
 * :func:`counting_sort`    count / cumulative sum / place (Section 4.1.1, Fig. 6)
 * :func:`first_seen_ids`   small numbers for keys (Section 4.1.2, Fig. 7)
 * :func:`group_bounds`     exact per-group table bound (Section 4.3)
-* :func:`table_slots`      the x1.3 probing-table rule (Section 2.2.1, Section 4.3)
+* :func:`table_slots`      the x1.3 probing-table rule (Section 2.3.1, Section 4.3)
 """
 from __future__ import annotations
 
@@ -246,5 +246,5 @@ def group_bounds(X, Y, cx: Sequence[int], cy: Sequence[int]) -> Groups:
 
 
 def table_slots(bound: int) -> int:
-    """Slots of a probing table for ``bound`` entries under the x1.3 rule (Section 2.2.1)."""
+    """Slots of a probing table for ``bound`` entries under the x1.3 rule (Section 2.3.1)."""
     return int(_lib().oracle_table_slots(int(bound)))

@@ -4,12 +4,12 @@
 // shares no code with the CUDA path.
 //
 // Each entry point writes out the definition, or the steps, of one passage of the paper:
-//   oracle_contract        the contraction itself, Eq. 2 (Section 2.1.3)
-//   oracle_ln_key          the "large number" (LN) key of a mode subset (Section 2.3.1, Fig. 3)
+//   oracle_contract        the contraction itself, Eq. 2 (Section 2.2)
+//   oracle_ln_key          the "large number" (LN) key of a mode subset (Section 2.4.1, Fig. 3)
 //   oracle_counting_sort   counting sort: count, cumulative sum, place (Section 4.1.1, Fig. 6)
 //   oracle_first_seen_ids  small numbers assigned in order of first sight (Section 4.1.2, Fig. 7)
 //   oracle_group_bounds    exact accumulation-table bound per X free group (Section 4.3)
-//   oracle_table_slots     the x1.3 probing-table sizing rule (Section 2.2.1, Section 4.3)
+//   oracle_table_slots     the x1.3 probing-table sizing rule (Section 2.3.1, Section 4.3)
 //
 // Floating point: FP64 throughout. The build passes -ffp-contract=off so that every
 // product x*y is rounded before it is added (no fused multiply-add).
@@ -59,7 +59,7 @@ std::vector<int32_t> free_modes(int32_t order, const std::vector<int32_t>& contr
 }
 
 // Validates the contraction's mode lists: cx[i] pairs with cy[i] and both have the same
-// length (Section 2.1.3: contracted modes must have equal lengths).
+// length (Section 2.2: contracted modes must have equal lengths).
 int check_pairs(const Tensor& X, const Tensor& Y, int32_t m, const int32_t* cx, const int32_t* cy,
                 std::vector<int32_t>& vx, std::vector<int32_t>& vy) {
   if (m < 0 || m > X.order || m > Y.order) return INVALID;
@@ -194,7 +194,7 @@ void oracle_result_copy(void* h, int32_t* coords, double* vals, double* abs, int
 
 void oracle_result_free(void* h) { delete static_cast<ContractResult*>(h); }
 
-// The LN key (Section 2.3.1, Fig. 3): the coordinates of the listed modes read as the
+// The LN key (Section 2.4.1, Fig. 3): the coordinates of the listed modes read as the
 // digits of one mixed-radix number, the first listed mode most significant and each
 // digit's radix its mode's length. Fig. 3's two-mode example with length 10 maps (5, 1)
 // to 51. Written in Horner form, key = (...(c0 * n1 + c1) * n2 + c2 ...).
@@ -333,7 +333,7 @@ void oracle_groups_copy(void* h, int32_t* coords, uint64_t* bound, int64_t* entr
 void oracle_groups_free(void* h) { delete static_cast<GroupResult*>(h); }
 
 // Probing tables are commonly made 1.3 times the largest number of entries they must hold
-// (Section 2.2.1); the Section 4.3 example turns a bound of 7 into 9 slots, i.e. the
+// (Section 2.3.1); the Section 4.3 example turns a bound of 7 into 9 slots, i.e. the
 // integer part of 1.3 * bound.
 uint64_t oracle_table_slots(uint64_t bound) { return (uint64_t)std::floor(1.3 * (double)bound); }
 

@@ -247,7 +247,7 @@ uint32_t log2_u64(uint64_t v) {
   return r;
 }
 
-// The key plan of a contraction (Section 2.3.1 LN keys; the output mode order of Eq. 4).
+// The key plan of a contraction (Section 2.4.1 LN keys; the output mode order of Eq. 4).
 struct Plan {
   KeyPlan kx{}, ky{};
   OutPlan op{};

@@ -24,7 +24,7 @@ enum : uint32_t {
   kStatTooLarge = 16u,    // one group's table would exceed 2^31 slots
 };
 
-// How one input tensor's coordinates map to its two keys (Section 2.3.1, the LN key):
+// How one input tensor's coordinates map to its two keys (Section 2.4.1, the LN key):
 // ckey = sum_j coord[j] * cstride[j] (contract modes, in the order of the contract list),
 // fkey = sum_j coord[j] * fstride[j] (free modes, ascending). A mode has a nonzero stride
 // in exactly one of the two. size[] bounds-checks each coordinate.

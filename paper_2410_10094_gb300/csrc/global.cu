@@ -1,6 +1,6 @@
-// Contraction and accumulation into one device-wide open-addressing table (Section 2.3.2
+// Contraction and accumulation into one device-wide open-addressing table (Section 2.4.2
 // contraction; Section 4.3 probing table sized from the exact product count), followed
-// by the writeback of occupied slots as COO output (Section 2.3.3).
+// by the writeback of occupied slots as COO output (Section 2.5).
 //
 // This is the "leave X ungrouped" form noted at the end of Section 4.4: every product
 // goes to one global table keyed on the full output key. It is chosen when the output
@@ -15,7 +15,7 @@ constexpr int kExThreads = 256;
 constexpr int kExTile = 2048;  // products per merge-path tile
 constexpr int kCpThreads = 256;
 
-// Linear probing (Section 2.2.1) with a compare-and-swap claim of empty slots. A slot's key
+// Linear probing (Section 2.3.1) with a compare-and-swap claim of empty slots. A slot's key
 // only ever changes from empty to its final key, so a stale read can only show "empty"
 // and is then settled by the CAS. The probe sequence is bounded by the table size.
 __device__ __forceinline__ void table_add(u64* __restrict__ keys, double* __restrict__ vals, u64 mask, u64 key,

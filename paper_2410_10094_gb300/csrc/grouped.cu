@@ -1,5 +1,5 @@
 // Per-X-free-group accumulation (Sections 4.1, 4.3): X entries that share a free key form
-// one group; its outputs can never collide with another group's (Section 2.3.2), so each
+// one group; its outputs can never collide with another group's (Section 2.4.2), so each
 // group gets its own probing table, sized from the group's exact bound
 // B_g = sum over its entries of count_Y[contract key], capped by the Y free key space.
 //
@@ -180,7 +180,7 @@ __device__ __forceinline__ u64 y_key(const void* yfk, u64 j) {
 
 // ---- shared-memory tables: buckets of 16 bytes (4 32-bit keys or 2 64-bit keys) probed
 // with one vector load; the first empty slot of the first bucket without the key is
-// claimed with a compare-and-swap (linear probing over buckets, Section 2.2.1).
+// claimed with a compare-and-swap (linear probing over buckets, Section 2.3.1).
 
 template <typename KT>
 struct Bucket;

@@ -1,4 +1,4 @@
-// Input processing on the device: LN keys (Section 2.3.1), grouping of Y by contract key
+// Input processing on the device: LN keys (Section 2.4.1), grouping of Y by contract key
 // with a counting sort (Sections 4.1.1 and 4.2), and the survey of X that finds each
 // entry's Y run and counts the products exactly (Section 4.3).
 #include "launch.h"

@@ -50,7 +50,7 @@ def check_against_dense(p: Problem):
 # ---------------------------------------------------------------------- worked examples
 
 def test_golden_accumulate_example():
-    g = golden("accumulate_sec23.json")
+    g = golden("accumulate_eq34.json")
     X, Y = coo_from_json(g["X"]), coo_from_json(g["Y"])
     res = oracle.contract(X, Y, g["cx"], g["cy"])
     np.testing.assert_array_equal(res.coords, np.asarray(g["expect_coords"], dtype=np.int32))
