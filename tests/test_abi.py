@@ -32,6 +32,50 @@ def test_header_declares_the_boundary():
         assert name in fns
 
 
+def test_header_is_plain_c():
+    """The boundary needs no C++: the header compiles as C99 on its own."""
+    import shutil
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    r = subprocess.run([cc, "-fsyntax-only", "-std=c99", "-Wall", "-Werror", "-x", "c",
+                        os.path.join(ROOT, "include", "stc.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """The ctypes mirrors of the C structs have the C compiler's field offsets and sizes."""
+    import ctypes as C
+    import shutil
+
+    from paper_2410_10094_gb300 import binding as B
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"stc_coo": B.stc_coo, "stc_problem": B.stc_problem, "stc_opts": B.stc_opts,
+               "stc_stats": B.stc_stats, "stc_server_opts": B.stc_server_opts}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "stc.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for row in filter(None, out):
+        name, field, value = row.split()
+        cls = structs[name]
+        got = C.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert got == int(value), f"{name}.{field}: ctypes {got}, C {value}"
+
+
 def test_library_exports_every_declared_symbol(libpath):
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
     exported = set(re.findall(r"\bT (stc_[a-z_0-9]+)$", out, flags=re.M))
