@@ -123,3 +123,11 @@ def test_library_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "stc_oracle" not in txt, f
+
+
+def test_missing_library_fails_loudly():
+    """Without libstc.so the binding raises: there is no CPU fallback."""
+    code = ("import sys; from paper_2410_10094_gb300 import binding as B; B.LIB_PATH = '/nonexistent/libstc.so'\n"
+            "try:\n    B.load()\nexcept ImportError as e:\n    print('raised', e); sys.exit(0)\nsys.exit(1)")
+    r = subprocess.run([__import__("sys").executable, "-c", code], capture_output=True, text=True, cwd=ROOT)
+    assert r.returncode == 0 and "no CPU fallback" in r.stdout, r.stdout + r.stderr
