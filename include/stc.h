@@ -232,14 +232,18 @@ stc_status stc_server_destroy(stc_server* s);
 /* The exact product count of the contraction (Section 4.3: each X entry meets exactly
  * count_Y[its contract key] Y entries) and the device bytes a stc_contract of the same
  * inputs with default options would hold at its peak (scratch + result), for the operand
- * order and contract-key handling AUTO picks. Used to admit work under a budget. */
+ * order and contract-key handling AUTO picks. Used to admit work under a budget.
+ * products, bytes_bound: host, each may be NULL. Returns after its device work completes.
+ * Errors: as stc_contract. */
 stc_status stc_count(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t ncontract,
                      const int32_t* cx, const int32_t* cy, void* stream, uint64_t* products,
                      uint64_t* bytes_bound);
 
 /* LN keys of the listed modes of every entry of T (Section 2.4.1, Fig. 3): the coordinates
  * of modes[0..nmodes) read as digits of one mixed-radix number, modes[0] most significant,
- * each digit's radix its mode length. keys_out: device, [T.nnz]. */
+ * each digit's radix its mode length. keys_out: device, [T.nnz], written. Returns after its
+ * device work completes. Errors: INVALID_ARG (NULL pointers, a mode listed twice or out of
+ * range), KEY_OVERFLOW (the listed lengths multiply past 2^64), COORD_OUT_OF_RANGE, CUDA. */
 stc_status stc_linearize(stc_ctx* ctx, const stc_coo* T, int32_t nmodes, const int32_t* modes,
                          uint64_t* keys_out, void* stream);
 
@@ -247,7 +251,9 @@ stc_status stc_linearize(stc_ctx* ctx, const stc_coo* T, int32_t nmodes, const i
  * scan, scatter. offsets_out: device, [k+1], offsets_out[v] = first slot of key v and
  * offsets_out[k] = n. perm_out: device, [n], perm_out[s] = index of the key placed in
  * slot s; the order inside one key's run is unspecified. keys: device, [n]. Requires
- * n <= STC_MAX_NNZ and k <= 2^26. */
+ * n <= STC_MAX_NNZ and k <= 2^26 (larger k: UNSUPPORTED; renumber with stc_dense_ids first).
+ * Returns after its device work completes. Errors: INVALID_ARG, COORD_OUT_OF_RANGE (a key
+ * >= k), OUT_OF_MEMORY, UNSUPPORTED, CUDA. */
 stc_status stc_group_keys(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint64_t k,
                           uint32_t* offsets_out, uint32_t* perm_out, void* stream);
 
@@ -293,7 +299,7 @@ stc_status stc_result_free(stc_result* r);
 /* A view of a result as an input tensor, for chains of contractions (the output of one
  * feeding the next, as in Section 5.4's motivation): out->coords, vals and shape point into
  * the result (device, device and host memory), valid until stc_result_free(r). Nothing is
- * copied. */
+ * copied. out: host, written. Errors: INVALID_ARG when r or out is NULL. */
 stc_status stc_result_as_coo(const stc_result* r, stc_coo* out);
 
 #ifdef __cplusplus
