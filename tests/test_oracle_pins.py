@@ -222,6 +222,31 @@ def test_swap_symmetry():
     np.testing.assert_array_equal(a.cnt, b.cnt)
 
 
+def test_chain_associativity():
+    """(A (x) B) (x) C equals A (x) (B (x) C) when the pairings do not overlap (Eq. 2 summed in
+    either order): the same structural entries, values within the propagated bound. Pins the
+    oracle for chains, where one call's output is the next call's input."""
+    rng = rng_for(16)
+    A = uniform_coo(rng, (3, 4, 5), 50)
+    B = uniform_coo(rng, (5, 6, 2), 60)
+    C = uniform_coo(rng, (6, 7), 30)
+    ab = oracle.contract(A, B, (2,), (0,))                               # (a0, a1, b1, b2)
+    left = oracle.contract(COO(ab.shape, ab.coords, ab.vals), C, (2,), (0,))  # (a0, a1, b2, c1)
+    bc = oracle.contract(B, C, (1,), (0,))                               # (b0, b2, c1)
+    right = oracle.contract(A, COO(bc.shape, bc.coords, bc.vals), (2,), (0,))  # (a0, a1, b2, c1)
+    np.testing.assert_array_equal(left.coords, right.coords)
+    absd = lambda t: COO(t.shape, t.coords, np.abs(t.vals))
+    ab_abs = oracle.contract(absd(A), absd(B), (2,), (0,))
+    bound = oracle.contract(COO(ab_abs.shape, ab_abs.coords, ab_abs.vals), absd(C), (2,), (0,))
+    np.testing.assert_array_equal(bound.coords, left.coords)
+    assert np.all(np.abs(left.vals - right.vals) <= 4 * REL_TOL * bound.vals)
+    # against the dense definition
+    dense = np.einsum("ijk,klm,ln->ijmn", coo_to_dense(A), coo_to_dense(B), coo_to_dense(C))
+    got = np.zeros_like(dense)
+    got[tuple(left.coords.T)] = left.vals
+    assert np.allclose(got, dense, rtol=0, atol=1e-12 * (1 + np.abs(dense).max()))
+
+
 def test_linearity_split_x():
     rng = rng_for(14)
     X = uniform_coo(rng, (6, 6, 6), 700)
