@@ -65,3 +65,24 @@ def test_reference_arm_declines_multi_problem_workloads():
     assert out.returncode == 0, out.stderr
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and "unavailable" in line
+
+
+def test_key_sample_is_a_sub_contraction():
+    """bench.key_sample keeps whole paired cells: every X and Y entry on a kept cell, no other,
+    so its products are exactly the workload's products on those cells."""
+    import bench
+
+    p = W.plain_large(seed=W.SEED_BASE + 2, nnz=40_000, n=16)
+    sp, desc = bench.key_sample(p, 7)
+    cell = lambda t, modes: [tuple(r) for r in t.coords[:, list(modes)]]
+    kept = set(cell(sp.X, sp.cx)) | set(cell(sp.Y, sp.cy))
+    xs, ys = cell(p.X, p.cx), cell(p.Y, p.cy)
+    assert sp.X.nnz == sum(c in kept for c in xs) and sp.Y.nnz == sum(c in kept for c in ys)
+    from collections import Counter
+
+    cx, cy = Counter(xs), Counter(ys)
+    cxs, cys = Counter(cell(sp.X, sp.cx)), Counter(cell(sp.Y, sp.cy))
+    for c in kept:
+        assert cxs[c] == cx[c] and cys[c] == cy[c]
+    assert 0.05 < len(kept) / len(set(xs) | set(ys)) < 0.3
+    assert bench.key_sample(p, 1)[0] is p
