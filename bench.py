@@ -318,16 +318,12 @@ def serve_bench(args):
     torch.cuda.set_device(0)
     stc.load()
     ctx = stc.default_context(0)
-    rng = W.rng_for(W.SEED_BASE + 5)
-    small = [W.small_pair(rng) for _ in range(96)]
-    large = [W.served_large(rng) for _ in range(12)]
+    small, large, rng = W.served_pools()
     dev = lambda t: (t.shape, torch.from_numpy(t.coords).cuda(), torch.from_numpy(t.vals).cuda())
     dsmall = [(dev(q.X), dev(q.Y), q.cx, q.cy) for q in small]
     dlarge = [(dev(q.X), dev(q.Y), q.cx, q.cy) for q in large]
     R = args.requests
-    is_large = rng.random(R) < 0.2
-    pick = [(dlarge[int(rng.integers(len(dlarge)))] if big else dsmall[int(rng.integers(len(dsmall)))])
-            for big in is_large]
+    pick = [(dlarge if kind == "large" else dsmall)[i] for kind, i in W.served_trace(rng, R, len(small), len(large))]
     prod = {}
 
     def run(trace, plain):

@@ -281,11 +281,13 @@ stc_status stc_dense_ids(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint32_t
  *     STC_ERR_INVALID_ARG with a message naming the limit.
  *   - It runs on the caller's current device. The first call on a device looks up the
  *     array's device address (set-up); make that first call before capturing any stream.
+ *     If the look-up fails the call returns STC_ERR_CUDA and the next call tries again.
  *   - All calls on a device share the one array. The call clears what must start at zero,
  *     but calls whose work overlaps on the GPU (other streams, other host threads) race on
  *     it: serialise them.
- *   - Returns after its device work completes; reports STC_ERR_COORD_OUT_OF_RANGE for a
- *     key >= k, as stc_group_keys does. */
+ *   - Every call copies its status word to the host and waits for its stream before it
+ *     returns; it reports STC_ERR_COORD_OUT_OF_RANGE for a key >= k, as stc_group_keys
+ *     does. */
 stc_status stc_group_keys_static(const uint64_t* keys, int64_t n, uint64_t k, uint32_t* offsets_out,
                                  uint32_t* perm_out, void* stream);
 

@@ -261,9 +261,38 @@ def stc_dense_ids(ctx: int, keys, ids_out, stream=None) -> int:
     return d.value
 
 
+def _check_static_group_args(keys, k: int, offsets_out, perm_out):
+    """The C call cannot see the size, type or device of the arrays it is given: anything
+    short or misplaced would be written past its end on the device. Checked here."""
+    import torch
+
+    for name, t in (("keys", keys), ("offsets_out", offsets_out), ("perm_out", perm_out)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor, not on {t.device}")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on {t.device}, not the current device cuda:{torch.cuda.current_device()}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if keys.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        raise ValueError(f"keys must be int64 or uint64, not {keys.dtype}")
+    for name, t in (("offsets_out", offsets_out), ("perm_out", perm_out)):
+        if t.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+            raise ValueError(f"{name} must be int32 or uint32, not {t.dtype}")
+    if int(k) < 0:
+        raise ValueError("k must be >= 0")
+    if offsets_out.numel() < int(k) + 1:
+        raise ValueError(f"offsets_out holds {offsets_out.numel()} entries; k + 1 = {int(k) + 1} are written")
+    if perm_out.numel() < keys.numel():
+        raise ValueError(f"perm_out holds {perm_out.numel()} entries; n = {keys.numel()} are written")
+
+
 def stc_group_keys_static(keys, k: int, offsets_out, perm_out, stream=None):
     """stc_group_keys without allocation (fixed device scratch; k <= 262144). Runs on the
-    current device; calls that overlap on the GPU race on the shared scratch."""
+    current device; calls that overlap on the GPU race on the shared scratch. The arrays'
+    sizes, types, layout and device are checked before the call (ValueError)."""
+    _check_static_group_args(keys, k, offsets_out, perm_out)
     n = int(keys.numel())
     check(load().stc_group_keys_static(C.c_void_p(keys.data_ptr() if n else 0), n, int(k),
                                        C.c_void_p(offsets_out.data_ptr()),

@@ -27,25 +27,34 @@ static __device__ __align__(256) uint32_t g_group_scratch[kStaticWords];
 constexpr int kMaxDevices = 64;
 
 struct DeviceScratch {
-  std::once_flag once;
+  std::mutex mu;
+  bool ready = false;         // set once the look-up has succeeded
   uint32_t* words = nullptr;  // device address of g_group_scratch on this device
   int sms = 0;
-  cudaError_t err = cudaSuccess;
 };
 
 DeviceScratch g_devices[kMaxDevices];
 
-// Resolves the array's device address for the current device (once per device).
+// Resolves the array's device address for the current device. A successful look-up is kept
+// for the rest of the process; a failed one is not, so the next call on that device tries
+// again.
 cudaError_t scratch_for(int dev, DeviceScratch** out) {
   DeviceScratch& d = g_devices[dev];
-  std::call_once(d.once, [&d, dev]() {
-    void* p = nullptr;
-    d.err = cudaGetSymbolAddress(&p, g_group_scratch);
-    if (d.err == cudaSuccess) d.err = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
-    if (d.err == cudaSuccess) d.words = static_cast<uint32_t*>(p);
-  });
+  std::lock_guard<std::mutex> lk(d.mu);
   *out = &d;
-  return d.err;
+  if (d.ready) return cudaSuccess;
+  void* p = nullptr;
+  int sms = 0;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_group_scratch);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // the failure is reported by this call, not left for a later one
+    return e;
+  }
+  d.words = static_cast<uint32_t*>(p);
+  d.sms = sms;
+  d.ready = true;
+  return cudaSuccess;
 }
 
 }  // namespace

@@ -64,3 +64,44 @@ def test_static_grouping_rejects_oversized_key_range(stc):
     with pytest.raises(stc.StcError) as e:
         stc.stc_group_keys_static(keys, 262_145, off, perm)
     assert e.value.status == 1 and "262144" in str(e.value)
+
+
+def test_static_grouping_allocates_nothing(stc):
+    """After one warm-up call, further calls leave the device's free memory and torch's
+    allocator untouched: the call's scratch is the fixed array, not an allocation."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(20241011))
+    keys = torch.from_numpy(rng.integers(0, 100_000, 300_000).astype(np.int64)).cuda()
+    off = torch.empty(100_001, dtype=torch.int32, device="cuda")
+    perm = torch.empty(keys.numel(), dtype=torch.int32, device="cuda")
+    stc.stc_group_keys_static(keys, 100_000, off, perm)  # warm-up: the address look-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(5):
+        stc.stc_group_keys_static(keys, 100_000, off, perm)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0
+
+
+def test_static_grouping_wrapper_rejects_bad_arrays(stc):
+    """The Python wrapper checks what the C call cannot: sizes, types, layout and device."""
+    import torch
+
+    keys = torch.zeros(10, dtype=torch.int64, device="cuda")
+    off = torch.empty(8, dtype=torch.int32, device="cuda")
+    perm = torch.empty(10, dtype=torch.int32, device="cuda")
+    bad = [
+        (keys, 7, off[:7], perm),                                   # offsets_out shorter than k + 1
+        (keys, 7, off, perm[:9]),                                   # perm_out shorter than n
+        (keys, 7, off.to(torch.int64), perm),                       # wrong offsets type
+        (keys.to(torch.int32), 7, off, perm),                       # wrong key type
+        (keys.cpu(), 7, off, perm),                                 # host keys
+        (torch.zeros(20, dtype=torch.int64, device="cuda")[::2], 7, off, perm),  # strided keys
+    ]
+    for args in bad:
+        with pytest.raises(ValueError):
+            stc.stc_group_keys_static(*args)

@@ -282,3 +282,24 @@ def random_case(rng: np.random.Generator, max_order: int = 4, max_size: int = 6,
     nz_order = (ox - m) + (oy - m)
     out = tuple(int(v) for v in rng.permutation(nz_order)) if rng.random() < 0.5 else None
     return Problem(X, Y, cx, cy, out, name="random_case")
+
+
+def served_pools(seed: int = SEED_BASE + 5, n_small: int = 96, n_large: int = 12):
+    """The distinct problems a served trace draws from: ``n_small`` pairs of the batched mix
+    and ``n_large`` order-4 128^4 pairs with 1e6 entries each contracting two random paired
+    modes (holding 20,000 distinct 1e6-entry pairs at once would take about 190 GB of HBM)."""
+    rng = rng_for(seed)
+    small = [small_pair(rng) for _ in range(n_small)]
+    large = [served_large(rng) for _ in range(n_large)]
+    return small, large, rng
+
+
+def served_trace(rng: np.random.Generator, n_requests: int, n_small: int, n_large: int,
+                 large_fraction: float = 0.2):
+    """``n_requests`` draws from the pools: each request is large with probability
+    ``large_fraction``, then uniform over its pool. Returns a list of ("small"|"large", index)."""
+    is_large = rng.random(n_requests) < large_fraction
+    picks = []
+    for big in is_large:
+        picks.append(("large", int(rng.integers(n_large))) if big else ("small", int(rng.integers(n_small))))
+    return picks
