@@ -39,11 +39,12 @@ typedef enum stc_status {
   STC_ERR_SHAPE_MISMATCH = 2,     /* paired modes have different lengths (Section 2.2) */
   STC_ERR_KEY_OVERFLOW = 3,       /* a key space (product of mode lengths) needs > 64 bits */
   STC_ERR_OUT_OF_MEMORY = 4,      /* device allocation failed or the context budget is exceeded */
-  STC_ERR_TABLE_FULL = 5,         /* an accumulation table overflowed (internal; never expected) */
+  STC_ERR_TABLE_FULL = 5,         /* an accumulation table overflowed (internal: retried, see stc_opts) */
   STC_ERR_TIMEOUT = 6,            /* a bounded wait gave up */
   STC_ERR_CUDA = 7,               /* a CUDA runtime call failed; see stc_last_error() */
   STC_ERR_COORD_OUT_OF_RANGE = 8, /* an input coordinate is negative or >= its mode length */
-  STC_ERR_UNSUPPORTED = 9         /* valid input outside what the library implements */
+  STC_ERR_UNSUPPORTED = 9,        /* valid input outside what the library implements */
+  STC_ERR_CANCELLED = 10          /* a queued server request was cancelled (stc_server_cancel) */
 } stc_status;
 
 #define STC_MAX_ORDER 8            /* modes per input tensor */
@@ -105,7 +106,12 @@ typedef struct stc_opts {
   int32_t accumulator;    /* STC_ACC_*; 0 = AUTO */
   int32_t contract_ids;   /* STC_IDS_*; 0 = AUTO */
   int32_t operands;       /* STC_OPERANDS_*; 0 = AUTO */
-  int32_t reserved_;      /* set to 0 */
+  int32_t table_shrink;   /* fault injection, normally 0: the first attempt of the one-global-table
+                             strategy divides its table's capacity (sized from the exact product
+                             count, Section 4.3) by 2^table_shrink (0..30). A table too small for
+                             the distinct output keys overflows; the call sees the overflow
+                             (STC_ERR_TABLE_FULL inside the call), discards that attempt and runs
+                             the expansion again with the full capacity; stats.retries counts it. */
 } stc_opts;
 
 /* Per-call statistics of a finished contraction. */
@@ -124,7 +130,7 @@ typedef struct stc_stats {
   uint64_t contract_ids;  /* distinct contract keys of Y when the contract keys were renumbered
                              to dense ids (STC_IDS_DENSE), else 0 */
   int32_t swapped;        /* 1 when the operands were swapped (STC_OPERANDS_*) */
-  int32_t reserved_;
+  int32_t retries;        /* expansions run again after a table overflowed (see stc_opts.table_shrink) */
 } stc_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -225,6 +231,12 @@ stc_status stc_server_poll(stc_server* s, uint64_t ticket, int32_t* done);
  * request is still running (the ticket stays valid); otherwise the ticket is consumed and the
  * request's own status is returned. */
 stc_status stc_server_wait(stc_server* s, uint64_t ticket, int64_t timeout_ms, stc_result** out, double* times);
+
+/* Cancel a request that is still queued: it is taken off the queue and never runs, and its
+ * wait returns STC_ERR_CANCELLED (consuming the ticket). cancelled receives 1 when the request
+ * was taken off the queue, 0 when it had already been taken by a worker (it then finishes
+ * normally) or had finished. Errors: INVALID_ARG (NULL server or cancelled, unknown ticket). */
+stc_status stc_server_cancel(stc_server* s, uint64_t ticket, int32_t* cancelled);
 
 /* Finish every queued request, stop the workers, free uncollected results, destroy. */
 stc_status stc_server_destroy(stc_server* s);

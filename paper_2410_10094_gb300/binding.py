@@ -15,7 +15,7 @@ STC_OK = 0
 STATUS_NAMES = {
     0: "STC_OK", 1: "STC_ERR_INVALID_ARG", 2: "STC_ERR_SHAPE_MISMATCH", 3: "STC_ERR_KEY_OVERFLOW",
     4: "STC_ERR_OUT_OF_MEMORY", 5: "STC_ERR_TABLE_FULL", 6: "STC_ERR_TIMEOUT", 7: "STC_ERR_CUDA",
-    8: "STC_ERR_COORD_OUT_OF_RANGE", 9: "STC_ERR_UNSUPPORTED",
+    8: "STC_ERR_COORD_OUT_OF_RANGE", 9: "STC_ERR_UNSUPPORTED", 10: "STC_ERR_CANCELLED",
 }
 STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_GROUPED = 0, 1, 2
 ACC_AUTO, ACC_HASH, ACC_DENSE, ACC_HASH_SCAN = 0, 1, 2, 3
@@ -48,7 +48,7 @@ class stc_server_opts(C.Structure):
 class stc_opts(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double),
                 ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("contract_ids", C.c_int32),
-                ("operands", C.c_int32), ("reserved_", C.c_int32)]
+                ("operands", C.c_int32), ("table_shrink", C.c_int32)]
 
 
 class stc_stats(C.Structure):
@@ -56,7 +56,7 @@ class stc_stats(C.Structure):
                 ("table_slots", C.c_uint64), ("groups", C.c_uint64), ("strategy", C.c_int32),
                 ("nstages", C.c_int32), ("launches", C.c_uint32), ("accumulator", C.c_int32),
                 ("stage_ms", C.c_float * 8), ("contract_ids", C.c_uint64), ("swapped", C.c_int32),
-                ("reserved_", C.c_int32)]
+                ("retries", C.c_int32)]
 
 
 EXPORTS = {
@@ -74,6 +74,7 @@ EXPORTS = {
     "stc_server_poll": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_int32)], C.c_int),
     "stc_server_wait": ([C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(C.c_void_p), C.POINTER(C.c_double)], C.c_int),
     "stc_server_destroy": ([C.c_void_p], C.c_int),
+    "stc_server_cancel": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_int32)], C.c_int),
     "stc_count": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
                    C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
     "stc_linearize": ([C.c_void_p, C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -355,6 +356,10 @@ class Context:
         self.device = device
         self.handle = stc_create(device, mem_budget_bytes)
 
+    def stats(self):
+        """(device bytes the context holds now, live results)."""
+        return stc_ctx_stats(self.handle)
+
     def close(self):
         if self.handle:
             stc_destroy(self.handle)
@@ -386,6 +391,7 @@ class Stats:
     stage_ms: tuple
     contract_ids: int = 0
     swapped: int = 0
+    retries: int = 0
 
 
 class Result:
@@ -400,7 +406,7 @@ class Result:
         st = stc_result_stats(handle)
         self.stats = Stats(st.products, st.survivors, st.out_capacity, st.table_slots, st.groups, st.strategy,
                            st.launches, st.accumulator, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))),
-                           st.contract_ids, st.swapped)
+                           st.contract_ids, st.swapped, st.retries)
         self._coords = self._vals = None
 
     @property
@@ -439,12 +445,13 @@ class Result:
 def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, strategy: int = STRATEGY_AUTO,
              load_factor: float = 0.0, group_load_factor: float = 0.0, accumulator: int = ACC_AUTO,
              contract_ids: int = IDS_AUTO, operands: int = OPERANDS_AUTO, record_times: bool = False,
-             stream=None, ctx: Context = None) -> Result:
+             table_shrink: int = 0, stream=None, ctx: Context = None) -> Result:
     """Z = X (x) Y (Eq. 2) on the GPU. X and Y are (shape, coords, vals) with coords a CUDA
-    int32 [nnz, order] tensor and vals a CUDA float64 [nnz] tensor."""
+    int32 [nnz, order] tensor and vals a CUDA float64 [nnz] tensor. ``table_shrink`` is the
+    fault-injection knob of stc_opts (an undersized first table, retried inside the call)."""
     ctx = ctx or default_context()
     o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor), float(group_load_factor),
-                 int(accumulator), int(contract_ids), int(operands), 0)
+                 int(accumulator), int(contract_ids), int(operands), int(table_shrink))
     return Result(stc_contract(ctx.handle, X, Y, cx, cy, out_order, o, stream))
 
 
@@ -484,6 +491,13 @@ class Server:
         check(load().stc_server_submit(C.c_void_p(self.handle), C.byref(req), C.byref(t)))
         self._inputs[t.value] = (X, Y)
         return t.value
+
+    def cancel(self, ticket: int) -> bool:
+        """Take a still-queued request off the queue (its wait then raises STC_ERR_CANCELLED);
+        False when a worker had already taken it."""
+        c = C.c_int32()
+        check(load().stc_server_cancel(C.c_void_p(self.handle), ticket, C.byref(c)))
+        return bool(c.value)
 
     def poll(self, ticket: int) -> bool:
         d = C.c_int32()

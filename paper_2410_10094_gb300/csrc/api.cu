@@ -861,6 +861,7 @@ const char* stc_status_string(stc_status s) {
     case STC_ERR_CUDA: return "CUDA error";
     case STC_ERR_COORD_OUT_OF_RANGE: return "coordinate out of range";
     case STC_ERR_UNSUPPORTED: return "unsupported";
+    case STC_ERR_CANCELLED: return "cancelled";
   }
   return "unknown status";
 }
@@ -934,6 +935,8 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
     return fail(STC_ERR_INVALID_ARG, "unknown contract_ids %d", o.contract_ids);
   if (o.operands < 0 || o.operands > STC_OPERANDS_SWAPPED)
     return fail(STC_ERR_INVALID_ARG, "unknown operands %d", o.operands);
+  if (o.table_shrink < 0 || o.table_shrink > 30)
+    return fail(STC_ERR_INVALID_ARG, "table_shrink %d outside 0..30", o.table_shrink);
   if (o.operands == STC_OPERANDS_SWAPPED ||
       (o.operands == STC_OPERANDS_AUTO && (uint64_t)Y->nnz > 4 * (uint64_t)X->nnz)) {
     // Y (x) X has output modes (Y free, X free); map each requested mode onto that order.
@@ -1014,6 +1017,8 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
     const uint64_t target = std::min<uint64_t>(h.P, pl.F);
     const uint64_t cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)((double)target / alpha) + 1));
     const uint64_t out_cap = std::min(target, cap);
+    // Fault injection (stc_opts.table_shrink): the first attempt uses a smaller table.
+    const uint64_t first_cap = std::max<uint64_t>(64, o.table_shrink > 0 ? cap >> o.table_shrink : cap);
     GlobalTable t{};
     u64* wpre = nullptr;
     u64* wscr = nullptr;
@@ -1021,26 +1026,37 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
     auto run = [&]() -> stc_status {
       STC_TRY(ar.alloc(&t.keys, cap));
       STC_TRY(ar.alloc(&t.vals, cap));
-      t.mask = cap - 1;
       STC_TRY(ar.alloc(&wpre, (size_t)h.ns + 1));
       STC_TRY(ar.alloc(&wscr, (size_t)scan_scratch_elems((int64_t)h.ns)));
       STC_TRY(ar.alloc(&r->coords, out_cap * (size_t)pl.oz));
       STC_TRY(ar.alloc(&r->vals, out_cap));
-      STC_CUDA(cudaMemsetAsync(t.keys, 0xff, cap * sizeof(u64), s));
-      STC_CUDA(cudaMemsetAsync(t.vals, 0, cap * sizeof(double), s));
       STC_CUDA(scan_u32_u64(pr.sv.w, wpre, (int64_t)h.ns, wscr, s));
       tm.mark(3);
-      STC_CUDA(launch_expand_global(wpre, (int64_t)h.ns, h.P, pr.sv, static_cast<const u64*>(pr.yfk), pr.yv, pl.FY,
-                                    t, &pr.ctr->status,
-                                    ctx->sms, s));
-      tm.mark(4);
-      STC_CUDA(launch_compact_global(t, pl.op, r->coords, r->vals, out_cap, &pr.ctr->nz, &pr.ctr->status, ctx->sms,
-                                     s));
-      tm.mark(5);
-      Counters h2{};
-      STC_TRY(read_counters(pr, s, h2));
-      r->nnz = (int64_t)h2.nz;
-      return STC_OK;
+      for (uint64_t c = first_cap;; c = cap) {
+        t.mask = c - 1;
+        STC_CUDA(cudaMemsetAsync(t.keys, 0xff, c * sizeof(u64), s));
+        STC_CUDA(cudaMemsetAsync(t.vals, 0, c * sizeof(double), s));
+        STC_CUDA(launch_expand_global(wpre, (int64_t)h.ns, h.P, pr.sv, static_cast<const u64*>(pr.yfk), pr.yv,
+                                      pl.FY, t, &pr.ctr->status, ctx->sms, s));
+        tm.mark(4);
+        STC_CUDA(launch_compact_global(t, pl.op, r->coords, r->vals, out_cap, &pr.ctr->nz, &pr.ctr->status,
+                                       ctx->sms, s));
+        tm.mark(5);
+        Counters h2{};
+        STC_CUDA(cudaMemcpyAsync(&h2, pr.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        STC_CUDA(cudaStreamSynchronize(s));
+        // A table that overflowed lost products: run the expansion again at full capacity
+        // (the compaction wrote at most out_cap entries, all of them overwritten now).
+        if (h2.status == kStatTableFull && c < cap) {
+          STC_CUDA(cudaMemsetAsync(&pr.ctr->nz, 0, sizeof(u64), s));
+          STC_CUDA(cudaMemsetAsync(&pr.ctr->status, 0, sizeof(uint32_t), s));
+          r->stats.retries++;
+          continue;
+        }
+        STC_TRY(status_word(h2.status));
+        r->nnz = (int64_t)h2.nz;
+        return STC_OK;
+      }
     };
     st = run();
     if (st != STC_OK) {

@@ -295,6 +295,31 @@ stc_status stc_server_wait(stc_server* sv, uint64_t ticket, int64_t timeout_ms, 
   return STC_OK;
 }
 
+stc_status stc_server_cancel(stc_server* sv, uint64_t ticket, int32_t* cancelled) {
+  if (!sv || !cancelled) return report_error(STC_ERR_INVALID_ARG, "NULL argument");
+  *cancelled = 0;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return report_error(STC_ERR_INVALID_ARG, "unknown ticket");
+    Ticket& t = it->second;
+    if (t.done) return STC_OK;
+    // Only a request no worker has taken is still in the queue (it holds no reservation yet).
+    for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q) {
+      if (*q != ticket) continue;
+      sv->queue.erase(q);
+      t.done = true;
+      t.status = STC_ERR_CANCELLED;
+      t.error = "the request was cancelled before it ran";
+      t.t_start = t.t_done = sv->now();
+      *cancelled = 1;
+      break;
+    }
+  }
+  if (*cancelled) sv->cv_done.notify_all();
+  return STC_OK;
+}
+
 stc_status stc_server_destroy(stc_server* sv) {
   if (!sv) return STC_OK;
   {
