@@ -193,10 +193,65 @@ def dist_env():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
-# kernel, from an ncu capture of the current kernels with the default strategy and
-# accumulator; workloads without a capture report null.
-NCU_TRAFFIC = {"plain_large": ("group_stream_kernel", 2.876e9 + 9.198e9),
-               "imbalanced": ("x_survey_kernel", 0.2746e9 + 0.0075e9)}
+# kernel, from ncu captures summarised in profiles/ncu_traffic.json. Each entry names the
+# sources that define the kernel and their SHA-256 at capture time: a kernel changed since its
+# capture reports null.
+KERNEL_SOURCES = {"group_stream_kernel": ["grouped.cu", "common.cuh", "launch.h"],
+                  "x_survey_bulk_kernel": ["prep.cu", "common.cuh", "launch.h"],
+                  "x_survey_kernel": ["prep.cu", "common.cuh", "launch.h"]}
+
+
+def source_sha(kernel):
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(kernel, []):
+        with open(os.path.join(ROOT, "paper_2410_10094_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(workload):
+    """(kernel, bytes per launch) of the workload's capture when it matches today's sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            entry = json.load(f).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not entry or entry.get("source_sha") != source_sha(entry["kernel"]):
+        return None
+    return entry["kernel"], float(entry["bytes_per_launch"])
+
+
+def record_traffic(workload, kernel, csv_path):
+    """Adds one capture to profiles/ncu_traffic.json: the mean dram__bytes_read.sum +
+    dram__bytes_write.sum per launch of `kernel` in an ncu --csv log, with today's source hash."""
+    import csv
+
+    per = {}
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(ln for ln in f if ln.startswith('"'))]
+    head = rows[0]
+    ki, mi, vi, ii = head.index("Kernel Name"), head.index("Metric Name"), head.index("Metric Value"), head.index("ID")
+    for r in rows[1:]:
+        if kernel in r[ki] and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            unit = r[head.index("Metric Unit")] if "Metric Unit" in head else "byte"
+            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(unit, 1)
+            per[r[ii]] = per.get(r[ii], 0.0) + float(r[vi].replace(",", "")) * scale
+    if not per:
+        raise SystemExit(f"no DRAM counters of {kernel} in {csv_path}")
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    data[workload] = {"kernel": kernel, "bytes_per_launch": sum(per.values()) / len(per), "launches": len(per),
+                      "source_sha": source_sha(kernel), "capture": os.path.basename(csv_path)}
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    print(json.dumps(data[workload]))
+    return 0
 
 
 def l2_note(bytes_in, bytes_out, l2=129e6):
@@ -247,6 +302,46 @@ def run_oracle_sample(p, workload, m=1):
     return r.products, dt, desc
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_parallel(p, workload, m, threads):
+    """The unchanged oracle on key_sample(p, m) split into `threads` independent parts that run
+    at once on the host's cores (threads: ctypes releases the GIL during each call). X is split
+    by ranges of its first free coordinate: outputs of different X free tuples never collide, so
+    the parts are sub-contractions of their own (each part indexes all of the sample's Y).
+    Batches: the first 48 // m pairs, one per task."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+
+    if workload == "batched":
+        n = max(1, 48 // max(m, 1))
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(threads) as ex:
+            prods = sum(ex.map(lambda q: oracle.contract(q.X, q.Y, q.cx, q.cy).products, p[:n]))
+        return prods, time.perf_counter() - t0, f"the first {n} of the 2,048 pairs, {threads} at a time"
+    sp, desc = key_sample(p, m)
+    xfree = [j for j in range(sp.X.order) if j not in set(sp.cx)]
+    if xfree and sp.out_order is None and threads > 1:
+        first = sp.X.coords[:, xfree[0]]
+        order = np.argsort(first, kind="stable")
+        cuts = np.searchsorted(first[order], np.quantile(first, np.linspace(0, 1, threads + 1)[1:-1]), side="left")
+        parts = [np.sort(c) for c in np.split(order, cuts) if c.size]
+    else:
+        parts = [np.arange(sp.X.nnz)]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(len(parts)) as ex:
+        prods = sum(ex.map(lambda rows: oracle.contract(sp.X.take(rows), sp.Y, sp.cx, sp.cy, sp.out_order).products,
+                           parts))
+    dt = time.perf_counter() - t0
+    return prods, dt, desc + f", X split by its first free coordinate into {len(parts)} parts run at once"
+
+
 REF_SECONDS = 120.0  # the reference arm's whole run (warm-up and timed steps) on the host
 CPU_SECONDS = 15.0   # the one timed oracle call of cpu_baseline
 
@@ -286,12 +381,15 @@ def reference_arm(args):
     p = WORKLOADS[args.workload](SEEDS[args.workload])
     # Each step is the sub-contraction over 1/m of the paired cells, m chosen so that warm-up
     # and timed steps together take about REF_SECONDS.
+    # On all the host's cores: each step the oracle on T independent parts of the sample one
+    # core would finish in REF_SECONDS / (steps + warm-up).
+    T = host_cores()
     m = sample_fraction(p, args.workload, REF_SECONDS / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        run_oracle_sample(p, args.workload, m)
+        run_oracle_parallel(p, args.workload, m, T)
     prods, times, desc = 0, [], ""
     for _ in range(args.steps):
-        pr, dt, desc = run_oracle_sample(p, args.workload, m)
+        pr, dt, desc = run_oracle_parallel(p, args.workload, m, T)
         prods += pr
         times.append(dt)
     total = sum(times)
@@ -301,7 +399,7 @@ def reference_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {DESCRIPTIONS[args.workload]}", "sample": desc},
-        "cpu_baseline": {"value": value, "unit": "products/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "products/s", "cores": T, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -475,7 +573,11 @@ def main(argv=None):
     ap.add_argument("--requests", type=int, default=1000, help="served workload: requests per arrival rate")
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 0.9, 1.2],
                     help="served workload: arrival rates as multiples of the one-at-a-time service rate")
+    ap.add_argument("--record-traffic", nargs=2, metavar=("KERNEL", "NCU_CSV"),
+                    help="store the DRAM bytes per launch of KERNEL from an ncu --csv log for --workload")
     args = ap.parse_args(argv)
+    if args.record_traffic:
+        return record_traffic(args.workload, *args.record_traffic)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -522,9 +624,15 @@ def main(argv=None):
                                       sum(r.stats.out_capacity for r in rs),
                                       0, 0, st.strategy, st.launches, st.accumulator, st.stage_ms)
 
+        # The timed steps replay one captured graph per step (a prepared batch whose first runs
+        # tune the load factor and capture); the per-stage pass runs ordinary batches.
+        plan = stc.BatchPlan(prepared, group_load_factor=args.group_load_factor, ctx=ctx)
+
         def step(record=False):
-            return _Agg(stc.contract_batch(prepared, group_load_factor=args.group_load_factor, record_times=record,
-                                           stream=stream, ctx=ctx))
+            if record:
+                return _Agg(stc.contract_batch(prepared, group_load_factor=args.group_load_factor, record_times=True,
+                                               stream=stream, ctx=ctx))
+            return _Agg(plan.run(stream=stream))
     else:
         X, Y = dev(p.X), dev(p.Y)
 
@@ -533,7 +641,7 @@ def main(argv=None):
                                 group_load_factor=args.group_load_factor, accumulator=args.accumulator,
                                 contract_ids=args.contract_ids, operands=args.operands, stream=stream, ctx=ctx)
 
-    for _ in range(args.warmup):
+    for _ in range(max(args.warmup, 4) if args.workload == "batched" else args.warmup):
         r = step()
         nz, oz, P, launches, ns = r.nnz, r.order, r.stats.products, r.stats.launches, r.stats.survivors
         cids, swp = r.stats.contract_ids, r.stats.swapped
@@ -558,6 +666,7 @@ def main(argv=None):
     clk.mark(tw0, time.time())
     barrier()
     ms, total_products = reduce_over_ranks(ev0.elapsed_time(ev1), float(P), world, "cuda")
+    plan_stats = plan.stats() if args.workload == "batched" else None
     value = total_products * args.steps / (ms / 1e3)
 
     # ---- per-stage times: K more steps with the library's stage events on (they wait for
@@ -647,19 +756,36 @@ def main(argv=None):
     achieved = kernel_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
     step_ms = ms / args.steps
     default_opts = args.strategy == 0 and args.accumulator == 0 and args.contract_ids == 0 and args.operands == 0
-    traffic = NCU_TRAFFIC.get(args.workload) if default_opts else None
+    traffic = ncu_traffic(args.workload) if default_opts else None
     roofline = {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic[1] if traffic else None,
                 "traffic_kernel": traffic[0] if traffic else None, "peak_kind": peak_kind,
                 "kernel_ms": dom_ms, "alg_bytes": kernel_bytes}
+    if args.workload == "imbalanced_both":
+        # Products fall on at most 262,144 outputs: the one-global-table expansion issues one FP64
+        # multiply and one FP64 atomic add in L2 per product, so its bounds are those two rates,
+        # measured here (stc_measure_peaks), not HBM bandwidth.
+        dmul, atom = stc.measure_peaks(torch.cuda.current_device())
+        acc_ms = float(per_step[4])
+        rate = P / (acc_ms / 1e3) if acc_ms > 0 else None
+        roofline = {"bound": "l2_atomic", "kernel": "accumulate", "achieved": rate and rate / 1e9,
+                    "peak": atom / 1e9, "unit": "G products/s (one L2 FP64 atomic add each)",
+                    "frac": rate and rate / atom, "traffic": None, "peak_kind": "measured in this run",
+                    "kernel_ms": acc_ms, "dmul_peak": dmul / 1e9, "dmul_frac": rate and rate / dmul,
+                    "hbm": roofline}
     step_alg = alg_bytes(p, nz, oz)
 
     cpu = None
     if not args.no_cpu_baseline:
+        # The oracle as it stands on all the host's cores (independent parts at once), beside
+        # one core, on the same sample (sized for about CPU_SECONDS on one core).
         m = sample_fraction(workload_problem, args.workload, CPU_SECONDS) if args.workload != "batched" else 1
         prods, dt, desc = run_oracle_sample(workload_problem, args.workload, m)
-        cpu = {"value": prods / dt, "unit": "products/s", "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": dt}
+        T = host_cores()
+        pprods, pdt, pdesc = run_oracle_parallel(workload_problem, args.workload, m, T)
+        cpu = {"value": pprods / pdt, "unit": "products/s", "cores": T, "kind": "oracle", "sample": pdesc,
+               "seconds": pdt,
+               "single_core": {"value": prods / dt, "cores": 1, "sample": desc, "seconds": dt}}
 
     line = {
         "metric": "products/s", "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
@@ -676,6 +802,8 @@ def main(argv=None):
         "stage_ms": {n: float(per_step[i]) for i, n in enumerate(stage_names)},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches) * args.steps,
         "sequential_calls": sequential,
+        "batch_plan": ({"runs": plan_stats[0], "graph_replays": plan_stats[1], "group_load_factor": plan_stats[2]}
+                       if plan_stats else None),
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

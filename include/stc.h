@@ -195,14 +195,42 @@ typedef struct stc_problem {
 stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* problems, const stc_opts* opts,
                               void* stream, stc_result** outs);
 
+/* A prepared batch: the problems of stc_contract_batch held by the library across runs, for a
+ * batch run again and again on the same device arrays (their contents may change between
+ * runs; the arrays themselves, shapes and mode lists may not). The plan keeps the problems'
+ * descriptors and every scratch array on the device. Its first runs are ordinary batches
+ * (with stc_opts.group_load_factor 0 they also let the context's autotuner time each
+ * candidate load factor for the batch's size bucket); once the load factor is settled the
+ * whole launch sequence of one run (grouping of Y, survey and grouping of X, binning,
+ * placement of every problem's output from its exact bound, accumulation) is captured in one
+ * CUDA graph, and every later run replays it: one output allocation of the previous run's
+ * exact size, one graph launch, one wait. A run whose outputs outgrow that size is run again
+ * the ordinary way (and captured anew). Runs of one plan must not overlap.
+ *   stc_batch_plan_create: n >= 1 problems (host arrays copied, device arrays borrowed for
+ *     the plan's lifetime); opts as stc_contract_batch.
+ *   stc_batch_plan_run: outs host [n], one result per problem, sharing one device block as
+ *     stc_contract_batch's do; returns after the run's device work completes.
+ *   stc_batch_plan_stats: runs so far, runs that replayed the graph, and the load factor the
+ *     graph was captured with (0 before a capture); each pointer may be NULL.
+ * Errors: as stc_contract_batch; INVALID_ARG for NULL arguments or n < 1. */
+typedef struct stc_batch_plan stc_batch_plan;
+stc_status stc_batch_plan_create(stc_ctx* ctx, int32_t n, const stc_problem* problems, const stc_opts* opts,
+                                 stc_batch_plan** out);
+stc_status stc_batch_plan_run(stc_batch_plan* plan, void* stream, stc_result** outs);
+stc_status stc_batch_plan_stats(const stc_batch_plan* plan, int64_t* runs, int64_t* graph_runs,
+                                double* group_load_factor);
+stc_status stc_batch_plan_destroy(stc_batch_plan* plan);
+
 /* ---------------------------------------------------------------- serving
  * A server takes contraction requests as they arrive and runs them on worker threads, each
- * with its own CUDA stream. Each request is admitted by its exact device-memory bound
- * (computed from the product count of Section 4.3 at submission) against the server's
- * budget; queued requests that fit are run together as one stc_contract_batch by the next
- * free worker, so requests that arrive while others run join the next batch and batches of
- * different workers overlap on the device (continuous batching). With `plain` set, one
- * worker runs one request at a time with stc_contract: the one-at-a-time baseline. */
+ * with its own CUDA stream. Counting threads (one per worker, each on a stream of its own)
+ * compute each request's exact device-memory bound (from the product count of Section 4.3),
+ * taking requests in arrival order;
+ * the request is then admitted against the server's budget: queued requests that fit are run
+ * together as one stc_contract_batch by the next free worker, so requests that arrive while
+ * others run join the next batch and batches of different workers overlap on the device
+ * (continuous batching). With `plain` set, one worker runs one request at a time with
+ * stc_contract: the one-at-a-time baseline. */
 typedef struct stc_server stc_server;
 
 typedef struct stc_server_opts {
@@ -217,8 +245,10 @@ typedef struct stc_server_opts {
 stc_status stc_server_create(stc_ctx* ctx, const stc_server_opts* opts, stc_server** out);
 
 /* Queue a request. Its device arrays must stay valid and unchanged until the request is
- * finished; its host arrays (shapes, mode lists) are copied. Runs the counting pass that
- * sizes the request before returning. ticket receives the request's id. */
+ * finished (its wait has returned); its host arrays (shapes, mode lists) are copied. Returns
+ * at once: the counting pass that sizes the request runs on one of the server's counting threads, and
+ * an error it finds (a bad argument, a coordinate out of range) is the request's status at
+ * its wait. ticket receives the request's id. */
 stc_status stc_server_submit(stc_server* s, const stc_problem* request, uint64_t* ticket);
 
 /* done receives 1 when the request has finished (successfully or not), else 0. */
@@ -232,10 +262,11 @@ stc_status stc_server_poll(stc_server* s, uint64_t ticket, int32_t* done);
  * request's own status is returned. */
 stc_status stc_server_wait(stc_server* s, uint64_t ticket, int64_t timeout_ms, stc_result** out, double* times);
 
-/* Cancel a request that is still queued: it is taken off the queue and never runs, and its
- * wait returns STC_ERR_CANCELLED (consuming the ticket). cancelled receives 1 when the request
- * was taken off the queue, 0 when it had already been taken by a worker (it then finishes
- * normally) or had finished. Errors: INVALID_ARG (NULL server or cancelled, unknown ticket). */
+/* Cancel a request that no worker has taken yet: it never runs, and its wait returns
+ * STC_ERR_CANCELLED (consuming the ticket; if its counting pass was running, the wait returns
+ * once that pass has finished with the request's arrays). cancelled receives 1 when the
+ * request was cancelled, 0 when a worker had already taken it (it then finishes normally) or
+ * it had finished. Errors: INVALID_ARG (NULL server or cancelled, unknown ticket). */
 stc_status stc_server_cancel(stc_server* s, uint64_t ticket, int32_t* cancelled);
 
 /* Finish every queued request, stop the workers, free uncollected results, destroy. */
@@ -302,6 +333,18 @@ stc_status stc_dense_ids(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint32_t
  *     does. */
 stc_status stc_group_keys_static(const uint64_t* keys, int64_t n, uint64_t k, uint32_t* offsets_out,
                                  uint32_t* perm_out, void* stream);
+
+/* Measured peak rates of the device's FP64 multiply pipe and of FP64 atomic adds resolved in
+ * L2 (measurement support; the paper has no counterpart: its CPU program has no such limits to
+ * report). Contractions whose products mostly fall on few outputs (both operands' contract
+ * keys skewed) are bound by these rather than by memory bandwidth.
+ *   dmul_per_s: rounded FP64 multiplies per second, from independent multiply chains filling
+ *     every SM; l2_atomic_per_s: FP64 atomicAdd per second to hashed slots of an 8 MB array
+ *     (resident in L2). Either may be NULL. Each is timed with CUDA events after one warm-up
+ *     launch, on a private stream of `device`; the call takes tens of milliseconds and
+ *     restores the calling thread's current device.
+ * Errors: INVALID_ARG (both NULL, bad device), CUDA. */
+stc_status stc_measure_peaks(int device, double* dmul_per_s, double* l2_atomic_per_s);
 
 /* Result accessors. Coordinates are device int32 [nnz][order] row-major, values device
  * double [nnz]; both stay valid until stc_result_free(). shape is host, [order]. */

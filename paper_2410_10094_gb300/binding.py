@@ -75,6 +75,13 @@ EXPORTS = {
     "stc_server_wait": ([C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(C.c_void_p), C.POINTER(C.c_double)], C.c_int),
     "stc_server_destroy": ([C.c_void_p], C.c_int),
     "stc_server_cancel": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_int32)], C.c_int),
+    "stc_batch_plan_create": ([C.c_void_p, C.c_int32, C.POINTER(stc_problem), C.POINTER(stc_opts),
+                               C.POINTER(C.c_void_p)], C.c_int),
+    "stc_batch_plan_run": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "stc_batch_plan_stats": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+                             C.c_int),
+    "stc_batch_plan_destroy": ([C.c_void_p], C.c_int),
+    "stc_measure_peaks": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "stc_count": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
                    C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
     "stc_linearize": ([C.c_void_p, C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -466,6 +473,47 @@ def contract_batch(problems, *, group_load_factor: float = 0.0, record_times: bo
     return [Result(h) for h in stc_contract_batch(ctx.handle, bp, o, stream)]
 
 
+class BatchPlan:
+    """A prepared batch (stc_batch_plan_*): the problems held by the library across runs; once
+    the group load factor is settled each run replays one captured CUDA graph. problems: a
+    BatchProblems or a sequence of (X, Y, cx, cy[, out_order]); their device tensors must stay
+    alive (kept here) for the plan's lifetime."""
+
+    def __init__(self, problems, *, group_load_factor: float = 0.0, record_times: bool = False,
+                 ctx: Context = None):
+        self.ctx = ctx or default_context()
+        self.problems = problems if isinstance(problems, BatchProblems) else BatchProblems(problems)
+        o = stc_opts(STRATEGY_GROUPED, 1 if record_times else 0, 0.0, float(group_load_factor), ACC_HASH, 0, 0, 0)
+        h = C.c_void_p()
+        check(load().stc_batch_plan_create(C.c_void_p(self.ctx.handle), self.problems.n, self.problems.arr,
+                                           C.byref(o), C.byref(h)))
+        self.handle = h.value
+        self.n = self.problems.n
+
+    def run(self, stream=None):
+        """One run: one Result per problem."""
+        outs = (C.c_void_p * max(self.n, 1))()
+        check(load().stc_batch_plan_run(C.c_void_p(self.handle), C.c_void_p(_stream_handle(stream)), outs))
+        return [Result(outs[i]) for i in range(self.n)]
+
+    def stats(self):
+        """(runs, runs that replayed the captured graph, load factor of the graph or 0)."""
+        r, g, a = C.c_int64(), C.c_int64(), C.c_double()
+        check(load().stc_batch_plan_stats(C.c_void_p(self.handle), C.byref(r), C.byref(g), C.byref(a)))
+        return int(r.value), int(g.value), float(a.value)
+
+    def close(self):
+        if self.handle:
+            check(load().stc_batch_plan_destroy(C.c_void_p(self.handle)))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Server:
     """The contraction server (stc_server_*). submit() takes (X, Y, cx, cy[, out_order]) with
     CUDA tensors (kept alive here until the request finishes) and returns a ticket;
@@ -518,6 +566,13 @@ class Server:
             check(load().stc_server_destroy(C.c_void_p(self.handle)))
             self.handle = 0
             self._inputs.clear()
+
+
+def measure_peaks(device: int = 0):
+    """(FP64 multiplies per second, L2 FP64 atomic adds per second) measured on the device."""
+    d, a = C.c_double(), C.c_double()
+    check(load().stc_measure_peaks(int(device), C.byref(d), C.byref(a)))
+    return float(d.value), float(a.value)
 
 
 def count(X, Y, cx, cy, *, stream=None, ctx: Context = None):

@@ -659,6 +659,7 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   const uint64_t out_cap = hg.out_cap;
   HugeGroups hh{};
   hh.count = hg.count[kMaxClasses];
+  hh.countp = gc->count + kMaxClasses;
   hh.list = b.huge_list;
   hh.off = b.huge_off;
   hh.cap = b.huge_cap;
@@ -846,6 +847,472 @@ void result_release_on_default_stream(stc_result* r) {
   if (r->mem) r->mem->stream = nullptr;
 }
 }  // namespace stc
+
+namespace {
+
+// ---------------------------------------------------------------- batches
+// The device state of one batch of problems: descriptors and every scratch array, all sized
+// from totals the host knows before any kernel runs (entries of X and Y, contract-key bins,
+// problems). Filled by batch_setup, consumed by the launch sequence that follows.
+struct BatchDev {
+  int32_t n = 0;
+  std::vector<Plan> plans;
+  std::vector<BatchOut> hbo;  // per problem: F_Y and the output plan (positions filled later)
+  BatchArgs ba{};
+  GroupedX gx{};
+  Bins b{};
+  GroupCounters* gc = nullptr;
+  Counters* ctr = nullptr;
+  u64* per = nullptr;          // [3n]: products, output bound, output count per problem
+  uint32_t* gprob = nullptr;
+  u64* gfk = nullptr;
+  BatchOut* dbo = nullptr;     // [n]
+  int32_t* doz = nullptr;      // [n] output order per problem
+  u64* offs = nullptr;         // [2n + 2] value and coordinate offsets of a captured run
+  BatchLayoutArgs* dargs = nullptr;
+  bool wide = false;
+  int64_t total_x = 0, total_y = 0;
+  int tune_bucket = 0;
+};
+
+// Plans, descriptors and scratch of a batch (no kernel runs; the descriptors are copied on s).
+stc_status batch_setup(stc_ctx* ctx, int32_t n, const stc_problem* problems, Arena& ar, cudaStream_t s,
+                       BatchDev& bd) {
+  bd.n = n;
+  bd.plans.assign(n, Plan{});
+  std::vector<BatchProb> hb(n);
+  std::vector<int64_t> xrow(n + 1, 0), yrow(n + 1, 0);
+  std::vector<u64> fxoff(n + 1, 0);
+  std::vector<int32_t> oz(n);
+  unsigned __int128 bins = 0, fxsum = 0;
+  bool key32 = true;
+  for (int32_t i = 0; i < n; i++) {
+    const stc_problem& q = problems[i];
+    STC_TRY(make_plan(&q.X, &q.Y, q.ncontract, q.cx, q.cy, q.out_order, bd.plans[i]));
+    const Plan& pl = bd.plans[i];
+    if (pl.FY > 0xffffffffull) key32 = false;
+    BatchProb& b = hb[i];
+    b = BatchProb{};
+    b.xc = q.X.coords;
+    b.xv = q.X.vals;
+    b.yc = q.Y.coords;
+    b.yv = q.Y.vals;
+    b.kx = pl.kx;
+    b.ky = pl.ky;
+    b.koff = (u64)bins;
+    b.fxoff = (u64)fxsum;
+    b.FY = pl.FY;
+    oz[i] = pl.oz;
+    bins += pl.K;
+    fxsum += pl.FX;
+    xrow[i + 1] = xrow[i] + q.X.nnz;
+    yrow[i + 1] = yrow[i] + q.Y.nnz;
+    fxoff[i + 1] = (u64)fxsum;
+    if (bins > kMaxDirectBins) return fail(STC_ERR_UNSUPPORTED, "the batch's contract key spaces exceed 2^26 bins");
+    if (fxsum >= ((unsigned __int128)1 << 63)) return fail(STC_ERR_KEY_OVERFLOW, "the batch's X free key spaces exceed 2^63");
+    if (xrow[i + 1] > STC_MAX_NNZ || yrow[i + 1] > STC_MAX_NNZ)
+      return fail(STC_ERR_INVALID_ARG, "the batch holds more than STC_MAX_NNZ entries of X or of Y");
+  }
+  bd.total_x = xrow[n];
+  bd.total_y = yrow[n];
+  bd.tune_bucket = log2_floor((uint64_t)(bd.total_x + bd.total_y)) * 32 + std::min(31, log2_floor((uint64_t)n));
+  bd.hbo.assign(n, BatchOut{});
+  for (int32_t i = 0; i < n; i++) {
+    bd.hbo[i].FY = bd.plans[i].FY;
+    bd.hbo[i].op = bd.plans[i].op;
+  }
+
+  BatchArgs& ba = bd.ba;
+  ba = BatchArgs{};
+  ba.n = n;
+  ba.total_x = bd.total_x;
+  ba.total_y = bd.total_y;
+  ba.bins = (u64)bins;
+  ba.key32 = key32;
+  BatchProb* dpb = nullptr;
+  int64_t *dxrow = nullptr, *dyrow = nullptr;
+  u64* dfxoff = nullptr;
+  STC_TRY(ar.alloc(&dpb, (size_t)n));
+  STC_TRY(ar.alloc(&dxrow, (size_t)n + 1));
+  STC_TRY(ar.alloc(&dyrow, (size_t)n + 1));
+  STC_TRY(ar.alloc(&dfxoff, (size_t)n + 1));
+  STC_TRY(ar.alloc(&bd.ctr, 1));
+  STC_TRY(ar.alloc(&bd.per, 3 * (size_t)n));
+  STC_TRY(ar.alloc(&bd.dbo, (size_t)n));
+  STC_TRY(ar.alloc(&bd.doz, (size_t)n));
+  STC_TRY(ar.alloc(&bd.offs, 2 * (size_t)n + 2));
+  STC_TRY(ar.alloc(&bd.dargs, 1));
+  STC_CUDA(cudaMemcpyAsync(dpb, hb.data(), n * sizeof(BatchProb), cudaMemcpyHostToDevice, s));
+  STC_CUDA(cudaMemcpyAsync(dxrow, xrow.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  STC_CUDA(cudaMemcpyAsync(dyrow, yrow.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  STC_CUDA(cudaMemcpyAsync(dfxoff, fxoff.data(), (n + 1) * sizeof(u64), cudaMemcpyHostToDevice, s));
+  STC_CUDA(cudaMemcpyAsync(bd.dbo, bd.hbo.data(), n * sizeof(BatchOut), cudaMemcpyHostToDevice, s));
+  STC_CUDA(cudaMemcpyAsync(bd.doz, oz.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  ba.pb = dpb;
+  ba.xrow = dxrow;
+  ba.yrow = dyrow;
+  ba.fxoff = dfxoff;
+  ba.P = &bd.ctr->P;
+  ba.Pp = bd.per;
+  ba.pcap = bd.per + n;
+  ba.status = &bd.ctr->status;
+
+  const int64_t total_x = bd.total_x, total_y = bd.total_y;
+  const u64 gcap = pow2_at_least(std::max<u64>(64, 2 * (u64)std::max<int64_t>(total_x, 1)));
+  STC_TRY(ar.alloc(&ba.ycnt, ba.bins));
+  STC_TRY(ar.alloc(&ba.yoff, ba.bins + 1));
+  STC_TRY(ar.alloc(&ba.ycur, ba.bins));
+  if (key32) {
+    uint32_t* k = nullptr;
+    STC_TRY(ar.alloc(&k, (size_t)total_y));
+    ba.yfk = k;
+  } else {
+    u64* k = nullptr;
+    STC_TRY(ar.alloc(&k, (size_t)total_y));
+    ba.yfk = k;
+  }
+  STC_TRY(ar.alloc(&ba.yv, (size_t)total_y));
+  STC_TRY(ar.alloc(&ba.sv.fk, (size_t)total_x));
+  STC_TRY(ar.alloc(&ba.sv.ystart, (size_t)total_x));
+  STC_TRY(ar.alloc(&ba.sv.w, (size_t)total_x));
+  STC_TRY(ar.alloc(&ba.sv.v, (size_t)total_x));
+  ba.sv.count = &bd.ctr->ns;
+  STC_TRY(ar.alloc(&ba.idmap.keys, gcap));
+  ba.idmap.mask = gcap - 1;
+  STC_TRY(ar.alloc(&ba.gid, (size_t)total_x));
+  STC_TRY(ar.alloc(&ba.gcnt, gcap));
+  STC_TRY(ar.alloc(&ba.goff, gcap + 1));
+  STC_TRY(ar.alloc(&ba.gcur, gcap));
+  STC_TRY(ar.alloc(&ba.scan_scratch32, (size_t)std::max(scan_scratch_elems((int64_t)ba.bins),
+                                                          scan_scratch_elems((int64_t)gcap))));
+
+  // Grouped X, the class lists and counters.
+  bd.wide = !key32;
+  const int ncls = bd.wide ? kNumClasses64 : kNumClasses32;
+  const size_t maxg = (size_t)std::max<int64_t>(total_x, 1);
+  STC_TRY(ar.alloc(&bd.gx.ystart, maxg));
+  STC_TRY(ar.alloc(&bd.gx.w, maxg));
+  STC_TRY(ar.alloc(&bd.gx.v, maxg));
+  STC_TRY(ar.alloc(&bd.gc, 1));
+  STC_TRY(ar.alloc(&bd.gprob, gcap));
+  STC_TRY(ar.alloc(&bd.gfk, gcap));
+  Bins& b = bd.b;
+  b = Bins{};
+  b.nclasses = ncls;
+  for (int c = 0; c < ncls; c++) STC_TRY(ar.alloc(&b.list[c], maxg));
+  STC_TRY(ar.alloc(&b.huge_list, maxg));
+  STC_TRY(ar.alloc(&b.huge_off, maxg));
+  STC_TRY(ar.alloc(&b.huge_cap, maxg));
+  b.count = bd.gc->count;
+  b.huge_slots = &bd.gc->huge_slots;
+  b.out_cap = &bd.gc->out_cap;
+  b.status = &bd.ctr->status;
+  return STC_OK;
+}
+
+// Class thresholds of a group load factor: a group of bound t goes to the first class with
+// t <= ga * slots.
+void batch_set_load_factor(BatchDev& bd, double ga) {
+  const ClassShape* shapes = bd.wide ? kClassShapes64 : kClassShapes32;
+  for (int c = 0; c < bd.b.nclasses; c++) bd.b.tmax[c] = (u64)(ga * shapes[c].slots);
+}
+
+// The batch up to its per-group bins: counters cleared, Y grouped, X surveyed, grouped by
+// (problem, X free key) and binned. Only enqueues work on s (no host reads).
+stc_status batch_front(stc_ctx* ctx, BatchDev& bd, cudaStream_t s, StageTimer& tm) {
+  BatchArgs& ba = bd.ba;
+  const int32_t n = bd.n;
+  STC_CUDA(cudaMemsetAsync(bd.ctr, 0, sizeof(Counters), s));
+  STC_CUDA(cudaMemsetAsync(bd.per, 0, 3 * n * sizeof(u64), s));
+  if (ba.bins) STC_CUDA(cudaMemsetAsync(ba.ycnt, 0, ba.bins * sizeof(uint32_t), s));
+  STC_CUDA(cudaMemsetAsync(ba.idmap.keys, 0xff, (ba.idmap.mask + 1) * sizeof(u64), s));
+  STC_CUDA(cudaMemsetAsync(ba.gcnt, 0, (ba.idmap.mask + 1) * sizeof(uint32_t), s));
+  STC_CUDA(launch_batch_prepare(ba, ctx->sms, s));
+  tm.mark(1);
+  STC_CUDA(cudaMemsetAsync(bd.gc, 0, sizeof(GroupCounters), s));
+  STC_CUDA(launch_batch_group(ba, bd.gx, bd.b, bd.gprob, bd.gfk, ctx->sms, s));
+  tm.mark(2);
+  return STC_OK;
+}
+
+// GroupArgs of the batch's accumulation kernels.
+GroupArgs batch_group_args(const BatchDev& bd) {
+  GroupArgs a{};
+  a.goff = bd.ba.goff;
+  a.gx = bd.gx;
+  a.yfk = bd.ba.yfk;
+  a.yv = bd.ba.yv;
+  a.status = &bd.ctr->status;
+  a.nz = &bd.ctr->nz;
+  a.bout = bd.dbo;
+  a.bnz = bd.per + 2 * bd.n;
+  a.gprob = bd.gprob;
+  a.gfk = bd.gfk;
+  return a;
+}
+
+// One result per problem over a shared output block (offsets in elements).
+void batch_results(stc_ctx* ctx, cudaStream_t s, const BatchDev& bd, const std::shared_ptr<DeviceBlock>& blk,
+                   double* vals, int32_t* coords, const u64* voff, const u64* coff, const u64* hper,
+                   const stc_stats& common, stc_result** outs) {
+  const int32_t n = bd.n;
+  for (int32_t i = 0; i < n; i++) {
+    stc_result* r = new stc_result;
+    r->ctx = ctx;
+    r->stream = s;
+    r->order = bd.plans[i].oz;
+    r->shape = bd.plans[i].zshape;
+    r->nnz = (int64_t)hper[2 * n + i];
+    r->coords = coords ? coords + coff[i] : nullptr;
+    r->vals = vals ? vals + voff[i] : nullptr;
+    r->mem = blk;
+    r->stats = common;
+    r->stats.products = hper[i];
+    r->stats.out_capacity = hper[n + i];
+    ctx->live_results++;
+    outs[i] = r;
+  }
+}
+
+// Sizes one run of a batch needed, read back after it: what a captured run must provide.
+struct BatchSizes {
+  u64 vals = 0;     // output entries over all problems (sum of the exact bounds)
+  u64 coords = 0;   // output coordinates over all problems
+  u64 huge = 0;     // overflow-table slots
+  u64 maxcap = 0;   // largest bound of one problem
+};
+
+// The rest of a batch with the host in the loop: the bins' counters are read back, one output
+// block of the exact size is taken from `run`, the groups are accumulated, and the output
+// counts are read back into hper[2n, 3n). bd.b.tmax must be set. tune_cand >= 0 times the
+// accumulation for the autotuner.
+stc_status batch_finish_eager(stc_ctx* ctx, BatchDev& bd, const stc_opts& o, Arena& run, cudaStream_t s,
+                              StageTimer& tm, int tune_cand, bool* timed, std::vector<u64>& hper, BatchSizes& sz,
+                              double** vals_out, int32_t** coords_out, std::vector<u64>& voff,
+                              std::vector<u64>& coff) {
+  const int32_t n = bd.n;
+  Counters h{};
+  GroupCounters hg{};
+  hper.assign(3 * (size_t)n, 0);
+  STC_CUDA(cudaMemcpyAsync(&hg, bd.gc, sizeof(GroupCounters), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaMemcpyAsync(hper.data(), bd.per, 2 * n * sizeof(u64), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaMemcpyAsync(&h, bd.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaStreamSynchronize(s));
+  STC_TRY(status_word(h.status));
+  tm.mark(3);
+
+  // One output allocation: every problem's values, then every problem's coordinates.
+  voff.assign(n + 1, 0);
+  coff.assign(n + 1, 0);
+  sz = BatchSizes{};
+  for (int32_t i = 0; i < n; i++) {
+    voff[i + 1] = voff[i] + hper[n + i];
+    coff[i + 1] = coff[i] + hper[n + i] * (u64)bd.plans[i].oz;
+    sz.maxcap = std::max<u64>(sz.maxcap, hper[n + i]);
+  }
+  sz.vals = voff[n];
+  sz.coords = coff[n];
+  sz.huge = hg.huge_slots;
+  double* vals = nullptr;
+  int32_t* coords = nullptr;
+  STC_TRY(run.alloc(&vals, voff[n]));
+  STC_TRY(run.alloc(&coords, coff[n]));
+  std::vector<BatchOut> hbo = bd.hbo;
+  for (int32_t i = 0; i < n; i++) {
+    hbo[i].out_cap = hper[n + i];
+    hbo[i].coords = coords ? coords + coff[i] : nullptr;
+    hbo[i].vals = vals ? vals + voff[i] : nullptr;
+  }
+  STC_CUDA(cudaMemcpyAsync(bd.dbo, hbo.data(), n * sizeof(BatchOut), cudaMemcpyHostToDevice, s));
+  HugeGroups hh{};
+  hh.count = hg.count[kMaxClasses];
+  hh.countp = bd.gc->count + kMaxClasses;
+  hh.list = bd.b.huge_list;
+  hh.off = bd.b.huge_off;
+  hh.cap = bd.b.huge_cap;
+  if (hh.count) {
+    STC_TRY(run.alloc(&hh.keys, hg.huge_slots));
+    STC_TRY(run.alloc(&hh.vals, hg.huge_slots));
+    STC_CUDA(cudaMemsetAsync(hh.keys, 0xff, hg.huge_slots * sizeof(u64), s));
+  }
+  const GroupArgs a = batch_group_args(bd);
+  if (h.P > 0) {
+    const bool direct = !bd.wide && sz.maxcap < 0xffffffffull && o.accumulator != STC_ACC_HASH_SCAN;
+    tune_mark(ctx, bd.tune_bucket, tune_cand, false, s);
+    STC_CUDA(launch_group_classes(a, bd.wide, direct, bd.b, hg.count, ctx->sms, s));
+    STC_CUDA(launch_group_huge(a, hh, bd.wide, ctx->sms, s));
+    tune_mark(ctx, bd.tune_bucket, tune_cand, true, s);
+    if (timed) *timed = true;
+  }
+  tm.mark(4);
+  STC_CUDA(cudaMemcpyAsync(hper.data() + 2 * n, bd.per + 2 * n, n * sizeof(u64), cudaMemcpyDeviceToHost, s));
+  Counters h2{};
+  STC_CUDA(cudaMemcpyAsync(&h2, bd.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  STC_CUDA(cudaStreamSynchronize(s));
+  STC_TRY(status_word(h2.status));
+  *vals_out = vals;
+  *coords_out = coords;
+  return STC_OK;
+}
+
+}  // namespace
+
+// A prepared batch: the problems' descriptors and every scratch array held on the device
+// across runs, and, once the load factor is settled, the whole launch sequence of a run
+// captured in one CUDA graph that each later run replays.
+struct stc_batch_plan {
+  stc_ctx* ctx = nullptr;
+  stc_opts opts{};
+  int32_t n = 0;
+  std::vector<stc_problem> probs;
+  std::vector<std::vector<int64_t>> shapes;
+  std::vector<std::vector<int32_t>> modes;
+  cudaStream_t stream = nullptr;  // scratch allocation and graph capture
+  std::unique_ptr<Arena> scratch;
+  BatchDev bd;
+  BatchSizes sizes{};
+  double ga = 0.0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned graph_launches = 0;
+  u64* huge_keys = nullptr;
+  double* huge_vals = nullptr;
+  u64 huge_cap = 0;
+  // pinned host mirrors written by the captured copies
+  BatchLayoutArgs* h_args = nullptr;
+  u64* h_per = nullptr;
+  Counters* h_ctr = nullptr;
+  u64* h_offs = nullptr;
+  GroupCounters* h_gc = nullptr;
+  int64_t runs = 0, graph_runs = 0;
+};
+
+namespace {
+
+// Captures one run of the plan's batch on the plan's stream: the layout arguments copied in,
+// the front of the batch, the device-side output layout, every class kernel with its count read
+// on the device, and the copies of the counters the host reads after the run.
+stc_status plan_capture(stc_batch_plan* pl) {
+  BatchDev& bd = pl->bd;
+  stc_ctx* ctx = pl->ctx;
+  cudaStream_t ps = pl->stream;
+  // The overflow groups' table is the plan's, sized by the last run.
+  if (pl->sizes.huge > pl->huge_cap) {
+    const u64 cap = std::max<u64>(pl->sizes.huge, 64);
+    STC_TRY(pl->scratch->alloc(&pl->huge_keys, cap));
+    STC_TRY(pl->scratch->alloc(&pl->huge_vals, cap));
+    pl->huge_cap = cap;
+    STC_CUDA(cudaStreamSynchronize(ps));
+  }
+  pl->h_args->huge_keys = pl->huge_keys;
+  pl->h_args->huge_vals = pl->huge_vals;
+  pl->h_args->huge_cap = pl->huge_cap;
+  batch_set_load_factor(bd, pl->ga);
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  pl->exec = nullptr;
+  pl->graph = nullptr;
+  take_launches();
+  STC_CUDA(cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal));
+  auto body = [&]() -> stc_status {
+    StageTimer tm;
+    const int32_t n = bd.n;
+    STC_CUDA(cudaMemcpyAsync(bd.dargs, pl->h_args, sizeof(BatchLayoutArgs), cudaMemcpyHostToDevice, ps));
+    STC_TRY(batch_front(ctx, bd, ps, tm));
+    STC_CUDA(launch_batch_layout(n, bd.per + n, bd.doz, bd.dbo, bd.dargs, bd.offs, &bd.gc->huge_slots,
+                                 bd.gc->count + kMaxClasses, &bd.ctr->status, ps));
+    const GroupArgs a = batch_group_args(bd);
+    const bool direct =
+        !bd.wide && pl->sizes.maxcap < 0x7fffffffull && pl->opts.accumulator != STC_ACC_HASH_SCAN;
+    STC_CUDA(launch_group_classes(a, bd.wide, direct, bd.b, nullptr, ctx->sms, ps));
+    HugeGroups hh{};
+    hh.count = kCountOnDevice;
+    hh.countp = bd.gc->count + kMaxClasses;
+    hh.list = bd.b.huge_list;
+    hh.off = bd.b.huge_off;
+    hh.cap = bd.b.huge_cap;
+    hh.keys = pl->huge_keys;
+    hh.vals = pl->huge_vals;
+    STC_CUDA(launch_group_huge(a, hh, bd.wide, ctx->sms, ps));
+    STC_CUDA(cudaMemcpyAsync(pl->h_per, bd.per, 3 * n * sizeof(u64), cudaMemcpyDeviceToHost, ps));
+    STC_CUDA(cudaMemcpyAsync(pl->h_ctr, bd.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ps));
+    STC_CUDA(cudaMemcpyAsync(pl->h_offs, bd.offs, (2 * n + 2) * sizeof(u64), cudaMemcpyDeviceToHost, ps));
+    STC_CUDA(cudaMemcpyAsync(pl->h_gc, bd.gc, sizeof(GroupCounters), cudaMemcpyDeviceToHost, ps));
+    return STC_OK;
+  };
+  const stc_status st = body();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ps, &g);  // ends the capture whatever happened
+  if (st != STC_OK) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+  }
+  STC_CUDA(e);
+  pl->graph = g;
+  STC_CUDA(cudaGraphInstantiate(&pl->exec, g, 0));
+  pl->graph_launches = take_launches();
+  return STC_OK;
+}
+
+// One run with the host in the loop (the first runs, while the load factor is tuned, and any
+// run whose sizes outgrew the captured layout). Captures the graph once the load factor is
+// settled.
+stc_status plan_run_eager(stc_batch_plan* pl, cudaStream_t s, stc_result** outs) {
+  BatchDev& bd = pl->bd;
+  stc_ctx* ctx = pl->ctx;
+  int tune_cand = -1;
+  const bool given = pl->opts.group_load_factor > 0.0;
+  const double ga = given ? pl->opts.group_load_factor : tune_pick(ctx, bd.tune_bucket, &tune_cand);
+  struct TuneGuard {
+    stc_ctx* c;
+    int b, k;
+    bool armed = true;
+    ~TuneGuard() {
+      if (armed) tune_abort(c, b, k);
+    }
+  } tune_guard{ctx, bd.tune_bucket, tune_cand};
+  batch_set_load_factor(bd, ga);
+  Arena run(ctx, s);
+  StageTimer tm;
+  tm.start(pl->opts.record_times != 0, s);
+  take_launches();
+  STC_TRY(batch_front(ctx, bd, s, tm));
+  std::vector<u64> hper, voff, coff;
+  double* vals = nullptr;
+  int32_t* coords = nullptr;
+  bool timed = false;
+  STC_TRY(batch_finish_eager(ctx, bd, pl->opts, run, s, tm, tune_cand, &timed, hper, pl->sizes, &vals, &coords, voff,
+                             coff));
+  if (timed) tune_guard.armed = false;
+  stc_stats common{};
+  tm.collect(common);
+  common.launches = take_launches();
+  common.strategy = STC_STRATEGY_GROUPED;
+  common.accumulator = STC_ACC_HASH;
+  auto blk = adopt(run, ctx, s, {vals, coords});
+  batch_results(ctx, s, bd, blk, vals, coords, voff.data(), coff.data(), hper.data(), common, outs);
+  // Capture once the load factor is settled (given, or the tuner's pick for this bucket).
+  double settled = given ? ga : 0.0;
+  if (!given) {
+    int probe = -1;
+    const double pick = tune_pick(ctx, bd.tune_bucket, &probe);
+    if (probe < 0) settled = pick;
+    else tune_abort(ctx, bd.tune_bucket, probe);
+  }
+  if (settled > 0.0 && (!pl->exec || settled != pl->ga || pl->sizes.huge > pl->huge_cap)) {
+    pl->ga = settled;
+    const stc_status st = plan_capture(pl);
+    if (st != STC_OK) {
+      // The results of this run stand; the plan keeps running with the host in the loop.
+      cudaGetLastError();
+      pl->exec = nullptr;
+    }
+  }
+  return STC_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1083,44 +1550,15 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
   const stc_opts o = opts ? *opts : stc_opts{};
   if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
     return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
-
-  std::vector<Plan> plans(n);
-  std::vector<BatchProb> hb(n);
-  std::vector<int64_t> xrow(n + 1, 0), yrow(n + 1, 0);
-  std::vector<u64> fxoff(n + 1, 0);
-  unsigned __int128 bins = 0, fxsum = 0;
-  bool key32 = true;
-  for (int32_t i = 0; i < n; i++) {
-    const stc_problem& q = problems[i];
-    STC_TRY(make_plan(&q.X, &q.Y, q.ncontract, q.cx, q.cy, q.out_order, plans[i]));
-    const Plan& pl = plans[i];
-    if (pl.FY > 0xffffffffull) key32 = false;
-    BatchProb& b = hb[i];
-    b = BatchProb{};
-    b.xc = q.X.coords;
-    b.xv = q.X.vals;
-    b.yc = q.Y.coords;
-    b.yv = q.Y.vals;
-    b.kx = pl.kx;
-    b.ky = pl.ky;
-    b.koff = (u64)bins;
-    b.fxoff = (u64)fxsum;
-    b.FY = pl.FY;
-    bins += pl.K;
-    fxsum += pl.FX;
-    xrow[i + 1] = xrow[i] + q.X.nnz;
-    yrow[i + 1] = yrow[i] + q.Y.nnz;
-    fxoff[i + 1] = (u64)fxsum;
-    if (bins > kMaxDirectBins) return fail(STC_ERR_UNSUPPORTED, "the batch's contract key spaces exceed 2^26 bins");
-    if (fxsum >= ((unsigned __int128)1 << 63)) return fail(STC_ERR_KEY_OVERFLOW, "the batch's X free key spaces exceed 2^63");
-    if (xrow[i + 1] > STC_MAX_NNZ || yrow[i + 1] > STC_MAX_NNZ)
-      return fail(STC_ERR_INVALID_ARG, "the batch holds more than STC_MAX_NNZ entries of X or of Y");
-  }
-  const int64_t total_x = xrow[n], total_y = yrow[n];
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(ctx, s);
+  BatchDev bd;
+  STC_TRY(batch_setup(ctx, n, problems, ar, s, bd));
   // Load factor: given, or picked by the autotuner for this size bucket (entries, problems).
   int tune_cand = -1;
-  const int tune_bucket = log2_floor((uint64_t)(total_x + total_y)) * 32 + std::min(31, log2_floor((uint64_t)n));
-  const double ga = o.group_load_factor > 0.0 ? o.group_load_factor : tune_pick(ctx, tune_bucket, &tune_cand);
+  const double ga = o.group_load_factor > 0.0 ? o.group_load_factor : tune_pick(ctx, bd.tune_bucket, &tune_cand);
   struct TuneGuard {  // gives a picked candidate back if the batch fails before it is timed
     stc_ctx* c;
     int b, k;
@@ -1128,204 +1566,154 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
     ~TuneGuard() {
       if (armed) tune_abort(c, b, k);
     }
-  } tune_guard{ctx, tune_bucket, tune_cand};
-
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  Arena ar(ctx, s);
+  } tune_guard{ctx, bd.tune_bucket, tune_cand};
+  batch_set_load_factor(bd, ga);
   StageTimer tm;
   tm.start(o.record_times != 0, s);
   take_launches();
-
-  BatchArgs ba{};
-  ba.n = n;
-  ba.total_x = total_x;
-  ba.total_y = total_y;
-  ba.bins = (u64)bins;
-  ba.key32 = key32;
-  BatchProb* dpb = nullptr;
-  int64_t *dxrow = nullptr, *dyrow = nullptr;
-  u64* dfxoff = nullptr;
-  Counters* ctr = nullptr;
-  u64* per = nullptr;  // [3n]: products, output bound, output count per problem
-  STC_TRY(ar.alloc(&dpb, (size_t)n));
-  STC_TRY(ar.alloc(&dxrow, (size_t)n + 1));
-  STC_TRY(ar.alloc(&dyrow, (size_t)n + 1));
-  STC_TRY(ar.alloc(&dfxoff, (size_t)n + 1));
-  STC_TRY(ar.alloc(&ctr, 1));
-  STC_TRY(ar.alloc(&per, 3 * (size_t)n));
-  STC_CUDA(cudaMemcpyAsync(dpb, hb.data(), n * sizeof(BatchProb), cudaMemcpyHostToDevice, s));
-  STC_CUDA(cudaMemcpyAsync(dxrow, xrow.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  STC_CUDA(cudaMemcpyAsync(dyrow, yrow.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  STC_CUDA(cudaMemcpyAsync(dfxoff, fxoff.data(), (n + 1) * sizeof(u64), cudaMemcpyHostToDevice, s));
-  STC_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
-  STC_CUDA(cudaMemsetAsync(per, 0, 3 * n * sizeof(u64), s));
-  ba.pb = dpb;
-  ba.xrow = dxrow;
-  ba.yrow = dyrow;
-  ba.fxoff = dfxoff;
-  ba.P = &ctr->P;
-  ba.Pp = per;
-  ba.pcap = per + n;
-  ba.status = &ctr->status;
-
-  const u64 gcap = pow2_at_least(std::max<u64>(64, 2 * (u64)std::max<int64_t>(total_x, 1)));
-  STC_TRY(ar.alloc(&ba.ycnt, ba.bins));
-  STC_TRY(ar.alloc(&ba.yoff, ba.bins + 1));
-  STC_TRY(ar.alloc(&ba.ycur, ba.bins));
-  if (key32) {
-    uint32_t* k = nullptr;
-    STC_TRY(ar.alloc(&k, (size_t)total_y));
-    ba.yfk = k;
-  } else {
-    u64* k = nullptr;
-    STC_TRY(ar.alloc(&k, (size_t)total_y));
-    ba.yfk = k;
-  }
-  STC_TRY(ar.alloc(&ba.yv, (size_t)total_y));
-  STC_TRY(ar.alloc(&ba.sv.fk, (size_t)total_x));
-  STC_TRY(ar.alloc(&ba.sv.ystart, (size_t)total_x));
-  STC_TRY(ar.alloc(&ba.sv.w, (size_t)total_x));
-  STC_TRY(ar.alloc(&ba.sv.v, (size_t)total_x));
-  ba.sv.count = &ctr->ns;
-  STC_TRY(ar.alloc(&ba.idmap.keys, gcap));
-  ba.idmap.mask = gcap - 1;
-  STC_TRY(ar.alloc(&ba.gid, (size_t)total_x));
-  STC_TRY(ar.alloc(&ba.gcnt, gcap));
-  STC_TRY(ar.alloc(&ba.goff, gcap + 1));
-  STC_TRY(ar.alloc(&ba.gcur, gcap));
-  STC_TRY(ar.alloc(&ba.scan_scratch32, (size_t)std::max(scan_scratch_elems((int64_t)ba.bins),
-                                                          scan_scratch_elems((int64_t)gcap))));
-  if (ba.bins) STC_CUDA(cudaMemsetAsync(ba.ycnt, 0, ba.bins * sizeof(uint32_t), s));
-  STC_CUDA(cudaMemsetAsync(ba.idmap.keys, 0xff, gcap * sizeof(u64), s));
-  STC_CUDA(cudaMemsetAsync(ba.gcnt, 0, gcap * sizeof(uint32_t), s));
-  STC_CUDA(launch_batch_prepare(ba, ctx->sms, s));
-  tm.mark(1);
-
-  // Group X, bin the groups into table classes.
-  const bool wide = !key32;
-  const int ncls = wide ? kNumClasses64 : kNumClasses32;
-  const ClassShape* shapes = wide ? kClassShapes64 : kClassShapes32;
-  const size_t maxg = (size_t)std::max<int64_t>(total_x, 1);
-  GroupedX gx{};
-  Bins b{};
-  GroupCounters* gc = nullptr;
-  uint32_t* gprob = nullptr;
-  u64* gfk = nullptr;
-  STC_TRY(ar.alloc(&gx.ystart, maxg));
-  STC_TRY(ar.alloc(&gx.w, maxg));
-  STC_TRY(ar.alloc(&gx.v, maxg));
-  STC_TRY(ar.alloc(&gc, 1));
-  STC_TRY(ar.alloc(&gprob, gcap));
-  STC_TRY(ar.alloc(&gfk, gcap));
-  b.nclasses = ncls;
-  for (int c = 0; c < ncls; c++) {
-    b.tmax[c] = (u64)(ga * shapes[c].slots);
-    STC_TRY(ar.alloc(&b.list[c], maxg));
-  }
-  STC_TRY(ar.alloc(&b.huge_list, maxg));
-  STC_TRY(ar.alloc(&b.huge_off, maxg));
-  STC_TRY(ar.alloc(&b.huge_cap, maxg));
-  b.count = gc->count;
-  b.huge_slots = &gc->huge_slots;
-  b.out_cap = &gc->out_cap;
-  b.status = &ctr->status;
-  STC_CUDA(cudaMemsetAsync(gc, 0, sizeof(GroupCounters), s));
-  STC_CUDA(launch_batch_group(ba, gx, b, gprob, gfk, ctx->sms, s));
-  tm.mark(2);
-
-  Counters h{};
-  GroupCounters hg{};
-  std::vector<u64> hper(3 * (size_t)n);
-  STC_CUDA(cudaMemcpyAsync(&hg, gc, sizeof(GroupCounters), cudaMemcpyDeviceToHost, s));
-  STC_CUDA(cudaMemcpyAsync(hper.data(), per, 2 * n * sizeof(u64), cudaMemcpyDeviceToHost, s));
-  STC_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-  STC_CUDA(cudaStreamSynchronize(s));
-  STC_TRY(status_word(h.status));
-  tm.mark(3);
-
-  // One output allocation: every problem's values, then every problem's coordinates.
-  std::vector<u64> voff(n + 1, 0), coff(n + 1, 0);
-  for (int32_t i = 0; i < n; i++) {
-    voff[i + 1] = voff[i] + hper[n + i];
-    coff[i + 1] = coff[i] + hper[n + i] * (u64)plans[i].oz;
-  }
+  STC_TRY(batch_front(ctx, bd, s, tm));
+  std::vector<u64> hper, voff, coff;
+  BatchSizes sz;
   double* vals = nullptr;
   int32_t* coords = nullptr;
-  STC_TRY(ar.alloc(&vals, voff[n]));
-  STC_TRY(ar.alloc(&coords, coff[n]));
-  std::vector<BatchOut> hbo(n);
-  for (int32_t i = 0; i < n; i++) {
-    hbo[i].FY = plans[i].FY;
-    hbo[i].out_cap = hper[n + i];
-    hbo[i].coords = coords ? coords + coff[i] : nullptr;
-    hbo[i].vals = vals ? vals + voff[i] : nullptr;
-    hbo[i].op = plans[i].op;
-  }
-  BatchOut* dbo = nullptr;
-  STC_TRY(ar.alloc(&dbo, (size_t)n));
-  STC_CUDA(cudaMemcpyAsync(dbo, hbo.data(), n * sizeof(BatchOut), cudaMemcpyHostToDevice, s));
-  HugeGroups hh{};
-  hh.count = hg.count[kMaxClasses];
-  hh.list = b.huge_list;
-  hh.off = b.huge_off;
-  hh.cap = b.huge_cap;
-  if (hh.count) {
-    STC_TRY(ar.alloc(&hh.keys, hg.huge_slots));
-    STC_TRY(ar.alloc(&hh.vals, hg.huge_slots));
-    STC_CUDA(cudaMemsetAsync(hh.keys, 0xff, hg.huge_slots * sizeof(u64), s));
-  }
-  GroupArgs a{};
-  a.goff = ba.goff;
-  a.gx = gx;
-  a.yfk = ba.yfk;
-  a.yv = ba.yv;
-  a.status = &ctr->status;
-  a.nz = &ctr->nz;
-  a.bout = dbo;
-  a.bnz = per + 2 * n;
-  a.gprob = gprob;
-  a.gfk = gfk;
-  if (h.P > 0) {
-    u64 maxcap = 0;
-    for (int32_t i = 0; i < n; i++) maxcap = std::max<u64>(maxcap, hper[n + i]);
-    const bool direct = !wide && maxcap < 0xffffffffull && o.accumulator != STC_ACC_HASH_SCAN;
-    tune_mark(ctx, tune_bucket, tune_cand, false, s);
-    STC_CUDA(launch_group_classes(a, wide, direct, b, hg.count, ctx->sms, s));
-    STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
-    tune_mark(ctx, tune_bucket, tune_cand, true, s);
-    tune_guard.armed = false;
-  }
-  tm.mark(4);
-  STC_CUDA(cudaMemcpyAsync(hper.data() + 2 * n, per + 2 * n, n * sizeof(u64), cudaMemcpyDeviceToHost, s));
-  Counters h2{};
-  STC_CUDA(cudaMemcpyAsync(&h2, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-  STC_CUDA(cudaStreamSynchronize(s));
-  STC_TRY(status_word(h2.status));
-
+  bool timed = false;
+  STC_TRY(batch_finish_eager(ctx, bd, o, ar, s, tm, tune_cand, &timed, hper, sz, &vals, &coords, voff, coff));
+  if (timed) tune_guard.armed = false;
   auto blk = adopt(ar, ctx, s, {vals, coords});
   stc_stats common{};
   tm.collect(common);
   common.launches = take_launches();
   common.strategy = STC_STRATEGY_GROUPED;
   common.accumulator = STC_ACC_HASH;
+  batch_results(ctx, s, bd, blk, vals, coords, voff.data(), coff.data(), hper.data(), common, outs);
+  return STC_OK;
+}
+
+stc_status stc_batch_plan_create(stc_ctx* ctx, int32_t n, const stc_problem* problems, const stc_opts* opts,
+                                 stc_batch_plan** out) {
+  if (!ctx || !out || n <= 0 || !problems) return fail(STC_ERR_INVALID_ARG, "bad batch plan arguments");
+  *out = nullptr;
+  const stc_opts o = opts ? *opts : stc_opts{};
+  if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
+    return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  std::unique_ptr<stc_batch_plan> pl(new stc_batch_plan);
+  pl->ctx = ctx;
+  pl->opts = o;
+  pl->n = n;
+  // The problems' host arrays are copied; their device arrays are the caller's.
+  pl->probs.assign(problems, problems + n);
+  pl->shapes.resize(2 * (size_t)n);
+  pl->modes.resize(3 * (size_t)n);
   for (int32_t i = 0; i < n; i++) {
-    stc_result* r = new stc_result;
-    r->ctx = ctx;
-    r->stream = s;
-    r->order = plans[i].oz;
-    r->shape = plans[i].zshape;
-    r->nnz = (int64_t)hper[2 * n + i];
-    r->coords = hbo[i].coords;
-    r->vals = hbo[i].vals;
-    r->mem = blk;
-    r->stats = common;
-    r->stats.products = hper[i];
-    r->stats.out_capacity = hper[n + i];
-    ctx->live_results++;
-    outs[i] = r;
+    stc_problem& q = pl->probs[i];
+    STC_TRY(check_coo(&q.X, "X"));
+    STC_TRY(check_coo(&q.Y, "Y"));
+    if (q.ncontract < 0 || q.ncontract > q.X.order || q.ncontract > q.Y.order || (q.ncontract && (!q.cx || !q.cy)))
+      return fail(STC_ERR_INVALID_ARG, "problem %d: bad contract mode lists", i);
+    pl->shapes[2 * i].assign(q.X.shape, q.X.shape + q.X.order);
+    pl->shapes[2 * i + 1].assign(q.Y.shape, q.Y.shape + q.Y.order);
+    pl->modes[3 * i].assign(q.cx, q.cx + q.ncontract);
+    pl->modes[3 * i + 1].assign(q.cy, q.cy + q.ncontract);
+    const int oz = (q.X.order - q.ncontract) + (q.Y.order - q.ncontract);
+    if (q.out_order) pl->modes[3 * i + 2].assign(q.out_order, q.out_order + oz);
+    q.X.shape = pl->shapes[2 * i].data();
+    q.Y.shape = pl->shapes[2 * i + 1].data();
+    q.cx = pl->modes[3 * i].data();
+    q.cy = pl->modes[3 * i + 1].data();
+    q.out_order = q.out_order ? pl->modes[3 * i + 2].data() : nullptr;
   }
+  STC_CUDA(cudaStreamCreateWithFlags(&pl->stream, cudaStreamNonBlocking));
+  pl->scratch.reset(new Arena(ctx, pl->stream));
+  stc_status st = batch_setup(ctx, n, pl->probs.data(), *pl->scratch, pl->stream, pl->bd);
+  cudaError_t e = cudaSuccess;
+  if (st == STC_OK) {
+    e = cudaMallocHost(&pl->h_args, sizeof(BatchLayoutArgs));
+    if (e == cudaSuccess) e = cudaMallocHost(&pl->h_per, 3 * (size_t)n * sizeof(u64));
+    if (e == cudaSuccess) e = cudaMallocHost(&pl->h_ctr, sizeof(Counters));
+    if (e == cudaSuccess) e = cudaMallocHost(&pl->h_offs, (2 * (size_t)n + 2) * sizeof(u64));
+    if (e == cudaSuccess) e = cudaMallocHost(&pl->h_gc, sizeof(GroupCounters));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+    if (e != cudaSuccess) st = fail(STC_ERR_CUDA, "batch plan set-up failed: %s", cudaGetErrorString(e));
+  }
+  if (st != STC_OK) {
+    stc_batch_plan_destroy(pl.release());
+    return st;
+  }
+  *out = pl.release();
+  return STC_OK;
+}
+
+stc_status stc_batch_plan_run(stc_batch_plan* pl, void* stream, stc_result** outs) {
+  if (!pl || !outs) return fail(STC_ERR_INVALID_ARG, "plan or outs is NULL");
+  for (int32_t i = 0; i < pl->n; i++) outs[i] = nullptr;
+  stc_ctx* ctx = pl->ctx;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  pl->runs++;
+  if (!pl->exec) return plan_run_eager(pl, s, outs);
+  // Replay: one output block of the last run's exact size, the layout arguments written for
+  // the graph's first copy, the graph, one wait.
+  const int32_t n = pl->n;
+  BatchDev& bd = pl->bd;
+  const u64 vbytes = (pl->sizes.vals * 8 + 15) & ~15ull;
+  const u64 bytes = vbytes + pl->sizes.coords * 4;
+  Arena run(ctx, s);
+  unsigned char* block = nullptr;
+  STC_TRY(run.alloc(&block, (size_t)std::max<u64>(bytes, 16)));
+  pl->h_args->out = block;
+  pl->h_args->out_bytes = bytes;
+  STC_CUDA(cudaGraphLaunch(pl->exec, s));
+  STC_CUDA(cudaStreamSynchronize(s));
+  const uint32_t status = pl->h_ctr->status;
+  if (status & kStatOutOverflow) {
+    // This run's bounds outgrew the captured layout (the inputs' contents changed): run it
+    // again with the host in the loop, which also captures a layout of the new sizes.
+    return plan_run_eager(pl, s, outs);
+  }
+  STC_TRY(status_word(status));
+  pl->graph_runs++;
+  const u64* offs = pl->h_offs;
+  std::vector<u64> voff(offs, offs + n + 1), coff(offs + n + 1, offs + 2 * n + 2);
+  double* vals = reinterpret_cast<double*>(block);
+  int32_t* coords = reinterpret_cast<int32_t*>(block + vbytes);
+  stc_stats common{};
+  common.launches = pl->graph_launches;
+  common.strategy = STC_STRATEGY_GROUPED;
+  common.accumulator = STC_ACC_HASH;
+  auto blk = adopt(run, ctx, s, {block});
+  batch_results(ctx, s, bd, blk, vals, coords, voff.data(), coff.data(), pl->h_per, common, outs);
+  return STC_OK;
+}
+
+stc_status stc_batch_plan_stats(const stc_batch_plan* pl, int64_t* runs, int64_t* graph_runs,
+                                double* group_load_factor) {
+  if (!pl) return fail(STC_ERR_INVALID_ARG, "plan is NULL");
+  if (runs) *runs = pl->runs;
+  if (graph_runs) *graph_runs = pl->graph_runs;
+  if (group_load_factor) *group_load_factor = pl->exec ? pl->ga : 0.0;
+  return STC_OK;
+}
+
+stc_status stc_batch_plan_destroy(stc_batch_plan* pl) {
+  if (!pl) return STC_OK;
+  DeviceGuard g(pl->ctx->device);
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  if (pl->stream) cudaStreamSynchronize(pl->stream);
+  pl->scratch.reset();  // scratch goes back to the pool in the plan stream's order
+  if (pl->stream) {
+    cudaStreamSynchronize(pl->stream);
+    cudaStreamDestroy(pl->stream);
+  }
+  if (pl->h_args) cudaFreeHost(pl->h_args);
+  if (pl->h_per) cudaFreeHost(pl->h_per);
+  if (pl->h_ctr) cudaFreeHost(pl->h_ctr);
+  if (pl->h_offs) cudaFreeHost(pl->h_offs);
+  if (pl->h_gc) cudaFreeHost(pl->h_gc);
+  delete pl;
   return STC_OK;
 }
 

@@ -269,6 +269,84 @@ __global__ void __launch_bounds__(kThreads) bin_batch_kernel(u64 G, const uint32
   }
 }
 
+// Output layout of a captured batch, on the device: every problem's output region is placed
+// in the run's output block by an exclusive scan of the exact bounds (values first, then
+// coordinates, 16-byte aligned), and the overflow groups' table is cleared. When the block
+// or the table is too small for this run's bounds, nothing is placed (every capacity 0, no
+// overflow group runs) and the status word says so; the host then runs the batch again with
+// the sizes it reads back.
+constexpr int kLayoutThreads = 1024;
+__global__ void __launch_bounds__(kLayoutThreads) batch_layout_kernel(int n, const u64* __restrict__ pcap,
+                                                                      const int32_t* __restrict__ oz,
+                                                                      BatchOut* __restrict__ bo,
+                                                                      const BatchLayoutArgs* __restrict__ args,
+                                                                      u64* __restrict__ offs, const u64* huge_slots,
+                                                                      uint32_t* huge_count, uint32_t* status) {
+  __shared__ u64 s_tot[2][kLayoutThreads / 32 + 1];
+  const int per = (n + kLayoutThreads - 1) / kLayoutThreads;
+  const int i0 = (int)threadIdx.x * per, i1 = i0 + per < n ? i0 + per : n;
+  u64 sv = 0, sc = 0;
+  for (int i = i0; i < i1; i++) {
+    sv += pcap[i];
+    sc += pcap[i] * (u64)oz[i];
+  }
+  // Block exclusive scans of the two sums.
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  u64 xv = sv, xc = sc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u64 a = __shfl_up_sync(0xffffffffu, xv, o), c = __shfl_up_sync(0xffffffffu, xc, o);
+    if ((int)lane >= o) xv += a, xc += c;
+  }
+  if (lane == 31) s_tot[0][warp] = xv, s_tot[1][warp] = xc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    constexpr int NW = kLayoutThreads / 32;
+    u64 tv = (int)lane < NW ? s_tot[0][lane] : 0, tc = (int)lane < NW ? s_tot[1][lane] : 0;
+    u64 iv = tv, ic = tc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 a = __shfl_up_sync(0xffffffffu, iv, o), c = __shfl_up_sync(0xffffffffu, ic, o);
+      if ((int)lane >= o) iv += a, ic += c;
+    }
+    if ((int)lane < NW) s_tot[0][lane] = iv - tv, s_tot[1][lane] = ic - tc;
+    if (lane == 31) s_tot[0][NW] = iv, s_tot[1][NW] = ic;
+  }
+  __syncthreads();
+  constexpr int NW = kLayoutThreads / 32;
+  const u64 tot_v = s_tot[0][NW], tot_c = s_tot[1][NW];
+  const u64 vbytes = (tot_v * 8 + 15) & ~15ull;
+  const bool fits = vbytes + tot_c * 4 <= args->out_bytes && *huge_slots <= args->huge_cap;
+  u64 ov = s_tot[0][warp] + xv - sv, oc = s_tot[1][warp] + xc - sc;
+  double* const vbase = reinterpret_cast<double*>(args->out);
+  int32_t* const cbase = reinterpret_cast<int32_t*>(args->out + vbytes);
+  for (int i = i0; i < i1; i++) {
+    offs[i] = ov;
+    offs[n + 1 + i] = oc;
+    bo[i].out_cap = fits ? pcap[i] : 0;
+    bo[i].vals = fits ? vbase + ov : nullptr;
+    bo[i].coords = fits ? cbase + oc : nullptr;
+    ov += pcap[i];
+    oc += pcap[i] * (u64)oz[i];
+  }
+  if (threadIdx.x == 0) {
+    offs[n] = tot_v;
+    offs[2 * n + 1] = tot_c;
+    if (!fits) {
+      atomicOr(status, kStatOutOverflow);
+      *huge_count = 0;
+    }
+  }
+  // Clear the overflow groups' table.
+  if (fits) {
+    const u64 hs = *huge_slots;
+    for (u64 k = threadIdx.x; k < hs; k += kLayoutThreads) {
+      args->huge_keys[k] = kEmpty64;
+      args->huge_vals[k] = 0.0;
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_batch_prepare(const BatchArgs& ba, int sms, cudaStream_t s) {
@@ -317,6 +395,15 @@ cudaError_t launch_batch_group(const BatchArgs& ba, GroupedX gx, const Bins& b, 
   bin_batch_kernel<<<grid_for(G, sms), kThreads, 0, s>>>((u64)G, ba.goff, gx.w, ba.idmap.keys, ba.fxoff, ba.n, ba.pb,
                                                          b, gprob, gfk, ba.pcap);
   note_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_layout(int n, const u64* pcap, const int32_t* oz, BatchOut* bo, const BatchLayoutArgs* args,
+                                u64* offs, const u64* huge_slots, uint32_t* huge_count, uint32_t* status,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  batch_layout_kernel<<<1, kLayoutThreads, 0, s>>>(n, pcap, oz, bo, args, offs, huge_slots, huge_count, status);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -399,7 +399,8 @@ __device__ __forceinline__ void write_group_smem(const GroupArgs& a, u64 g, KT* 
 // once; write_group_smem empties it again after each group.
 template <int SLOTS, int THREADS, typename KT>
 __global__ void __launch_bounds__(THREADS) group_smem_kernel(GroupArgs a, const uint32_t* __restrict__ list,
-                                                             uint32_t count) {
+                                                             const uint32_t* __restrict__ countp) {
+  const uint32_t count = *countp;
   extern __shared__ __align__(16) unsigned char smem[];
   double* vals = reinterpret_cast<double*>(smem);
   KT* keys = reinterpret_cast<KT*>(vals + SLOTS);
@@ -517,7 +518,8 @@ __global__ void __launch_bounds__(THREADS) group_global_kernel(GroupArgs a, Huge
   __shared__ uint32_t warp_cnt[THREADS / 32];
   __shared__ u64 warp_base[THREADS / 32];
   __shared__ OutTarget tg;
-  for (uint32_t k = blockIdx.x; k < h.count; k += gridDim.x) {
+  const uint32_t count = *h.countp;
+  for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
     const uint32_t g = h.list[k];
     u64* keys = h.keys + h.off[k];
     double* vals = h.vals + h.off[k];
@@ -1665,7 +1667,8 @@ static_assert(sizeof(WarpSlice<256, uint32_t>) % 16 == 0 && sizeof(WarpSlice<102
 
 template <int SLOTS, typename KT, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) group_warp_kernel(GroupArgs a, const uint32_t* __restrict__ list,
-                                                                uint32_t count) {
+                                                                const uint32_t* __restrict__ countp) {
+  const uint32_t count = *countp;
   constexpr int B = Bucket<KT>::N;
   constexpr uint32_t NB = SLOTS / B;
   constexpr int D = 4;
@@ -1794,7 +1797,8 @@ __global__ void __launch_bounds__(WARPS * 32) group_warp_kernel(GroupArgs a, con
 }
 
 template <int SLOTS, typename KT>
-cudaError_t launch_warp_class(const GroupArgs& a, const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
+cudaError_t launch_warp_class(const GroupArgs& a, const uint32_t* list, const uint32_t* countp, uint32_t count, int sms,
+                              cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   constexpr int WARPS = 8;
   const size_t smem = WARPS * sizeof(WarpSlice<SLOTS, KT>);
@@ -1805,9 +1809,9 @@ cudaError_t launch_warp_class(const GroupArgs& a, const uint32_t* list, uint32_t
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const uint32_t need = (count + WARPS - 1) / WARPS;
+  const uint32_t need = count == kCountOnDevice ? count : (count + WARPS - 1) / WARPS;
   const uint32_t cap = (uint32_t)(sms * per_sm);
-  kern<<<need < cap ? need : cap, WARPS * 32, smem, s>>>(a, list, count);
+  kern<<<need < cap ? need : cap, WARPS * 32, smem, s>>>(a, list, countp);
   note_launch();
   return cudaGetLastError();
 }
@@ -1822,7 +1826,8 @@ cudaError_t launch_warp_class(const GroupArgs& a, const uint32_t* list, uint32_t
 // is visible. No values are kept in shared memory and no table scan writes the output.
 template <int SLOTS, int THREADS, int D, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) group_direct_kernel(GroupArgs a, const uint32_t* __restrict__ list,
-                                                                     uint32_t count) {
+                                                                     const uint32_t* __restrict__ countp) {
+  const uint32_t count = *countp;
   constexpr int NW = THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
@@ -1933,7 +1938,8 @@ __global__ void __launch_bounds__(THREADS, MINB) group_direct_kernel(GroupArgs a
 }
 
 template <int SLOTS, int THREADS, int D, int MINB>
-cudaError_t launch_direct_class(const GroupArgs& a, const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
+cudaError_t launch_direct_class(const GroupArgs& a, const uint32_t* list, const uint32_t* countp, uint32_t count,
+                                int sms, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   const size_t smem = 2 * SLOTS * sizeof(uint32_t) + sizeof(Chunk<THREADS>);
   auto kern = group_direct_kernel<SLOTS, THREADS, D, MINB>;
@@ -1944,13 +1950,14 @@ cudaError_t launch_direct_class(const GroupArgs& a, const uint32_t* list, uint32
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const uint32_t cap = (uint32_t)(sms * per_sm);
-  kern<<<count < cap ? count : cap, THREADS, smem, s>>>(a, list, count);
+  kern<<<count < cap ? count : cap, THREADS, smem, s>>>(a, list, countp);
   note_launch();
   return cudaGetLastError();
 }
 
 template <int SLOTS, int THREADS, typename KT>
-cudaError_t launch_class(const GroupArgs& a, const uint32_t* list, uint32_t count, int sms, cudaStream_t s) {
+cudaError_t launch_class(const GroupArgs& a, const uint32_t* list, const uint32_t* countp, uint32_t count, int sms,
+                         cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   const size_t smem = SLOTS * (sizeof(double) + sizeof(KT)) + sizeof(Chunk<THREADS>);
   auto kern = group_smem_kernel<SLOTS, THREADS, KT>;
@@ -1961,7 +1968,7 @@ cudaError_t launch_class(const GroupArgs& a, const uint32_t* list, uint32_t coun
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const uint32_t cap = (uint32_t)(sms * per_sm);
-  kern<<<count < cap ? count : cap, THREADS, smem, s>>>(a, list, count);
+  kern<<<count < cap ? count : cap, THREADS, smem, s>>>(a, list, countp);
   note_launch();
   return cudaGetLastError();
 }
@@ -1994,23 +2001,28 @@ cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, 
 cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct, const Bins& b,
                                  const uint32_t* counts, int sms, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
+  // Host counts size the grids (a class without groups is not launched); without them
+  // (counts == nullptr) each class kernel runs a full persistent grid and reads its count.
+  uint32_t h[kMaxClasses];
+  for (int c = 0; c < kMaxClasses; c++) h[c] = counts ? counts[c] : kCountOnDevice;
+  const uint32_t* d = b.count;
   if (!wide_keys && direct) {
-    if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], counts[0], sms, s))) return e;
-    if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], counts[1], sms, s))) return e;
-    if ((e = launch_direct_class<4096, 256, 6, 4>(a, b.list[2], counts[2], sms, s))) return e;
-    if ((e = launch_direct_class<8192, 512, 6, 2>(a, b.list[3], counts[3], sms, s))) return e;
-    if ((e = launch_direct_class<16384, 1024, 4, 1>(a, b.list[4], counts[4], sms, s))) return e;
+    if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], d + 0, h[0], sms, s))) return e;
+    if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], d + 1, h[1], sms, s))) return e;
+    if ((e = launch_direct_class<4096, 256, 6, 4>(a, b.list[2], d + 2, h[2], sms, s))) return e;
+    if ((e = launch_direct_class<8192, 512, 6, 2>(a, b.list[3], d + 3, h[3], sms, s))) return e;
+    if ((e = launch_direct_class<16384, 1024, 4, 1>(a, b.list[4], d + 4, h[4], sms, s))) return e;
   } else if (!wide_keys) {
-    if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], counts[0], sms, s))) return e;
-    if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], counts[1], sms, s))) return e;
-    if ((e = launch_class<4096, 256, uint32_t>(a, b.list[2], counts[2], sms, s))) return e;
-    if ((e = launch_class<8192, 512, uint32_t>(a, b.list[3], counts[3], sms, s))) return e;
-    if ((e = launch_class<16384, 1024, uint32_t>(a, b.list[4], counts[4], sms, s))) return e;
+    if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], d + 0, h[0], sms, s))) return e;
+    if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], d + 1, h[1], sms, s))) return e;
+    if ((e = launch_class<4096, 256, uint32_t>(a, b.list[2], d + 2, h[2], sms, s))) return e;
+    if ((e = launch_class<8192, 512, uint32_t>(a, b.list[3], d + 3, h[3], sms, s))) return e;
+    if ((e = launch_class<16384, 1024, uint32_t>(a, b.list[4], d + 4, h[4], sms, s))) return e;
   } else {
-    if ((e = launch_warp_class<256, u64>(a, b.list[0], counts[0], sms, s))) return e;
-    if ((e = launch_warp_class<1024, u64>(a, b.list[1], counts[1], sms, s))) return e;
-    if ((e = launch_class<4096, 256, u64>(a, b.list[2], counts[2], sms, s))) return e;
-    if ((e = launch_class<8192, 512, u64>(a, b.list[3], counts[3], sms, s))) return e;
+    if ((e = launch_warp_class<256, u64>(a, b.list[0], d + 0, h[0], sms, s))) return e;
+    if ((e = launch_warp_class<1024, u64>(a, b.list[1], d + 1, h[1], sms, s))) return e;
+    if ((e = launch_class<4096, 256, u64>(a, b.list[2], d + 2, h[2], sms, s))) return e;
+    if ((e = launch_class<8192, 512, u64>(a, b.list[3], d + 3, h[3], sms, s))) return e;
   }
   return cudaSuccess;
 }
@@ -2090,7 +2102,7 @@ cudaError_t launch_group_dense(const GroupArgs& a, const uint32_t* yoff, uint32_
 }
 
 cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s) {
-  if (h.count == 0) return cudaSuccess;
+  if (h.count == 0) return cudaSuccess;  // h.count == kCountOnDevice: unknown on the host
   const uint32_t cap = (uint32_t)sms * 2;
   if (wide_keys)
     group_global_kernel<512, u64><<<h.count < cap ? h.count : cap, 512, 0, s>>>(a, h);

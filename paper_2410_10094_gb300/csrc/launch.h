@@ -195,8 +195,12 @@ struct OutTarget {
   OutPlan op;
 };
 
+// A count only the device knows (launchers then run a full persistent grid).
+constexpr uint32_t kCountOnDevice = 0xffffffffu;
+
 struct HugeGroups {
-  uint32_t count;
+  uint32_t count;             // number of overflow groups, or kCountOnDevice
+  const uint32_t* countp;     // device copy of the count, read by the kernel
   const uint32_t* list;
   const u64* off;
   const u64* cap;
@@ -209,7 +213,8 @@ cudaError_t launch_x_group_scatter(Survivors sv, uint32_t* gcur, GroupedX gx, in
 cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, u64 FY, const Bins& b, int sms,
                               cudaStream_t s);
 // direct: the shared-memory classes may write outputs as keys are first claimed (needs 32-bit
-// keys and output positions below 2^32 in every problem).
+// keys and output positions below 2^32 in every problem). counts: host copies of the class
+// counts (b.count), used to size the grids, or null when only the device knows them.
 cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct, const Bins& b,
                                  const uint32_t* counts, int sms, cudaStream_t s);
 cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s);
@@ -261,6 +266,21 @@ struct BatchArgs {
 };
 
 cudaError_t launch_batch_prepare(const BatchArgs& ba, int sms, cudaStream_t s);
+
+// Where one run of a captured batch puts its outputs (written by the host before each replay).
+struct BatchLayoutArgs {
+  unsigned char* out;  // output block: values of every problem, then coordinates
+  u64 out_bytes;       // its size
+  u64* huge_keys;      // overflow groups' table
+  double* huge_vals;
+  u64 huge_cap;        // its slots
+};
+// Places every problem's output region in the run's block from the exact bounds pcap[n]
+// (offs: [n + 1] value offsets, then [n + 1] coordinate offsets, in elements) and clears the
+// overflow table; flags kStatOutOverflow (and places nothing) when the block is too small.
+cudaError_t launch_batch_layout(int n, const u64* pcap, const int32_t* oz, BatchOut* bo, const BatchLayoutArgs* args,
+                                u64* offs, const u64* huge_slots, uint32_t* huge_count, uint32_t* status,
+                                cudaStream_t s);
 cudaError_t launch_batch_group(const BatchArgs& ba, GroupedX gx, const Bins& b, uint32_t* gprob, u64* gfk, int sms,
                                cudaStream_t s);
 

@@ -449,6 +449,186 @@ __global__ void __launch_bounds__(kThreads, kXMinBlocks) x_scatter_dense_kernel(
 }
 
 // Runs `body.template operator()<ORDER, VEC>()` for the runtime order and alignment.
+// ---- the survey with X's coordinates streamed through shared memory by bulk copies: one
+// persistent CTA per SM, a ring of kSvStages chunks of coordinate rows filled by one producer
+// thread (cp.async.bulk, completion counted on the stage's mbarrier) and consumed by
+// kSvConsumers warps, which release each stage through a second mbarrier. The copies keep
+// up to kSvStages chunks per SM in flight without holding them in registers. Rows whose
+// contract key has a Y run (bitmap in shared memory) are appended to the survivor list as in
+// x_survey_kernel. Needs 16-byte aligned coordinates and K <= kNonemptyMaxKeys.
+#ifndef SV_CONSUMERS
+#define SV_CONSUMERS 16
+#endif
+#ifndef SV_STAGES
+#define SV_STAGES 6
+#endif
+#ifndef SV_ROWS
+#define SV_ROWS 1024
+#endif
+constexpr int kSvConsumers = SV_CONSUMERS;
+constexpr int kSvThreads = (kSvConsumers + 1) * 32;
+constexpr int kSvStages = SV_STAGES;
+template <int ORDER>
+__host__ __device__ constexpr int sv_rows() {
+  // rows per chunk: a multiple of 4 (16-byte chunk sizes) and of 32 * kSvConsumers
+  return ORDER <= 4 || SV_ROWS / 2 < 32 * kSvConsumers ? SV_ROWS : SV_ROWS / 2;
+}
+template <int ORDER>
+__host__ __device__ constexpr size_t sv_ring_bytes() {
+  return (size_t)kSvStages * sv_rows<ORDER>() * ORDER * 4;
+}
+
+template <int ORDER, bool GROUPS>
+__global__ void __launch_bounds__(kSvThreads, 1) x_survey_bulk_kernel(const int32_t* __restrict__ coords,
+                                                                     const double* __restrict__ vals, int64_t n,
+                                                                     KeyPlan p, const uint32_t* __restrict__ yoff,
+                                                                     Survivors sv, u64* __restrict__ P,
+                                                                     uint32_t* __restrict__ gcnt, uint32_t* status,
+                                                                     const uint32_t* __restrict__ nonempty,
+                                                                     uint32_t ne_words) {
+  constexpr int R = sv_rows<ORDER>();
+  constexpr int RPW = R / kSvConsumers;  // rows of a chunk per consumer warp
+  static_assert(R % 4 == 0 && RPW % 32 == 0, "chunk shape");
+  extern __shared__ __align__(128) unsigned char smem[];
+  int32_t* const ring = reinterpret_cast<int32_t*>(smem);
+  uint32_t* const ne = reinterpret_cast<uint32_t*>(smem + sv_ring_bytes<ORDER>());
+  __shared__ __align__(8) uint64_t full[kSvStages], empty[kSvStages];
+  __shared__ u64 b_fk[kSvConsumers][64];
+  __shared__ uint32_t b_ck[kSvConsumers][64];
+  __shared__ u64 b_row[kSvConsumers][64];
+  __shared__ u64 warp_p[kSvConsumers];
+  __shared__ int s_abort;
+  const unsigned lane = lane_id(), wq = threadIdx.x >> 5;
+  const int64_t nchunks = n / R;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSvStages; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kSvConsumers);
+    }
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  for (uint32_t i = threadIdx.x; i < ne_words; i += kSvThreads) ne[i] = nonempty[i];
+  __syncthreads();
+
+  if (wq == kSvConsumers) {
+    // ---- producer: one thread issues the chunk copies of this CTA, kSvStages ahead.
+    if (lane == 0) {
+      int64_t issued = 0;
+      for (int64_t k = 0;; k++) {
+        const int64_t c = (int64_t)blockIdx.x + k * gridDim.x;
+        if (c >= nchunks) break;
+        const int st = (int)(k % kSvStages);
+        const uint32_t round = (uint32_t)(k / kSvStages);
+        if (round > 0 && !mbar_wait(&empty[st], (round - 1) & 1u)) {
+          atomicOr(status, kStatTimeout);
+          s_abort = 1;
+          break;
+        }
+        if (s_abort) break;
+        constexpr uint32_t bytes = (uint32_t)(R * ORDER * 4);
+        mbar_arrive_expect_tx(&full[st], bytes);
+        bulk_load(ring + (size_t)st * R * ORDER, coords + c * (int64_t)R * ORDER, bytes, &full[st]);
+        issued = k + 1;
+      }
+      if (s_abort) {
+        // Let the copies already issued land before the CTA exits (bounded).
+        const int64_t k0 = issued > kSvStages ? issued - kSvStages : 0;
+        for (int64_t k = k0; k < issued; k++) mbar_wait(&full[k % kSvStages], (uint32_t)(k / kSvStages) & 1u);
+      }
+    }
+    return;
+  }
+  // ---- consumers.
+  uint32_t held = 0;  // warp-uniform
+  u64 my_p = 0;
+  auto flush = [&]() {
+    __syncwarp();
+    unsigned pos = 0;
+    if (lane == 0) pos = atomicAdd(sv.count, held);
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    for (uint32_t k = lane; k < held; k += 32) {
+      const uint32_t c = b_ck[wq][k];
+      const u64 fk = b_fk[wq][k];
+      const uint32_t lo = __ldg(yoff + (u64)c * p.nseg);
+      const uint32_t w = __ldg(yoff + ((u64)c + 1) * p.nseg) - lo;
+      const double v = __ldg(vals + b_row[wq][k]);
+      sv.fk[pos + k] = fk;
+      if (sv.ck) sv.ck[pos + k] = c;
+      sv.ystart[pos + k] = lo;
+      sv.w[pos + k] = w;
+      sv.v[pos + k] = v;
+      my_p += w;
+      if (GROUPS) atomicAdd(gcnt + fk, 1u);
+    }
+    __syncwarp();
+    held = 0;
+  };
+  // One row per lane: keys, the range check, the bitmap test, and the append of survivors.
+  auto take = [&](const int32_t* c, int64_t row, bool in) {
+    uint64_t ck = 0, fk = 0;
+    bool live = false;
+    if (in) {
+      const bool ok = keys_of<ORDER>(c, p, ck, fk);
+      if (!ok) atomicOr(status, kStatCoordRange);
+      live = ok && ((ne[ck >> 5] >> (ck & 31)) & 1u);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, live);
+    if (live) {
+      const uint32_t k = held + __popc(m & lanemask_lt());
+      b_fk[wq][k] = fk;
+      b_ck[wq][k] = (uint32_t)ck;
+      b_row[wq][k] = (u64)row;
+    }
+    held += __popc(m);
+    if (held >= 32) flush();
+  };
+  bool aborted = false;
+  for (int64_t k = 0;; k++) {
+    const int64_t c = (int64_t)blockIdx.x + k * gridDim.x;
+    if (c >= nchunks) break;
+    const int st = (int)(k % kSvStages);
+    if (!mbar_wait(&full[st], (uint32_t)(k / kSvStages) & 1u)) {
+      atomicOr(status, kStatTimeout);
+      s_abort = 1;
+      aborted = true;
+      break;
+    }
+    const int32_t* rows = ring + (size_t)st * R * ORDER;
+#pragma unroll
+    for (int i = 0; i < RPW / 32; i++) {
+      const int r = (int)wq * RPW + i * 32 + (int)lane;
+      int32_t cr[ORDER > 0 ? ORDER : 1];
+#pragma unroll
+      for (int j = 0; j < ORDER; j++) cr[j] = rows[r * ORDER + j];
+      take(cr, c * R + r, true);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+  // The rows after the last whole chunk, read directly by the last CTA.
+  if (!aborted && blockIdx.x == gridDim.x - 1) {
+    for (int64_t base = nchunks * R + (int64_t)wq * 32; base < n; base += 32 * kSvConsumers) {
+      const int64_t row = base + lane;
+      int32_t cr[ORDER > 0 ? ORDER : 1];
+#pragma unroll
+      for (int j = 0; j < ORDER; j++) cr[j] = row < n ? __ldg(coords + row * ORDER + j) : 0;
+      take(cr, row, row < n);
+    }
+  }
+  if (held) flush();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_p += __shfl_down_sync(0xffffffffu, my_p, o);
+  if (lane == 0) warp_p[wq] = my_p;
+  // Consumer warps only (the producer warp has returned): a named barrier over them.
+  asm volatile("bar.sync 1, %0;" ::"n"(kSvConsumers * 32) : "memory");
+  if (threadIdx.x == 0) {
+    u64 t = 0;
+    for (int k = 0; k < kSvConsumers; k++) t += warp_p[k];
+    if (t) atomicAdd(P, t);
+  }
+}
+
 template <typename F>
 cudaError_t dispatch_order(int order, bool vec, F&& body) {
   switch (order) {
@@ -539,6 +719,24 @@ cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n
     note_launch();
   }
   const size_t smem = (size_t)ne_words * 4;
+  if (ne_words && p.order >= 1 && aligned16(coords)) {
+    // Coordinates streamed through shared memory by bulk copies, one persistent CTA per SM.
+    return dispatch_order(p.order, false, [&]<int O, bool V>() {
+      if constexpr (O == 0) {
+        return cudaErrorInvalidValue;
+      } else {
+        auto kern = groups ? x_survey_bulk_kernel<O, true> : x_survey_bulk_kernel<O, false>;
+        const size_t bytes = sv_ring_bytes<O>() + smem;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        const int64_t nchunks = n / sv_rows<O>();
+        const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, nchunks));
+        kern<<<gb, kSvThreads, bytes, s>>>(coords, vals, n, p, yoff, sv, P, gcnt, status, nonempty, ne_words);
+        note_launch();
+        return cudaGetLastError();
+      }
+    });
+  }
   return dispatch_order(p.order, vec_ok(coords, p.order), [&]<int O, bool V>() {
     auto kern = groups ? x_survey_kernel<O, V, true> : x_survey_kernel<O, V, false>;
     if (smem) {

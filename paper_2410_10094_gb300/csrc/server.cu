@@ -1,10 +1,13 @@
-// A contraction server: requests (each one stc_contract's arguments) are queued, admitted
+// A contraction server: requests (each one stc_contract's arguments) are queued, counted, admitted
 // against a device-memory budget by their exact bound (the product count of Section 4.3
 // gives the output bound before any product is formed), and run in batches by worker
-// threads, each on its own stream, so that batches overlap on the device. Requests that
-// arrive while batches are running join the next batch of a free worker (continuous
-// batching). With `plain` set the server runs one request at a time with stc_contract on
-// one worker: the one-at-a-time baseline on the same arrival trace.
+// threads, each on its own stream, so that batches overlap on the device. Submission only
+// queues a request: a counting thread runs the counting pass of each request in arrival order
+// on its own stream and hands it to the admission queue (one counting thread per worker,
+// taking requests in arrival order). Requests that arrive while batches
+// are running join the next batch of a free worker (continuous batching). With `plain` set the
+// server runs one request at a time with stc_contract on one worker: the one-at-a-time
+// baseline on the same arrival trace.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -37,6 +40,8 @@ struct Ticket {
   uint64_t bytes = 0;  // admission bound
   uint64_t products = 0;  // exact product count
   bool alone = false;     // runs as a plain contraction (its contract keys need renumbering)
+  bool counting = false;  // its counting pass is running
+  bool cancel = false;    // cancelled during its counting pass: finished when that pass ends
   bool done = false;
   stc_status status = STC_OK;
   std::string error;
@@ -51,7 +56,10 @@ struct stc_server {
   stc_server_opts opts{};
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<uint64_t> queue;
+  std::deque<uint64_t> queue;     // counted, waiting for admission
+  std::deque<uint64_t> pending;   // submitted, waiting for the counting pass
+  std::condition_variable cv_count;
+  std::vector<std::thread> counters;  // counting threads, one per worker
   std::map<uint64_t, Ticket> tickets;
   uint64_t next_ticket = 1;
   uint64_t reserved = 0;
@@ -59,8 +67,7 @@ struct stc_server {
   bool stopping = false;
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
-  cudaStream_t count_stream = nullptr;
-  std::mutex count_mu;
+  std::vector<cudaStream_t> count_streams;
   Clock::time_point epoch;
   double now() const { return std::chrono::duration<double>(Clock::now() - epoch).count(); }
 };
@@ -83,6 +90,76 @@ void own_request(Ticket& t, const stc_problem& r) {
     t.oo.assign(r.out_order, r.out_order + (oz > 0 ? oz : 0));
     t.req.out_order = t.oo.data();
     t.has_oo = true;
+  }
+}
+
+// A counting thread: the exact product count and memory bound of the submitted requests it
+// takes (in arrival order), then admission.
+void counter_main(stc_server* sv, int c) {
+  cudaStream_t cs = sv->count_streams[c];
+  cudaSetDevice(ctx_device(sv->ctx));
+  for (;;) {
+    uint64_t id = 0;
+    stc_problem req{};
+    // The request's host arrays are copied: a cancelled ticket may be consumed by its wait
+    // while its counting pass still runs.
+    std::vector<int64_t> xs, ys;
+    std::vector<int32_t> cx, cy;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv_count.wait(lk, [&] { return sv->stopping || !sv->pending.empty(); });
+      if (sv->pending.empty()) return;  // stopping and drained
+      id = sv->pending.front();
+      sv->pending.pop_front();
+      Ticket& t = sv->tickets[id];
+      t.counting = true;
+      req = t.req;
+      xs = t.xshape;
+      ys = t.yshape;
+      cx = t.cx;
+      cy = t.cy;
+      req.X.shape = xs.data();
+      req.Y.shape = ys.data();
+      req.cx = cx.data();
+      req.cy = cy.data();
+      req.out_order = nullptr;
+    }
+    uint64_t P = 0, bytes = 0;
+    const stc_status st = stc_count(sv->ctx, &req.X, &req.Y, req.ncontract, req.cx, req.cy, cs, &P,
+                                     &bytes);
+    const std::string err = st == STC_OK ? std::string() : std::string(stc_last_error());
+    // The batched launch groups Y by contract key directly; a key space above 2^26 is
+    // renumbered to dense ids by the plain path only.
+    unsigned __int128 K = 1;
+    for (int32_t i = 0; i < req.ncontract; i++) {
+      K *= (unsigned __int128)req.X.shape[req.cx[i]];
+      if (K > ((unsigned __int128)1 << 26)) break;
+    }
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      auto it = sv->tickets.find(id);
+      if (it == sv->tickets.end() || it->second.done) continue;
+      Ticket& t = it->second;
+      t.counting = false;
+      if (t.cancel) {  // cancelled while it was counted: its arrays are no longer read
+        t.done = true;
+        t.status = STC_ERR_CANCELLED;
+        t.error = "the request was cancelled before it ran";
+        t.t_start = t.t_done = sv->now();
+      } else if (st != STC_OK) {
+        t.done = true;
+        t.status = st;
+        t.error = err;
+        t.t_start = t.t_done = sv->now();
+      } else {
+        t.bytes = bytes;
+        t.products = P;
+        t.alone = K > ((unsigned __int128)1 << 26);
+        sv->queue.push_back(id);
+      }
+    }
+    sv->cv_done.notify_all();
+    sv->cv_work.notify_one();
   }
 }
 
@@ -204,18 +281,19 @@ stc_status stc_server_create(stc_ctx* ctx, const stc_server_opts* opts, stc_serv
     delete sv;
     return report_error(STC_ERR_INVALID_ARG, "the current device is not the context's device");
   }
-  for (int w = 0; w < sv->opts.workers + 1; w++) {
+  for (int w = 0; w < 2 * sv->opts.workers; w++) {
     cudaStream_t s = nullptr;
     const cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
       for (auto x : sv->streams) cudaStreamDestroy(x);
+      for (auto x : sv->count_streams) cudaStreamDestroy(x);
       delete sv;
       return report_error(STC_ERR_CUDA, cudaGetErrorString(e));
     }
-    if (w < sv->opts.workers) sv->streams.push_back(s);
-    else sv->count_stream = s;
+    (w < sv->opts.workers ? sv->streams : sv->count_streams).push_back(s);
   }
   for (int w = 0; w < sv->opts.workers; w++) sv->workers.emplace_back(worker_main, sv, w);
+  for (int c = 0; c < sv->opts.workers; c++) sv->counters.emplace_back(counter_main, sv, c);
   *out = sv;
   return STC_OK;
 }
@@ -225,24 +303,6 @@ stc_status stc_server_submit(stc_server* sv, const stc_problem* req, uint64_t* t
   const double t_arrive = sv->now();
   Ticket t;
   own_request(t, *req);
-  // Admission bound: the exact product count bounds the output (Section 4.3).
-  {
-    std::lock_guard<std::mutex> lk(sv->count_mu);
-    uint64_t P = 0, bytes = 0;
-    const stc_status st = stc_count(sv->ctx, &t.req.X, &t.req.Y, t.req.ncontract, t.req.cx, t.req.cy,
-                                    sv->count_stream, &P, &bytes);
-    if (st != STC_OK) return st;
-    t.bytes = bytes;
-    t.products = P;
-  }
-  // The batched launch groups Y by contract key directly; a key space above 2^26 is
-  // renumbered to dense ids by the plain path only.
-  unsigned __int128 K = 1;
-  for (int32_t i = 0; i < t.req.ncontract; i++) {
-    K *= (unsigned __int128)t.req.X.shape[t.req.cx[i]];
-    if (K > ((unsigned __int128)1 << 26)) break;
-  }
-  t.alone = K > ((unsigned __int128)1 << 26);
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->stopping) return report_error(STC_ERR_INVALID_ARG, "server is shutting down");
   const uint64_t id = sv->next_ticket++;
@@ -255,9 +315,9 @@ stc_status stc_server_submit(stc_server* sv, const stc_problem* req, uint64_t* t
   tt.req.cx = tt.cx.data();
   tt.req.cy = tt.cy.data();
   tt.req.out_order = tt.has_oo ? tt.oo.data() : nullptr;
-  sv->queue.push_back(id);
+  sv->pending.push_back(id);
   *ticket = id;
-  sv->cv_work.notify_one();
+  sv->cv_count.notify_one();
   return STC_OK;
 }
 
@@ -304,16 +364,29 @@ stc_status stc_server_cancel(stc_server* sv, uint64_t ticket, int32_t* cancelled
     if (it == sv->tickets.end()) return report_error(STC_ERR_INVALID_ARG, "unknown ticket");
     Ticket& t = it->second;
     if (t.done) return STC_OK;
-    // Only a request no worker has taken is still in the queue (it holds no reservation yet).
-    for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q) {
-      if (*q != ticket) continue;
-      sv->queue.erase(q);
+    // Only a request no worker has taken is still queued (it holds no reservation yet): in the
+    // admission queue or in the counting queue; one being counted is finished by the counting
+    // thread when its pass ends (its wait returns only then, its arrays no longer in use).
+    if (t.counting) {
+      t.cancel = true;
+      *cancelled = 1;
+      return STC_OK;
+    }
+    bool taken = true;
+    for (auto* dq : {&sv->queue, &sv->pending}) {
+      for (auto q = dq->begin(); q != dq->end(); ++q) {
+        if (*q != ticket) continue;
+        dq->erase(q);
+        taken = false;
+        break;
+      }
+    }
+    if (!taken) {
       t.done = true;
       t.status = STC_ERR_CANCELLED;
       t.error = "the request was cancelled before it ran";
       t.t_start = t.t_done = sv->now();
       *cancelled = 1;
-      break;
     }
   }
   if (*cancelled) sv->cv_done.notify_all();
@@ -326,13 +399,16 @@ stc_status stc_server_destroy(stc_server* sv) {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->stopping = true;
   }
+  // The counting threads drain the counting queue first, then the workers drain the rest.
+  sv->cv_count.notify_all();
+  for (auto& th : sv->counters) th.join();
   sv->cv_work.notify_all();
   for (auto& th : sv->workers) th.join();
   // Results nobody collected are freed here.
   for (auto& kv : sv->tickets)
     if (kv.second.result) stc_result_free(kv.second.result);
   for (auto s : sv->streams) cudaStreamDestroy(s);
-  if (sv->count_stream) cudaStreamDestroy(sv->count_stream);
+  for (auto s : sv->count_streams) cudaStreamDestroy(s);
   delete sv;
   return STC_OK;
 }

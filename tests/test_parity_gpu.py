@@ -346,3 +346,40 @@ def test_plain_large_full():
     total = float(res.vals.sum())
     # sum over 3.65e8 outputs in any order: within (n-1) u sum|z| of the exact sum
     assert abs(total - float(sx @ sy)) <= 4e8 * 2.0 ** -53 * float(ax @ ay) * 2
+
+
+def test_imbalanced_both_zipf():
+    """Both operands' contract cells Zipf(1.2) (the product-heavy variant of the imbalanced
+    workload). Full size (2e10 products into at most 262,144 outputs): P equal to the count per
+    cell, nnz bounded by the output space, and the checksum's closed form within the bound of
+    a sum of P terms. Output by output against the oracle on a sub-problem of the same tensors:
+    the paired cells at Zipf ranks 8, 12 and 20 (hundreds of terms per output) and every 97th
+    cell, all of their entries."""
+    from fullsize import check_full
+
+    p = W.imbalanced(both_zipf=True)
+    cx = p.X.coords[:, 1].astype(np.int64) * 512 + p.X.coords[:, 2]
+    cy = p.Y.coords[:, 0].astype(np.int64) * 512 + p.Y.coords[:, 1]
+    nxc = np.bincount(cx, minlength=512 * 512)
+    nyc = np.bincount(cy, minlength=512 * 512)
+    res = gpu_contract(p, operands=0)
+    assert res.stats.products == int((nxc * nyc).sum())
+    assert 0 < res.nnz <= 4096 * 64
+    sx = np.bincount(cx, weights=p.X.vals, minlength=512 * 512)
+    sy = np.bincount(cy, weights=p.Y.vals, minlength=512 * 512)
+    ax = np.bincount(cx, weights=np.abs(p.X.vals), minlength=512 * 512)
+    ay = np.bincount(cy, weights=np.abs(p.Y.vals), minlength=512 * 512)
+    total = float(res.vals.sum())
+    bound = 2 * (res.stats.products + res.nnz) * 2.0 ** -53 * float(ax @ ay)
+    assert abs(total - float(sx @ sy)) <= bound
+    del res
+    by_rank = np.argsort(-nyc, kind="stable")
+    cells = np.concatenate([by_rank[[7, 11, 19]], np.arange(0, 512 * 512, 97)])
+    xi = np.flatnonzero(np.isin(cx, cells))
+    yi = np.flatnonzero(np.isin(cy, cells))
+    sub = W.Problem(p.X.take(xi), p.Y.take(yi), p.cx, p.cy)
+    res = gpu_contract(sub, operands=0)
+    info = check_full(sub, res)
+    print(f"imbalanced_both sample: {info.products} products into {info.outputs} outputs "
+          f"({info.products / max(info.outputs, 1):.0f} per output) against the oracle")
+    assert info.products > 50 * info.outputs
