@@ -53,6 +53,16 @@ typedef enum stc_status {
 typedef struct stc_ctx stc_ctx;
 typedef struct stc_result stc_result;
 
+/* A sparse tensor in key form: each entry's row-major linear index over `shape` (the last
+ * mode fastest) instead of its coordinates, e.g. a result made with stc_opts.output_keys. */
+typedef struct stc_keyed {
+  int32_t order;          /* number of modes, 1..STC_MAX_ORDER */
+  const int64_t* shape;   /* host, [order] */
+  int64_t nnz;            /* 0..STC_MAX_NNZ */
+  const uint64_t* keys;   /* device, [nnz], each < prod(shape) */
+  const double* vals;     /* device, [nnz] */
+} stc_keyed;
+
 /* A COO tensor (Section 2.1.2): nnz (coordinate, value) pairs. Repeated coordinates are
  * allowed and are additive. */
 typedef struct stc_coo {
@@ -112,6 +122,12 @@ typedef struct stc_opts {
                              the distinct output keys overflows; the call sees the overflow
                              (STC_ERR_TABLE_FULL inside the call), discards that attempt and runs
                              the expansion again with the full capacity; stats.retries counts it. */
+  int32_t output_keys;    /* nonzero: the result holds each output entry's key (its row-major linear
+                             index over the output shape, uint64) instead of its coordinates, for
+                             the next contraction of a chain (stc_contract_keyed); needs the
+                             output modes in concatenation order (out_order NULL or identity);
+                             stc_contract and stc_contract_keyed only */
+  int32_t reserved_;      /* set to 0 */
 } stc_opts;
 
 /* Per-call statistics of a finished contraction. */
@@ -358,6 +374,26 @@ stc_status stc_result_free(stc_result* r);
  * the result (device, device and host memory), valid until stc_result_free(r). Nothing is
  * copied. out: host, written. Errors: INVALID_ARG when r or out is NULL. */
 stc_status stc_result_as_coo(const stc_result* r, stc_coo* out);
+
+/* Results made with stc_opts.output_keys: the output keys (device uint64 [nnz], valid until
+ * stc_result_free) and a key-form view of the result for the next contraction of a chain.
+ * keys receives NULL for a result in coordinate form; stc_result_as_keyed returns INVALID_ARG
+ * for one. */
+stc_status stc_result_keys(const stc_result* r, const uint64_t** keys);
+stc_status stc_result_as_keyed(const stc_result* r, stc_keyed* out);
+
+/* Z = X (x) Y (Eq. 2) with X given in key form, as the output of an earlier contraction is
+ * handed to the next one of a chain without being turned into coordinates (the chains of
+ * contractions of Section 5.4). X's contracted modes must be a contiguous block at the end of
+ * its modes (cx[i] = X.order - m + i) or at the start (cx[i] = i): each key then splits, by one
+ * division, into its free part (already the row-major index over X's free modes, carried into
+ * the output key as it is) and its contract part, whose m digits pair with Y's modes cy. The
+ * operands keep their roles (no swap) and the contract key space must fit direct counting
+ * (at most 2^26 keys). Output, options (output_keys included) and errors as stc_contract;
+ * INVALID_ARG also for a contract block that is not contiguous at an end of X's modes. */
+stc_status stc_contract_keyed(stc_ctx* ctx, const stc_keyed* X, const stc_coo* Y, int32_t ncontract,
+                              const int32_t* cx, const int32_t* cy, const int32_t* out_order, const stc_opts* opts,
+                              void* stream, stc_result** out);
 
 #ifdef __cplusplus
 }

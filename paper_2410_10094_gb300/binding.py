@@ -35,6 +35,11 @@ class stc_coo(C.Structure):
                 ("coords", C.c_void_p), ("vals", C.c_void_p)]
 
 
+class stc_keyed(C.Structure):
+    _fields_ = [("order", C.c_int32), ("shape", C.POINTER(C.c_int64)), ("nnz", C.c_int64),
+                ("keys", C.c_void_p), ("vals", C.c_void_p)]
+
+
 class stc_problem(C.Structure):
     _fields_ = [("X", stc_coo), ("Y", stc_coo), ("ncontract", C.c_int32), ("cx", C.POINTER(C.c_int32)),
                 ("cy", C.POINTER(C.c_int32)), ("out_order", C.POINTER(C.c_int32))]
@@ -48,7 +53,8 @@ class stc_server_opts(C.Structure):
 class stc_opts(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double),
                 ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("contract_ids", C.c_int32),
-                ("operands", C.c_int32), ("table_shrink", C.c_int32)]
+                ("operands", C.c_int32), ("table_shrink", C.c_int32), ("output_keys", C.c_int32),
+                ("reserved_", C.c_int32)]
 
 
 class stc_stats(C.Structure):
@@ -82,6 +88,10 @@ EXPORTS = {
                              C.c_int),
     "stc_batch_plan_destroy": ([C.c_void_p], C.c_int),
     "stc_measure_peaks": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "stc_contract_keyed": ([C.c_void_p, C.POINTER(stc_keyed), C.POINTER(stc_coo), C.c_int32, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.POINTER(stc_opts), C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "stc_result_keys": ([C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "stc_result_as_keyed": ([C.c_void_p, C.POINTER(stc_keyed)], C.c_int),
     "stc_count": ([C.c_void_p, C.POINTER(stc_coo), C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p,
                    C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
     "stc_linearize": ([C.c_void_p, C.POINTER(stc_coo), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -197,6 +207,31 @@ def stc_contract(ctx: int, X, Y, cx: Sequence[int], cy: Sequence[int], out_order
     check(load().stc_contract(C.c_void_p(ctx), C.byref(xa.coo), C.byref(ya.coo), len(cx), acx, acy, oo,
                               C.byref(opts) if opts is not None else None, C.c_void_p(_stream_handle(stream)),
                               C.byref(r)))
+    return r.value
+
+
+def stc_contract_keyed(ctx: int, X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None,
+                       opts: stc_opts = None, stream=None) -> int:
+    """Calls stc_contract_keyed; X is (shape, keys, vals) with keys a CUDA int64 tensor holding
+    the uint64 keys, Y is (shape, coords, vals). Returns the stc_result handle."""
+    import torch
+
+    shape, keys, vals = X
+    if keys.numel() and (keys.device.type != "cuda" or keys.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64))
+                         or not keys.is_contiguous()):
+        raise ValueError("keys must be a contiguous CUDA int64 (or uint64) tensor")
+    xs = (C.c_int64 * max(len(shape), 1))(*[int(v) for v in shape])
+    xk = stc_keyed(len(shape), C.cast(xs, C.POINTER(C.c_int64)), int(vals.shape[0]),
+                   C.c_void_p(keys.data_ptr() if keys.numel() else 0), C.c_void_p(vals.data_ptr() if vals.numel() else 0))
+    ya = _CooArg(*Y)
+    if len(cx) != len(cy):
+        raise ValueError("cx and cy must have the same length")
+    acx, acy = _mode_array(cx), _mode_array(cy)
+    oo = _mode_array(out_order) if out_order is not None else None
+    r = C.c_void_p()
+    check(load().stc_contract_keyed(C.c_void_p(ctx), C.byref(xk), C.byref(ya.coo), len(cx), acx, acy, oo,
+                                    C.byref(opts) if opts is not None else None, C.c_void_p(_stream_handle(stream)),
+                                    C.byref(r)))
     return r.value
 
 
@@ -414,10 +449,32 @@ class Result:
         self.stats = Stats(st.products, st.survivors, st.out_capacity, st.table_slots, st.groups, st.strategy,
                            st.launches, st.accumulator, tuple(st.stage_ms[i] for i in range(max(st.nstages, 0))),
                            st.contract_ids, st.swapped, st.retries)
-        self._coords = self._vals = None
+        self._coords = self._vals = self._keys = None
+        kp = C.c_void_p()
+        check(load().stc_result_keys(C.c_void_p(handle), C.byref(kp)))
+        self.keys_form = bool(kp.value)
+
+    @property
+    def keys(self):
+        """Output keys (int64 [nnz], the uint64 row-major indices over ``shape``) of a result made
+        with output_keys; None for a result in coordinate form."""
+        if not self.keys_form:
+            return None
+        if self._keys is None:
+            import torch
+
+            if self.nnz:
+                kp = C.c_void_p()
+                check(load().stc_result_keys(C.c_void_p(self.handle), C.byref(kp)))
+                self._keys = torch.as_tensor(_DeviceArray(self._h, kp.value, (self.nnz,), "<i8"), device="cuda")
+            else:
+                self._keys = torch.empty((0,), dtype=torch.int64, device="cuda")
+        return self._keys
 
     @property
     def coords(self):
+        if self.keys_form:
+            return None
         if self._coords is None:
             import torch
 
@@ -443,23 +500,35 @@ class Result:
 
     @property
     def tensor(self):
-        """(shape, coords, vals): the result as the input of a further contraction (a chain),
-        with no copy; the tensors keep the result's memory alive."""
-        return (tuple(self.shape), self.coords, self.vals)
+        """(shape, coords, vals), or (shape, keys, vals) for a result in key form: the result as
+        the input of a further contraction (a chain; stc_contract_keyed takes the key form), with
+        no copy; the tensors keep the result's memory alive."""
+        return (tuple(self.shape), self.keys if self.keys_form else self.coords, self.vals)
 
 
 
 def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, strategy: int = STRATEGY_AUTO,
              load_factor: float = 0.0, group_load_factor: float = 0.0, accumulator: int = ACC_AUTO,
              contract_ids: int = IDS_AUTO, operands: int = OPERANDS_AUTO, record_times: bool = False,
-             table_shrink: int = 0, stream=None, ctx: Context = None) -> Result:
+             table_shrink: int = 0, output_keys: bool = False, stream=None, ctx: Context = None) -> Result:
     """Z = X (x) Y (Eq. 2) on the GPU. X and Y are (shape, coords, vals) with coords a CUDA
     int32 [nnz, order] tensor and vals a CUDA float64 [nnz] tensor. ``table_shrink`` is the
     fault-injection knob of stc_opts (an undersized first table, retried inside the call)."""
     ctx = ctx or default_context()
     o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor), float(group_load_factor),
-                 int(accumulator), int(contract_ids), int(operands), int(table_shrink))
+                 int(accumulator), int(contract_ids), int(operands), int(table_shrink), 1 if output_keys else 0, 0)
     return Result(stc_contract(ctx.handle, X, Y, cx, cy, out_order, o, stream))
+
+
+def contract_keyed(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, strategy: int = STRATEGY_AUTO,
+                   accumulator: int = ACC_AUTO, output_keys: bool = False, record_times: bool = False, stream=None,
+                   ctx: Context = None) -> Result:
+    """Z = X (x) Y with X in key form, (shape, keys, vals) as Result.tensor gives for a result made
+    with output_keys; X's contracted modes must be its last (or first) len(cx) modes, in order."""
+    ctx = ctx or default_context()
+    o = stc_opts(int(strategy), 1 if record_times else 0, 0.0, 0.0, int(accumulator), IDS_DIRECT, OPERANDS_AS_GIVEN, 0,
+                 1 if output_keys else 0, 0)
+    return Result(stc_contract_keyed(ctx.handle, X, Y, cx, cy, out_order, o, stream))
 
 
 def contract_batch(problems, *, group_load_factor: float = 0.0, record_times: bool = False, stream=None,

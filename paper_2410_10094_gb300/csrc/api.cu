@@ -131,8 +131,9 @@ struct stc_result {
   int64_t nnz = 0;
   int32_t order = 0;
   std::vector<int64_t> shape;
-  int32_t* coords = nullptr;
+  int32_t* coords = nullptr;  // coordinates, or with keys_form the output keys (2 words each)
   double* vals = nullptr;
+  bool keys_form = false;
   std::shared_ptr<DeviceBlock> mem;
   stc_stats stats{};
 };
@@ -225,6 +226,10 @@ struct Arena {
 
 bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
 
+// Output key spaces up to this size take the one-global-table strategy without a host read
+// between the survey and the expansion: table and output sized from F (16 MB of table at most).
+constexpr uint64_t kGlobalFromF = 1ull << 18;
+
 // Moves the listed blocks from an arena into a shared block that results can own.
 std::shared_ptr<DeviceBlock> adopt(Arena& ar, stc_ctx* ctx, cudaStream_t s, std::initializer_list<void*> ptrs) {
   auto blk = std::make_shared<DeviceBlock>();
@@ -253,6 +258,8 @@ struct Plan {
   OutPlan op{};
   uint64_t K = 1, FX = 1, FY = 1, F = 1;
   int32_t oz = 0;
+  int32_t ocols = 0;      // int32 words per output entry: oz, or 2 for a 64-bit output key
+  bool keys_out = false;  // outputs are keys (row-major over the output shape), not coordinates
   std::vector<int64_t> zshape;
 };
 
@@ -271,8 +278,12 @@ stc_status check_coo(const stc_coo* t, const char* name) {
   return STC_OK;
 }
 
+// keys_out: outputs as 64-bit keys. xfree_sizes: when X is the split form of a tensor in key
+// form, the lengths of that tensor's free modes, which the output's X part then has (the split
+// form's free key is already the row-major index over them).
 stc_status make_plan(const stc_coo* X, const stc_coo* Y, int32_t m, const int32_t* cx, const int32_t* cy,
-                     const int32_t* out_order, Plan& pl) {
+                     const int32_t* out_order, Plan& pl, bool keys_out = false,
+                     const std::vector<int64_t>* xfree_sizes = nullptr) {
   STC_TRY(check_coo(X, "X"));
   STC_TRY(check_coo(Y, "Y"));
   if (m < 0 || m > X->order || m > Y->order)
@@ -334,10 +345,21 @@ stc_status make_plan(const stc_coo* X, const stc_coo* Y, int32_t m, const int32_
   pl.F = (uint64_t)F;
 
   // Output: the concatenation (X free, Y free) is row-major in zkey = fX * FY + fY.
-  pl.oz = (int32_t)(xf.size() + yf.size());
+  std::vector<uint64_t> xs;
+  if (xfree_sizes) {
+    unsigned __int128 fx = 1;
+    for (int64_t v : *xfree_sizes) xs.push_back((uint64_t)v), fx *= (unsigned __int128)v;
+    if (fx > (unsigned __int128)pl.FX) return fail(STC_ERR_INVALID_ARG, "free modes do not fit the split key");
+    const unsigned __int128 F2 = fx * pl.FY;
+    if (F2 > (unsigned __int128)(UINT64_MAX - 1)) return fail(STC_ERR_KEY_OVERFLOW, "output key space exceeds 2^64 - 1");
+    pl.F = (uint64_t)F2;
+  } else {
+    for (int a : xf) xs.push_back((uint64_t)X->shape[a]);
+  }
+  pl.oz = (int32_t)(xs.size() + yf.size());
   std::vector<uint64_t> csize(pl.oz), cstr(pl.oz);
-  for (size_t a = 0; a < xf.size(); a++) csize[a] = (uint64_t)X->shape[xf[a]];
-  for (size_t b = 0; b < yf.size(); b++) csize[xf.size() + b] = (uint64_t)Y->shape[yf[b]];
+  for (size_t a = 0; a < xs.size(); a++) csize[a] = xs[a];
+  for (size_t b = 0; b < yf.size(); b++) csize[xs.size() + b] = (uint64_t)Y->shape[yf[b]];
   uint64_t st = 1;
   for (int t = pl.oz - 1; t >= 0; t--) {
     cstr[t] = st;
@@ -381,6 +403,23 @@ stc_status make_plan(const stc_coo* X, const stc_coo* Y, int32_t m, const int32_
     pl.op.dpos[j] = (uint8_t)pos_of[t];
     pl.op.dsh1[j] = (uint8_t)(l < 1 ? l : 1);
     pl.op.dsh2[j] = (uint8_t)(l > 1 ? l - 1 : 0);
+  }
+  pl.ocols = pl.oz;
+  pl.keys_out = keys_out;
+  if (keys_out) {
+    // The key itself, written by every output writer as two 32-bit "coordinates": the low and
+    // the high half of zkey (a power-of-two plan of radix 2^32), i.e. one little-endian uint64.
+    if (!pl.op.ident) return fail(STC_ERR_INVALID_ARG, "output_keys needs the output modes in concatenation order");
+    OutPlan k{};
+    k.order = 2;
+    k.pow2 = 1;
+    k.z32 = 0;
+    k.ident = 1;
+    k.mod[0] = k.mod[1] = 1ull << 32;
+    k.shift[0] = 0;
+    k.shift[1] = 32;
+    pl.op = k;
+    pl.ocols = 2;
   }
   return STC_OK;
 }
@@ -491,6 +530,20 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
     pr.yfk = k64;
   }
   STC_TRY(ar.alloc(&pr.yv, (size_t)nY));
+  // X's arrays too, before any launch: the stages' events then enclose device work, not the
+  // host's allocation calls.
+  pr.sv.count = &pr.ctr->ns;
+  if (groups) STC_TRY(ar.alloc(&pr.gcnt, pl.FX));
+  pr.dense = mode == Survey::kDenseGroups;
+  uint32_t* nonempty = nullptr;
+  if (!pr.dense) {
+    STC_TRY(ar.alloc(&pr.sv.fk, (size_t)nX));
+    if (pr.keep_ck) STC_TRY(ar.alloc(&pr.sv.ck, (size_t)nX));
+    STC_TRY(ar.alloc(&pr.sv.ystart, (size_t)nX));
+    STC_TRY(ar.alloc(&pr.sv.w, (size_t)nX));
+    STC_TRY(ar.alloc(&pr.sv.v, (size_t)nX));
+    if (pl.K <= kNonemptyMaxKeys) STC_TRY(ar.alloc(&nonempty, (size_t)((pl.K + 31) / 32)));
+  }
   STC_CUDA(cudaMemsetAsync(ycnt, 0, bins * sizeof(uint32_t), s));
   STC_CUDA(launch_y_count(Y->coords, nY, pl.ky, ycnt, status, ctx->sms, s));
   STC_CUDA(scan_u32(ycnt, pr.yoff, (int64_t)bins, scr, s));
@@ -499,22 +552,10 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
   tm.mark(0);
 
   // X: find each entry's Y run and count the products exactly (Section 4.3).
-  pr.sv.count = &pr.ctr->ns;
-  if (groups) {
-    STC_TRY(ar.alloc(&pr.gcnt, pl.FX));
-    STC_CUDA(cudaMemsetAsync(pr.gcnt, 0, pl.FX * sizeof(uint32_t), s));
-  }
-  pr.dense = mode == Survey::kDenseGroups;
+  if (groups) STC_CUDA(cudaMemsetAsync(pr.gcnt, 0, pl.FX * sizeof(uint32_t), s));
   if (pr.dense) {
     STC_CUDA(launch_x_count(X->coords, nX, pl.kx, pr.yoff, &pr.ctr->P, pr.gcnt, status, ctx->sms, s));
   } else {
-    STC_TRY(ar.alloc(&pr.sv.fk, (size_t)nX));
-    if (pr.keep_ck) STC_TRY(ar.alloc(&pr.sv.ck, (size_t)nX));
-    STC_TRY(ar.alloc(&pr.sv.ystart, (size_t)nX));
-    STC_TRY(ar.alloc(&pr.sv.w, (size_t)nX));
-    STC_TRY(ar.alloc(&pr.sv.v, (size_t)nX));
-    uint32_t* nonempty = nullptr;
-    if (pl.K <= kNonemptyMaxKeys) STC_TRY(ar.alloc(&nonempty, (size_t)((pl.K + 31) / 32)));
     STC_CUDA(launch_x_survey(X->coords, X->vals, nX, pl.kx, pr.yoff, pl.K, pr.sv, &pr.ctr->P, pr.gcnt, status,
                              nonempty, ctx->sms, s));
   }
@@ -530,13 +571,16 @@ stc_status read_counters(const Prepared& pr, cudaStream_t s, Counters& h) {
 
 // Peak device bytes of the GLOBAL strategy for these counts.
 uint64_t global_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t ns, uint64_t P, double alpha) {
-  const uint64_t target = std::min<uint64_t>(P, pl.F);
+  // Small output key spaces are sized from F itself (no host read of P), with a prefix over nX.
+  const bool from_f = pl.F <= kGlobalFromF;
+  const uint64_t target = from_f ? pl.F : std::min<uint64_t>(P, pl.F);
+  if (from_f) ns = (uint64_t)nX;
   const uint64_t cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)((double)target / alpha) + 1));
   const uint64_t out_cap = std::min(target, cap);
   uint64_t b = sizeof(Counters) + pl.K * 4 * 3 + (uint64_t)scan_scratch_elems((int64_t)pl.K) * 4 + (pl.K + 31) / 32 * 4;
   b += (uint64_t)nY * 16 + (uint64_t)nX * 24;
   b += (ns + 1) * 8 + (uint64_t)scan_scratch_elems((int64_t)ns) * 8;
-  b += cap * 16 + out_cap * (4ull * pl.oz + 8);
+  b += cap * 16 + out_cap * (4ull * pl.ocols + 8);
   return b;
 }
 
@@ -549,7 +593,7 @@ uint64_t grouped_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t P) {
   uint64_t b = sizeof(Counters) + pl.K * 4 * 3 + (uint64_t)scan_scratch_elems((int64_t)pl.K) * 4 + (pl.K + 31) / 32 * 4;
   b += (uint64_t)nY * 16 + (uint64_t)nX * (24 + 16);
   b += pl.FX * (4 * 3) + std::min<uint64_t>(pl.FX, (uint64_t)nX) * 4 * (kMaxClasses + 5);
-  b += out * (4ull * pl.oz + 8);
+  b += out * (4ull * pl.ocols + 8);
   return b;
 }
 
@@ -663,7 +707,7 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   hh.list = b.huge_list;
   hh.off = b.huge_off;
   hh.cap = b.huge_cap;
-  STC_TRY(ar.alloc(&r->coords, out_cap * (size_t)pl.oz));
+  STC_TRY(ar.alloc(&r->coords, out_cap * (size_t)pl.ocols));
   STC_TRY(ar.alloc(&r->vals, out_cap));
   if (hh.count) {
     STC_TRY(ar.alloc(&hh.keys, hg.huge_slots));
@@ -724,7 +768,7 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
     uint32_t* src_pos = nullptr;
     STC_TRY(ar.alloc(&src_pos, (size_t)holes));
     STC_CUDA(launch_stream_fill(sa.rec, sa.nrec, (u64)r->nnz, holes, src_pos, gc->fill_counters, r->coords,
-                                r->vals, pl.oz, &pr.ctr->status, ctx->sms, s));
+                                r->vals, pl.ocols, &pr.ctr->status, ctx->sms, s));
     tm.mark(5);
   }
   r->stats.out_capacity = out_cap;
@@ -1134,6 +1178,7 @@ stc_status batch_finish_eager(stc_ctx* ctx, BatchDev& bd, const stc_opts& o, Are
     STC_TRY(run.alloc(&hh.keys, hg.huge_slots));
     STC_TRY(run.alloc(&hh.vals, hg.huge_slots));
     STC_CUDA(cudaMemsetAsync(hh.keys, 0xff, hg.huge_slots * sizeof(u64), s));
+    STC_CUDA(cudaMemsetAsync(hh.vals, 0, hg.huge_slots * sizeof(double), s));
   }
   const GroupArgs a = batch_group_args(bd);
   if (h.P > 0) {
@@ -1314,6 +1359,12 @@ stc_status plan_run_eager(stc_batch_plan* pl, cudaStream_t s, stc_result** outs)
 
 }  // namespace
 
+namespace {
+stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m, const int32_t* cx,
+                         const int32_t* cy, const int32_t* out_order, const stc_opts* opts, void* stream,
+                         stc_result** out, const std::vector<int64_t>* xfree);
+}  // namespace
+
 extern "C" {
 
 const char* stc_status_string(stc_status s) {
@@ -1385,11 +1436,22 @@ stc_status stc_destroy(stc_ctx* ctx) {
 stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m, const int32_t* cx,
                         const int32_t* cy, const int32_t* out_order, const stc_opts* opts, void* stream,
                         stc_result** out) {
+  return contract_impl(ctx, X, Y, m, cx, cy, out_order, opts, stream, out, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+// stc_contract, and the contraction of the split form of a tensor in key form (xfree: the
+// lengths of that tensor's free modes; the operands then keep their roles).
+stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_t m, const int32_t* cx,
+                         const int32_t* cy, const int32_t* out_order, const stc_opts* opts, void* stream,
+                         stc_result** out, const std::vector<int64_t>* xfree) {
   if (!ctx || !out) return fail(STC_ERR_INVALID_ARG, "ctx or out is NULL");
   *out = nullptr;
-  Plan pl;
-  STC_TRY(make_plan(X, Y, m, cx, cy, out_order, pl));
   const stc_opts o = opts ? *opts : stc_opts{};
+  Plan pl;
+  STC_TRY(make_plan(X, Y, m, cx, cy, out_order, pl, o.output_keys != 0, xfree));
   const double alpha = (o.load_factor > 0.0) ? o.load_factor : 0.5;
   if (!(alpha > 0.0 && alpha <= 0.9)) return fail(STC_ERR_INVALID_ARG, "load_factor %g outside (0, 0.9]", alpha);
   if (o.strategy < 0 || o.strategy > STC_STRATEGY_GROUPED)
@@ -1404,8 +1466,9 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
     return fail(STC_ERR_INVALID_ARG, "unknown operands %d", o.operands);
   if (o.table_shrink < 0 || o.table_shrink > 30)
     return fail(STC_ERR_INVALID_ARG, "table_shrink %d outside 0..30", o.table_shrink);
-  if (o.operands == STC_OPERANDS_SWAPPED ||
-      (o.operands == STC_OPERANDS_AUTO && (uint64_t)Y->nnz > 4 * (uint64_t)X->nnz)) {
+  // A swap permutes the output modes back, so outputs in key form keep the operands as given.
+  if (!xfree && (o.operands == STC_OPERANDS_SWAPPED ||
+                 (o.operands == STC_OPERANDS_AUTO && !o.output_keys && (uint64_t)Y->nnz > 4 * (uint64_t)X->nnz))) {
     // Y (x) X has output modes (Y free, X free); map each requested mode onto that order.
     const int nfx = X->order - m, nfy = Y->order - m;
     std::vector<int32_t> oo(nfx + nfy);
@@ -1419,7 +1482,7 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
     (*out)->stats.swapped = 1;
     return STC_OK;
   }
-  if (use_dense_ids(pl, X, Y, o.contract_ids)) {
+  if (!xfree && use_dense_ids(pl, X, Y, o.contract_ids)) {
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
     Relabelled rl(ctx, static_cast<cudaStream_t>(stream));
@@ -1451,6 +1514,7 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
     r->ctx = ctx;
     r->stream = s;
     r->order = pl.oz;
+    r->keys_form = pl.keys_out;
     r->shape = pl.zshape;
     r->stats.strategy = STC_STRATEGY_GROUPED;
     const stc_status st = contract_grouped(ctx, ar, X, Y, pl, o, s, tm, r);
@@ -1467,6 +1531,60 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
 
   Prepared pr;
   STC_TRY(prepare(ctx, ar, X, Y, pl, Survey::kSurvivors, s, tm, pr));
+  if (pl.F <= kGlobalFromF && o.table_shrink == 0 && X->nnz > 0 && Y->nnz > 0) {
+    // A small output key space: the table and the output are sized from F itself, and P and
+    // the survivor count are read on the device, so the call waits once, at its end.
+    const uint64_t cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)((double)pl.F / alpha) + 1));
+    const uint64_t out_cap = std::min<uint64_t>(pl.F, cap);
+    const int64_t nX = X->nnz;
+    stc_result* r = new stc_result;
+    r->ctx = ctx;
+    r->stream = s;
+    r->order = pl.oz;
+    r->keys_form = pl.keys_out;
+    r->shape = pl.zshape;
+    r->stats.strategy = STC_STRATEGY_GLOBAL;
+    auto run = [&]() -> stc_status {
+      GlobalTable t{};
+      u64 *wpre = nullptr, *wscr = nullptr;
+      STC_TRY(ar.alloc(&t.keys, cap));
+      STC_TRY(ar.alloc(&t.vals, cap));
+      STC_TRY(ar.alloc(&wpre, (size_t)nX + 1));
+      STC_TRY(ar.alloc(&wscr, (size_t)scan_scratch_elems(nX)));
+      STC_TRY(ar.alloc(&r->coords, out_cap * (size_t)pl.ocols));
+      STC_TRY(ar.alloc(&r->vals, out_cap));
+      t.mask = cap - 1;
+      STC_CUDA(cudaMemsetAsync(t.keys, 0xff, cap * sizeof(u64), s));
+      STC_CUDA(cudaMemsetAsync(t.vals, 0, cap * sizeof(double), s));
+      STC_CUDA(scan_u32_u64_dev(pr.sv.w, wpre, nX, &pr.ctr->ns, wscr, s));
+      tm.mark(3);
+      STC_CUDA(launch_expand_global_dev(wpre, &pr.ctr->ns, &pr.ctr->P, pr.sv, static_cast<const u64*>(pr.yfk), pr.yv,
+                                        pl.FY, t, &pr.ctr->status, ctx->sms, s));
+      tm.mark(4);
+      STC_CUDA(launch_compact_global(t, pl.op, r->coords, r->vals, out_cap, &pr.ctr->nz, &pr.ctr->status, ctx->sms,
+                                     s));
+      tm.mark(5);
+      Counters h{};
+      STC_TRY(read_counters(pr, s, h));
+      r->nnz = (int64_t)h.nz;
+      r->stats.products = h.P;
+      r->stats.survivors = h.ns;
+      r->stats.table_slots = cap;
+      r->stats.out_capacity = out_cap;
+      return STC_OK;
+    };
+    const stc_status st = run();
+    if (st != STC_OK) {
+      delete r;
+      return st;
+    }
+    r->mem = adopt(ar, ctx, s, {r->coords, r->vals});
+    tm.collect(r->stats);
+    r->stats.launches = take_launches();
+    ctx->live_results++;
+    *out = r;
+    return STC_OK;
+  }
   Counters h{};
   STC_TRY(read_counters(pr, s, h));
   tm.mark(3);
@@ -1475,6 +1593,7 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
   r->ctx = ctx;
   r->stream = s;
   r->order = pl.oz;
+  r->keys_form = pl.keys_out;
   r->shape = pl.zshape;
   r->stats.products = h.P;
   r->stats.survivors = h.ns;
@@ -1495,7 +1614,7 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
       STC_TRY(ar.alloc(&t.vals, cap));
       STC_TRY(ar.alloc(&wpre, (size_t)h.ns + 1));
       STC_TRY(ar.alloc(&wscr, (size_t)scan_scratch_elems((int64_t)h.ns)));
-      STC_TRY(ar.alloc(&r->coords, out_cap * (size_t)pl.oz));
+      STC_TRY(ar.alloc(&r->coords, out_cap * (size_t)pl.ocols));
       STC_TRY(ar.alloc(&r->vals, out_cap));
       STC_CUDA(scan_u32_u64(pr.sv.w, wpre, (int64_t)h.ns, wscr, s));
       tm.mark(3);
@@ -1542,6 +1661,10 @@ stc_status stc_contract(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32_
 }
 
 
+}  // namespace
+
+extern "C" {
+
 stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* problems, const stc_opts* opts,
                               void* stream, stc_result** outs) {
   if (!ctx || n < 0 || (n > 0 && (!problems || !outs))) return fail(STC_ERR_INVALID_ARG, "bad batch arguments");
@@ -1550,6 +1673,7 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
   const stc_opts o = opts ? *opts : stc_opts{};
   if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
     return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
+  if (o.output_keys) return fail(STC_ERR_UNSUPPORTED, "batches return coordinates (output_keys is for stc_contract)");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1596,6 +1720,7 @@ stc_status stc_batch_plan_create(stc_ctx* ctx, int32_t n, const stc_problem* pro
   const stc_opts o = opts ? *opts : stc_opts{};
   if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
     return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
+  if (o.output_keys) return fail(STC_ERR_UNSUPPORTED, "batches return coordinates (output_keys is for stc_contract)");
   DeviceGuard g(ctx->device);
   if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
   std::unique_ptr<stc_batch_plan> pl(new stc_batch_plan);
@@ -1878,11 +2003,103 @@ stc_status stc_result_stats(const stc_result* r, stc_stats* stats) {
 
 stc_status stc_result_as_coo(const stc_result* r, stc_coo* out) {
   if (!r || !out) return fail(STC_ERR_INVALID_ARG, "NULL argument");
+  if (r->keys_form) return fail(STC_ERR_INVALID_ARG, "the result is in key form (stc_result_as_keyed)");
   out->order = r->order;
   out->shape = r->shape.empty() ? nullptr : r->shape.data();
   out->nnz = r->nnz;
   out->coords = r->coords;
   out->vals = r->vals;
+  return STC_OK;
+}
+
+stc_status stc_result_keys(const stc_result* r, const uint64_t** keys) {
+  if (!r || !keys) return fail(STC_ERR_INVALID_ARG, "NULL argument");
+  *keys = r->keys_form ? reinterpret_cast<const uint64_t*>(r->coords) : nullptr;
+  return STC_OK;
+}
+
+stc_status stc_result_as_keyed(const stc_result* r, stc_keyed* out) {
+  if (!r || !out) return fail(STC_ERR_INVALID_ARG, "NULL argument");
+  if (!r->keys_form) return fail(STC_ERR_INVALID_ARG, "the result holds coordinates, not keys");
+  out->order = r->order;
+  out->shape = r->shape.empty() ? nullptr : r->shape.data();
+  out->nnz = r->nnz;
+  out->keys = reinterpret_cast<const uint64_t*>(r->coords);
+  out->vals = r->vals;
+  return STC_OK;
+}
+
+stc_status stc_contract_keyed(stc_ctx* ctx, const stc_keyed* X, const stc_coo* Y, int32_t m, const int32_t* cx,
+                              const int32_t* cy, const int32_t* out_order, const stc_opts* opts, void* stream,
+                              stc_result** out) {
+  if (!ctx || !out || !X) return fail(STC_ERR_INVALID_ARG, "ctx, X or out is NULL");
+  *out = nullptr;
+  if (X->order < 1 || X->order > STC_MAX_ORDER || !X->shape)
+    return fail(STC_ERR_INVALID_ARG, "X.order = %d outside 1..%d", X->order, STC_MAX_ORDER);
+  if (X->nnz < 0 || X->nnz > STC_MAX_NNZ || (X->nnz > 0 && (!X->keys || !X->vals)))
+    return fail(STC_ERR_INVALID_ARG, "bad X.nnz, keys or vals");
+  if (m < 0 || m > X->order || (m > 0 && (!cx || !cy))) return fail(STC_ERR_INVALID_ARG, "bad contract mode lists");
+  for (int j = 0; j < X->order; j++)
+    if (X->shape[j] < 1 || X->shape[j] > (int64_t)1 << 31)
+      return fail(STC_ERR_INVALID_ARG, "X.shape[%d] = %lld outside 1..2^31", j, (long long)X->shape[j]);
+  // The contracted modes: a contiguous block at the end (or the start) of X's modes, in order.
+  bool trailing = true, leading = true;
+  for (int i = 0; i < m; i++) {
+    trailing = trailing && cx[i] == X->order - m + i;
+    leading = leading && cx[i] == i;
+  }
+  if (!trailing && !leading)
+    return fail(STC_ERR_INVALID_ARG, "X's contracted modes must be its last (or first) %d modes, in order", m);
+  KeySplit ks{};
+  ks.m = m;
+  ks.trailing = trailing ? 1 : 0;
+  unsigned __int128 K = 1, F = 1;
+  std::vector<int64_t> xfree;
+  for (int j = 0; j < X->order; j++) {
+    const bool contracted = trailing ? j >= X->order - m : j < m;
+    if (contracted) K *= (unsigned __int128)X->shape[j];
+    else F *= (unsigned __int128)X->shape[j], xfree.push_back(X->shape[j]);
+  }
+  for (int i = 0; i < m; i++) ks.csize[i] = X->shape[cx[i]];
+  if (K * F > (unsigned __int128)UINT64_MAX) return fail(STC_ERR_KEY_OVERFLOW, "X's key space exceeds 2^64");
+  if (K > kMaxDirectBins) return fail(STC_ERR_UNSUPPORTED, "X's contract key space exceeds 2^26");
+  ks.K = (u64)K;
+  ks.F = (u64)F;
+  ks.FL = std::min<u64>(ks.F, 1ull << 30);
+  const u64 FH = (ks.F + ks.FL - 1) / ks.FL;
+  if (FH > (1ull << 31)) return fail(STC_ERR_UNSUPPORTED, "X's free key space exceeds 2^61");
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return fail(STC_ERR_CUDA, "cannot make device %d current", ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(ctx, s);
+  int32_t* rows = nullptr;
+  uint32_t* status = nullptr;
+  STC_TRY(ar.alloc(&rows, (size_t)X->nnz * (2 + m)));
+  STC_TRY(ar.alloc(&status, 1));
+  STC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  take_launches();
+  STC_CUDA(launch_keyed_split(reinterpret_cast<const u64*>(X->keys), X->nnz, ks, rows, status, ctx->sms, s));
+  const unsigned split_launches = take_launches();
+  // The split form: modes (free / FL, free % FL, contracted modes), its free key the original
+  // free index, paired on its last m modes.
+  std::vector<int64_t> shape2 = {(int64_t)FH, (int64_t)ks.FL};
+  std::vector<int32_t> cx2(m);
+  for (int i = 0; i < m; i++) shape2.push_back(ks.csize[i]), cx2[i] = 2 + i;
+  const stc_coo X2{2 + m, shape2.data(), X->nnz, rows, X->vals};
+  stc_opts o = opts ? *opts : stc_opts{};
+  o.operands = STC_OPERANDS_AS_GIVEN;
+  o.contract_ids = STC_IDS_DIRECT;
+  STC_TRY(contract_impl(ctx, &X2, Y, m, cx2.data(), cy, out_order, &o, stream, out, &xfree));
+  uint32_t h = 0;
+  const cudaError_t e1 = cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, s);
+  const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamSynchronize(s) : e1;
+  const stc_status st = e2 != cudaSuccess ? fail(STC_ERR_CUDA, "%s", cudaGetErrorString(e2)) : status_word(h);
+  if (st != STC_OK) {
+    stc_result_free(*out);
+    *out = nullptr;
+    return st;
+  }
+  (*out)->stats.launches += split_launches;
   return STC_OK;
 }
 

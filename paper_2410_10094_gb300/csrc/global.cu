@@ -40,10 +40,15 @@ __device__ __forceinline__ void table_add(u64* __restrict__ keys, double* __rest
 // survivors' exclusive prefix `wpre`: survivor s owns products [wpre[s], wpre[s+1]), its
 // r-th product pairs it with slot ystart[s] + r of its Y run. Within a tile, thread t
 // handles products t, t+256, ...; consecutive threads read consecutive Y slots.
+// With dP / dns non-null, P and the survivor count are read on the device (the grid then is a
+// persistent one sized by the host without them).
 __global__ void __launch_bounds__(kExThreads) expand_global_kernel(
     const u64* __restrict__ wpre, int64_t ns, u64 P, const u64* __restrict__ sfk, const uint32_t* __restrict__ systart,
     const double* __restrict__ sv, const u64* __restrict__ yfk, const double* __restrict__ yv, u64 FY,
-    GlobalTable t, uint32_t* status) {
+    GlobalTable t, uint32_t* status, const u64* dP, const unsigned* dns) {
+  if (dP) P = *dP;
+  if (dns) ns = (int64_t)*dns;
+  if (P == 0 || ns <= 0) return;
   __shared__ u64 s_pre[kExTile + 1];
   __shared__ int64_t s_lo;
   __shared__ int s_n;
@@ -117,7 +122,17 @@ cudaError_t launch_expand_global(const u64* wpre, int64_t ns, u64 P, Survivors s
   const u64 ntiles = (P + kExTile - 1) / kExTile;
   const u64 cap = (u64)sms * 8;
   const unsigned g = (unsigned)(ntiles < cap ? ntiles : cap);
-  expand_global_kernel<<<g, kExThreads, 0, s>>>(wpre, ns, P, sv.fk, sv.ystart, sv.v, yfk, yv, FY, t, status);
+  expand_global_kernel<<<g, kExThreads, 0, s>>>(wpre, ns, P, sv.fk, sv.ystart, sv.v, yfk, yv, FY, t, status, nullptr,
+                                                nullptr);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_global_dev(const u64* wpre, const unsigned* dns, const u64* dP, Survivors sv, const u64* yfk,
+                                     const double* yv, u64 FY, GlobalTable t, uint32_t* status, int sms,
+                                     cudaStream_t s) {
+  expand_global_kernel<<<(unsigned)sms * 8, kExThreads, 0, s>>>(wpre, 0, 0, sv.fk, sv.ystart, sv.v, yfk, yv, FY, t,
+                                                                status, dP, dns);
   note_launch();
   return cudaGetLastError();
 }

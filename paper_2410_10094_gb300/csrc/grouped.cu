@@ -1546,8 +1546,9 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
         if (!one_chunk) __syncthreads();
       }
       if (Pq == 0) continue;
-      // First products' stores and repeats' records are visible device-wide past this point.
-      __threadfence();
+      // The block barrier orders every thread's earlier global stores (first products, repeats'
+      // records) before the later reads and atomics of the block's threads, which are the only
+      // ones that touch this group's reservation; no device-wide fence is needed.
       __syncthreads();
       const uint32_t nkeys = s_cnt & 0xffffu, reps = s_cnt >> 16;
       if (reps) {

@@ -18,6 +18,10 @@ int64_t scan_scratch_elems(int64_t n);
 cudaError_t scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* scratch, cudaStream_t s);
 cudaError_t scan_u32_u64(const uint32_t* in, u64* out, int64_t n, u64* scratch, cudaStream_t s);
 cudaError_t scan_u64(const u64* in, u64* out, int64_t n, u64* scratch, cudaStream_t s);
+// scan_u32_u64 over the first min(*dn, nmax) elements, the count read on the device (the grid
+// and scratch sized for nmax); out[min(*dn, nmax)] = total.
+cudaError_t scan_u32_u64_dev(const uint32_t* in, u64* out, int64_t nmax, const unsigned* dn, u64* scratch,
+                             cudaStream_t s);
 
 // ------------------------------------------------------------------ preparation (prep.cu)
 // Contract key of every entry (the LN key of the contract modes): keys[i] = ckey(i).
@@ -68,6 +72,17 @@ cudaError_t launch_x_scatter_dense(const int32_t* coords, const double* vals, in
                                    const uint32_t* yoff, uint32_t* gcur, GroupedX gx, uint32_t* status, int sms,
                                    cudaStream_t s);
 
+// A tensor in key form split into (free part / FL, free part % FL, contract digits): see
+// keyed_split_kernel. K and F are the contract and free key spaces (K * F = prod(shape)).
+struct KeySplit {
+  u64 K, F, FL;
+  int32_t m;
+  int32_t trailing;  // contracted modes last (1) or first (0)
+  int64_t csize[kMaxOrder];
+};
+cudaError_t launch_keyed_split(const u64* keys, int64_t n, const KeySplit& ks, int32_t* out, uint32_t* status,
+                               int sms, cudaStream_t s);
+
 // ------------------------------------------------------------------ dense ids (ids.cu)
 // Distinct keys collected in an open-addressing table and numbered densely (Section 4.1.2).
 // keys[slots] (all-ones = empty), flags[slots + 1] (flags[slots] = the all-ones key was
@@ -106,6 +121,11 @@ struct GlobalTable {
 cudaError_t launch_expand_global(const u64* wpre, int64_t ns, u64 P, Survivors sv, const u64* yfk,
                                  const double* yv, u64 FY, GlobalTable t, uint32_t* status, int sms,
                                  cudaStream_t s);
+// The same with P and the survivor count read on the device (no host read between the survey
+// and the expansion).
+cudaError_t launch_expand_global_dev(const u64* wpre, const unsigned* dns, const u64* dP, Survivors sv, const u64* yfk,
+                                     const double* yv, u64 FY, GlobalTable t, uint32_t* status, int sms,
+                                     cudaStream_t s);
 // Occupied slots -> COO output (coordinates decoded from the key).
 cudaError_t launch_compact_global(GlobalTable t, const OutPlan& op, int32_t* coords, double* vals,
                                   u64 out_cap, u64* nz, uint32_t* status, int sms, cudaStream_t s);

@@ -457,13 +457,13 @@ __global__ void __launch_bounds__(kThreads, kXMinBlocks) x_scatter_dense_kernel(
 // contract key has a Y run (bitmap in shared memory) are appended to the survivor list as in
 // x_survey_kernel. Needs 16-byte aligned coordinates and K <= kNonemptyMaxKeys.
 #ifndef SV_CONSUMERS
-#define SV_CONSUMERS 16
+#define SV_CONSUMERS 24
 #endif
 #ifndef SV_STAGES
-#define SV_STAGES 6
+#define SV_STAGES 4
 #endif
 #ifndef SV_ROWS
-#define SV_ROWS 1024
+#define SV_ROWS 1536
 #endif
 constexpr int kSvConsumers = SV_CONSUMERS;
 constexpr int kSvThreads = (kSvConsumers + 1) * 32;
@@ -629,6 +629,41 @@ __global__ void __launch_bounds__(kSvThreads, 1) x_survey_bulk_kernel(const int3
   }
 }
 
+// The split form of a tensor in key form (chains of contractions): row i = (f / FL, f % FL,
+// c_1 .. c_m), where the key's free part f and contract part c are key / K and key % K when
+// the contracted modes are the last ones, key % F and key / F when they are the first ones,
+// and c_1 .. c_m are c's digits over the contracted modes' lengths, first most significant.
+// The free part stays one number: the row-major index over the free modes.
+__global__ void __launch_bounds__(kThreads) keyed_split_kernel(const u64* __restrict__ keys, int64_t n, KeySplit ks,
+                                                               int32_t* __restrict__ out, uint32_t* status) {
+  const int w = 2 + ks.m;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    const u64 key = keys[i];
+    int32_t* row = out + i * w;
+    if (key / ks.F >= ks.K) {  // outside prod(shape)
+      atomicOr(status, kStatCoordRange);
+      for (int j = 0; j < w; j++) row[j] = 0;
+      continue;
+    }
+    u64 f, c;
+    if (ks.trailing) {
+      f = key / ks.K;
+      c = key - f * ks.K;
+    } else {
+      c = key / ks.F;
+      f = key - c * ks.F;
+    }
+    const u64 fh = f / ks.FL;
+    row[0] = (int32_t)fh;
+    row[1] = (int32_t)(f - fh * ks.FL);
+    for (int j = ks.m - 1; j >= 0; j--) {
+      const u64 q = c / (u64)ks.csize[j];
+      row[2 + j] = (int32_t)(c - q * (u64)ks.csize[j]);
+      c = q;
+    }
+  }
+}
+
 template <typename F>
 cudaError_t dispatch_order(int order, bool vec, F&& body) {
   switch (order) {
@@ -770,6 +805,14 @@ cudaError_t launch_x_scatter_dense(const int32_t* coords, const double* vals, in
     note_launch();
     return cudaGetLastError();
   });
+}
+
+cudaError_t launch_keyed_split(const u64* keys, int64_t n, const KeySplit& ks, int32_t* out, uint32_t* status,
+                               int sms, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  keyed_split_kernel<<<grid_for(n, sms), kThreads, 0, s>>>(keys, n, ks, out, status);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace stc

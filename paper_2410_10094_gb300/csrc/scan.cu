@@ -40,9 +40,12 @@ __device__ T block_exclusive_scan(T v, T& total, T* warp_sums) {
   return before + x - v;
 }
 
+// With `dn` the scan's length is min(*dn, n), read on the device (n bounds it and sizes the
+// grid); tiles past it sum to zero.
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(kThreads) tile_sums_kernel(const TI* __restrict__ in, int64_t n,
-                                                             TO* __restrict__ sums) {
+                                                             TO* __restrict__ sums, const unsigned* dn) {
+  if (dn && (int64_t)*dn < n) n = (int64_t)*dn;
   __shared__ TO warp_sums[kWarps];
   const int64_t base = (int64_t)blockIdx.x * kTile;
   TO acc = 0;
@@ -59,7 +62,8 @@ __global__ void __launch_bounds__(kThreads) tile_sums_kernel(const TI* __restric
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(kThreads) tile_scan_kernel(const TI* __restrict__ in, int64_t n,
                                                              TO* __restrict__ out,
-                                                             const TO* __restrict__ tile_offsets) {
+                                                             const TO* __restrict__ tile_offsets, const unsigned* dn) {
+  if (dn && (int64_t)*dn < n) n = (int64_t)*dn;
   // Padded so that thread t's run of kItems consecutive elements spreads over banks.
   __shared__ TO tile[kTile + kTile / 32];
   __shared__ TO warp_sums[kWarps];
@@ -95,27 +99,31 @@ __global__ void __launch_bounds__(kThreads) tile_scan_kernel(const TI* __restric
     const int64_t i = base + e;
     if (i < n) out[i] = tile[at(e)];
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
+  // The total goes after the last element, written by the tile that holds position n (the
+  // last tile when n is one past its end).
+  if (threadIdx.x == 0 && ((base <= n && n < base + kTile) || (blockIdx.x == gridDim.x - 1 && n >= base + kTile)))
+    out[n] = off + total;
 }
 
 template <typename TI, typename TO>
-cudaError_t exclusive_scan(const TI* in, TO* out, int64_t n, TO* scratch, cudaStream_t s) {
+cudaError_t exclusive_scan(const TI* in, TO* out, int64_t n, TO* scratch, cudaStream_t s,
+                           const unsigned* dn = nullptr) {
   if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(TO), s);
   const int64_t nb = (n + kTile - 1) / kTile;
   if (nb == 1) {
-    tile_scan_kernel<TI, TO><<<1, kThreads, 0, s>>>(in, n, out, nullptr);
+    tile_scan_kernel<TI, TO><<<1, kThreads, 0, s>>>(in, n, out, nullptr, dn);
     note_launch();
     return cudaGetLastError();
   }
   TO* sums = scratch;
   TO* offs = scratch + nb;
-  tile_sums_kernel<TI, TO><<<(unsigned)nb, kThreads, 0, s>>>(in, n, sums);
+  tile_sums_kernel<TI, TO><<<(unsigned)nb, kThreads, 0, s>>>(in, n, sums, dn);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = exclusive_scan<TO, TO>(sums, offs, nb, scratch + 2 * nb + 1, s);
   if (e != cudaSuccess) return e;
-  tile_scan_kernel<TI, TO><<<(unsigned)nb, kThreads, 0, s>>>(in, n, out, offs);
+  tile_scan_kernel<TI, TO><<<(unsigned)nb, kThreads, 0, s>>>(in, n, out, offs, dn);
   note_launch();
   return cudaGetLastError();
 }
@@ -143,6 +151,10 @@ cudaError_t scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* scr
 }
 cudaError_t scan_u32_u64(const uint32_t* in, u64* out, int64_t n, u64* scratch, cudaStream_t s) {
   return exclusive_scan<uint32_t, u64>(in, out, n, scratch, s);
+}
+cudaError_t scan_u32_u64_dev(const uint32_t* in, u64* out, int64_t nmax, const unsigned* dn, u64* scratch,
+                             cudaStream_t s) {
+  return exclusive_scan<uint32_t, u64>(in, out, nmax, scratch, s, dn);
 }
 cudaError_t scan_u64(const u64* in, u64* out, int64_t n, u64* scratch, cudaStream_t s) {
   return exclusive_scan<u64, u64>(in, out, n, scratch, s);

@@ -55,7 +55,7 @@ def test_struct_layouts_match_the_binding(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"stc_coo": B.stc_coo, "stc_problem": B.stc_problem, "stc_opts": B.stc_opts,
-               "stc_stats": B.stc_stats, "stc_server_opts": B.stc_server_opts}
+               "stc_stats": B.stc_stats, "stc_server_opts": B.stc_server_opts, "stc_keyed": B.stc_keyed}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "stc.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')

@@ -142,3 +142,28 @@ def test_batch_autotuned_calls_agree():
             c, v = host(r)
             assert_matches_oracle(c, v, ref)
         del res
+
+
+def test_batch_overflow_groups_twice_in_a_row():
+    """A batch whose groups overflow every shared-memory class, run twice on one context: the
+    second run reuses the pool's memory of the first, so its overflow table must start cleared
+    (keys and values)."""
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(8250)
+    probs = [W.Problem(W.uniform_coo(rng, (3, 50), 3_000), W.uniform_coo(rng, (50, 100_000), 40_000), (1,), (0,)),
+             W.Problem(W.uniform_coo(rng, (4, 30), 2_000), W.uniform_coo(rng, (30, 80_000), 30_000), (1,), (0,))]
+    refs = [oracle.contract(p.X, p.Y, p.cx, p.cy) for p in probs]
+    ctx = stc.Context(0)
+    try:
+        for _ in range(2):
+            res = stc.contract_batch([(to_dev(p.X), to_dev(p.Y), p.cx, p.cy) for p in probs], ctx=ctx)
+            for ref, r in zip(refs, res):
+                c, v = host(r)
+                assert_matches_oracle(c, v, ref)
+            del res, r
+    finally:
+        import gc
+
+        gc.collect()
+        ctx.close()
