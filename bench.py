@@ -413,6 +413,7 @@ def serve_bench(args):
 
     import paper_2410_10094_gb300 as stc
 
+    clk = ClockSampler(0).start()
     torch.cuda.set_device(0)
     stc.load()
     ctx = stc.default_context(0)
@@ -457,6 +458,7 @@ def serve_bench(args):
                 "requests_per_s": len(trace) / span, "products_per_s": products / span, "span_s": span}
 
     warm = run(np.zeros(min(40, R)), plain=False)
+    tw0 = time.time()
     base = run(np.zeros(min(200, R)), plain=True)
     mu_plain = base["requests_per_s"]
     rows = []
@@ -466,6 +468,8 @@ def serve_bench(args):
         plain_r = run(trace, plain=True)
         batch_r = run(trace, plain=False)
         rows.append({"rate_over_mu_plain": f, "lambda_per_s": lam, "plain": plain_r, "served": batch_r})
+    clk.mark(tw0, time.time())
+    clk.stop()
     best = rows[-1]["served"]
     line = {
         "metric": "p50/p99 latency served vs plain", "value": best["p99_ms"], "unit": "ms (p99, highest rate)",
@@ -475,7 +479,7 @@ def serve_bench(args):
         "config": {"workload": f"served: {R} requests, 80% batched-mix pairs, 20% order-4 128^4 pairs with 1e6 nnz "
                                "each contracting 2 modes; Poisson arrivals; 150 GB admission budget",
                    "mu_plain_requests_per_s": mu_plain, "pools": "96 small and 12 large distinct problems"},
-        "rates": rows,
+        "rates": rows, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -567,9 +571,12 @@ def main(argv=None):
     ap.add_argument("--accumulator", type=int, default=0, help="0 auto, 1 hash tables, 2 dense rows")
     ap.add_argument("--contract-ids", type=int, default=0, help="0 auto, 1 direct contract keys, 2 dense ids")
     ap.add_argument("--operands", type=int, default=0, help="0 auto, 1 as given, 2 swapped")
+    ap.add_argument("--probe", type=int, default=0, help="one global table: lanes probing together (0 auto, 1, 4, 8)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="the default workload's line leaves out the other configurations' measurements")
     ap.add_argument("--requests", type=int, default=1000, help="served workload: requests per arrival rate")
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 0.9, 1.2],
                     help="served workload: arrival rates as multiples of the one-at-a-time service rate")
@@ -639,7 +646,8 @@ def main(argv=None):
         def step(record=False):
             return stc.contract(X, Y, p.cx, p.cy, p.out_order, strategy=args.strategy, record_times=record,
                                 group_load_factor=args.group_load_factor, accumulator=args.accumulator,
-                                contract_ids=args.contract_ids, operands=args.operands, stream=stream, ctx=ctx)
+                                contract_ids=args.contract_ids, operands=args.operands, probe=args.probe,
+                                stream=stream, ctx=ctx)
 
     for _ in range(max(args.warmup, 4) if args.workload == "batched" else args.warmup):
         r = step()
@@ -703,27 +711,39 @@ def main(argv=None):
         barrier()
         torch.cuda.synchronize()
         t0 = None
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        parts = np.zeros(3)
         for it in range(args.e2e_steps + 1):  # the first step warms the copies and is not timed
             if it == 1:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
+            evs[0].record(stream)
             Xd = (p.X.shape, hx[0].to("cuda", non_blocking=True), hx[1].to("cuda", non_blocking=True))
             Yd = (p.Y.shape, hy[0].to("cuda", non_blocking=True), hy[1].to("cuda", non_blocking=True))
+            evs[1].record(stream)
             r = stc.contract(Xd, Yd, p.cx, p.cy, p.out_order, strategy=args.strategy,
                              group_load_factor=args.group_load_factor, accumulator=args.accumulator,
-                             contract_ids=args.contract_ids, operands=args.operands, stream=stream, ctx=ctx)
+                             contract_ids=args.contract_ids, operands=args.operands, probe=args.probe,
+                             stream=stream, ctx=ctx)
+            evs[2].record(stream)
             hc[: r.nnz].copy_(r.coords, non_blocking=True)
             hv[: r.nnz].copy_(r.vals, non_blocking=True)
+            evs[3].record(stream)
             torch.cuda.synchronize()
+            if it >= 1:
+                parts += [evs[i].elapsed_time(evs[i + 1]) for i in range(3)]
             del r, Xd, Yd
         dt = time.perf_counter() - t0
+        parts /= args.e2e_steps
         barrier()
         if world > 1:
             t = torch.tensor([dt], device="cuda", dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             dt = float(t.item())
         e2e = {"value": total_products * args.e2e_steps / dt, "unit": "products/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "ms_per_step": 1e3 * dt / args.e2e_steps}
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "ms_per_step": 1e3 * dt / args.e2e_steps,
+               "parts_ms": {"h2d": parts[0], "contract": parts[1], "d2h": parts[2]},
+               "d2h_gbs": d2h / (parts[2] * 1e-3) / 1e9 if parts[2] > 0 else None}
         del hc, hv
 
     if rank != 0:
@@ -796,20 +816,42 @@ def main(argv=None):
                    "l2": l2_note(bytes_in, (4 * oz + 8) * nz), "strategy": args.strategy,
                    "group_load_factor": args.group_load_factor, "accumulator": args.accumulator,
                    "contract_ids_mode": args.contract_ids, "contract_ids": int(cids),
-                   "operands_mode": args.operands, "swapped": int(swp)},
+                   "operands_mode": args.operands, "swapped": int(swp), "probe": args.probe},
         "step_hbm": {"alg_bytes": step_alg, "gbs": step_alg / (step_ms / 1e3) / 1e9,
                      "frac": step_alg / (step_ms / 1e3) / 1e9 / hbm},
         "stage_ms": {n: float(per_step[i]) for i, n in enumerate(stage_names)},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches) * args.steps,
         "sequential_calls": sequential,
-        "batch_plan": ({"runs": plan_stats[0], "graph_replays": plan_stats[1], "group_load_factor": plan_stats[2]}
-                       if plan_stats else None),
+        "batch_plan": ({"runs": plan_stats[0], "graph_replays": plan_stats[1], "group_load_factor": plan_stats[2],
+                        "warp_table_max": plan_stats[3], "expansion_depth": plan_stats[4]} if plan_stats else None),
         "clocks": clk.summary(),
     }
+    if args.workload == "plain_large" and world == 1 and default_opts and not args.no_secondary:
+        line["secondary"] = secondary_workloads()
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def secondary_workloads():
+    """The other configurations' lines, measured in this run (each in a process of its own):
+    the imbalanced contraction (config 3) and the batched workload replayed as one captured
+    graph per step, with the 2,048 sequential calls beside it (config 4)."""
+    out = {}
+    for wl, steps in (("imbalanced", 20), ("batched", 10)):
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", wl, "--steps", str(steps), "--warmup", "4",
+               "--no-e2e", "--no-cpu-baseline", "--no-secondary"]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+            ln = [x for x in r.stdout.splitlines() if x.startswith("{")]
+            d = json.loads(ln[-1]) if ln else {"error": (r.stderr or "")[-300:]}
+        except Exception as e:  # reported, never fatal to the main line
+            d = {"error": repr(e)}
+        keep = ("value", "unit", "ms_per_step", "stage_ms", "roofline", "sequential_calls", "batch_plan", "clocks",
+                "config", "error")
+        out[wl] = {k: d.get(k) for k in keep if k in d}
+    return out
 
 
 if __name__ == "__main__":

@@ -127,7 +127,13 @@ typedef struct stc_opts {
                              the next contraction of a chain (stc_contract_keyed); needs the
                              output modes in concatenation order (out_order NULL or identity);
                              stc_contract and stc_contract_keyed only */
-  int32_t reserved_;      /* set to 0 */
+  int32_t probe;          /* one-global-table strategy: lanes that probe the table together.
+                             0 = AUTO; 1 = every lane probes its own key over single slots
+                             (linear probing, Section 2.3.1); 4 or 8 = warp-cooperative probing:
+                             tiles of that many lanes take their keys in turn and read buckets of
+                             that many consecutive slots, one slot per lane, with one ballot for
+                             the key and one for the first free slot. Other values:
+                             STC_ERR_INVALID_ARG. */
 } stc_opts;
 
 /* Per-call statistics of a finished contraction. */
@@ -215,8 +221,9 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
  * batch run again and again on the same device arrays (their contents may change between
  * runs; the arrays themselves, shapes and mode lists may not). The plan keeps the problems'
  * descriptors and every scratch array on the device. Its first runs are ordinary batches
- * (with stc_opts.group_load_factor 0 they also let the context's autotuner time each
- * candidate load factor for the batch's size bucket); once the load factor is settled the
+ * (with stc_opts.group_load_factor 0 they also let the context's autotuner time each of its
+ * candidates for the batch's size bucket: load factor, group-per-warp granularity, expansion
+ * split); once the choice is settled the
  * whole launch sequence of one run (grouping of Y, survey and grouping of X, binning,
  * placement of every problem's output from its exact bound, accumulation) is captured in one
  * CUDA graph, and every later run replays it: one output allocation of the previous run's
@@ -226,15 +233,18 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
  *     the plan's lifetime); opts as stc_contract_batch.
  *   stc_batch_plan_run: outs host [n], one result per problem, sharing one device block as
  *     stc_contract_batch's do; returns after the run's device work completes.
- *   stc_batch_plan_stats: runs so far, runs that replayed the graph, and the load factor the
- *     graph was captured with (0 before a capture); each pointer may be NULL.
+ *   stc_batch_plan_stats: runs so far, runs that replayed the graph, and the choice the graph
+ *     was captured with (0s before a capture): the group load factor, the largest table a
+ *     group gets in a warp of its own (256 or 1024 slots; larger groups take a CTA), and the
+ *     expansion split (0: the default products per lane per round, 1: half as many). Each
+ *     pointer may be NULL.
  * Errors: as stc_contract_batch; INVALID_ARG for NULL arguments or n < 1. */
 typedef struct stc_batch_plan stc_batch_plan;
 stc_status stc_batch_plan_create(stc_ctx* ctx, int32_t n, const stc_problem* problems, const stc_opts* opts,
                                  stc_batch_plan** out);
 stc_status stc_batch_plan_run(stc_batch_plan* plan, void* stream, stc_result** outs);
 stc_status stc_batch_plan_stats(const stc_batch_plan* plan, int64_t* runs, int64_t* graph_runs,
-                                double* group_load_factor);
+                                double* group_load_factor, int32_t* warp_table_max, int32_t* expansion_depth);
 stc_status stc_batch_plan_destroy(stc_batch_plan* plan);
 
 /* ---------------------------------------------------------------- serving

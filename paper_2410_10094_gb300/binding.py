@@ -54,7 +54,7 @@ class stc_opts(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("record_times", C.c_int32), ("load_factor", C.c_double),
                 ("group_load_factor", C.c_double), ("accumulator", C.c_int32), ("contract_ids", C.c_int32),
                 ("operands", C.c_int32), ("table_shrink", C.c_int32), ("output_keys", C.c_int32),
-                ("reserved_", C.c_int32)]
+                ("probe", C.c_int32)]
 
 
 class stc_stats(C.Structure):
@@ -84,8 +84,8 @@ EXPORTS = {
     "stc_batch_plan_create": ([C.c_void_p, C.c_int32, C.POINTER(stc_problem), C.POINTER(stc_opts),
                                C.POINTER(C.c_void_p)], C.c_int),
     "stc_batch_plan_run": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
-    "stc_batch_plan_stats": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
-                             C.c_int),
+    "stc_batch_plan_stats": ([C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                              C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
     "stc_batch_plan_destroy": ([C.c_void_p], C.c_int),
     "stc_measure_peaks": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "stc_contract_keyed": ([C.c_void_p, C.POINTER(stc_keyed), C.POINTER(stc_coo), C.c_int32, C.c_void_p,
@@ -510,13 +510,16 @@ class Result:
 def contract(X, Y, cx: Sequence[int], cy: Sequence[int], out_order=None, *, strategy: int = STRATEGY_AUTO,
              load_factor: float = 0.0, group_load_factor: float = 0.0, accumulator: int = ACC_AUTO,
              contract_ids: int = IDS_AUTO, operands: int = OPERANDS_AUTO, record_times: bool = False,
-             table_shrink: int = 0, output_keys: bool = False, stream=None, ctx: Context = None) -> Result:
+             table_shrink: int = 0, output_keys: bool = False, probe: int = 0, stream=None,
+             ctx: Context = None) -> Result:
     """Z = X (x) Y (Eq. 2) on the GPU. X and Y are (shape, coords, vals) with coords a CUDA
     int32 [nnz, order] tensor and vals a CUDA float64 [nnz] tensor. ``table_shrink`` is the
-    fault-injection knob of stc_opts (an undersized first table, retried inside the call)."""
+    fault-injection knob of stc_opts (an undersized first table, retried inside the call);
+    ``probe`` the lanes that probe the one global table together (0 auto, 1, 4 or 8)."""
     ctx = ctx or default_context()
     o = stc_opts(int(strategy), 1 if record_times else 0, float(load_factor), float(group_load_factor),
-                 int(accumulator), int(contract_ids), int(operands), int(table_shrink), 1 if output_keys else 0, 0)
+                 int(accumulator), int(contract_ids), int(operands), int(table_shrink), 1 if output_keys else 0,
+                 int(probe))
     return Result(stc_contract(ctx.handle, X, Y, cx, cy, out_order, o, stream))
 
 
@@ -566,10 +569,12 @@ class BatchPlan:
         return [Result(outs[i]) for i in range(self.n)]
 
     def stats(self):
-        """(runs, runs that replayed the captured graph, load factor of the graph or 0)."""
-        r, g, a = C.c_int64(), C.c_int64(), C.c_double()
-        check(load().stc_batch_plan_stats(C.c_void_p(self.handle), C.byref(r), C.byref(g), C.byref(a)))
-        return int(r.value), int(g.value), float(a.value)
+        """(runs, runs that replayed the captured graph, load factor of the graph or 0, largest
+        warp table, expansion split)."""
+        r, g, a, w, d = C.c_int64(), C.c_int64(), C.c_double(), C.c_int32(), C.c_int32()
+        check(load().stc_batch_plan_stats(C.c_void_p(self.handle), C.byref(r), C.byref(g), C.byref(a), C.byref(w),
+                                          C.byref(d)))
+        return int(r.value), int(g.value), float(a.value), int(w.value), int(d.value)
 
     def close(self):
         if self.handle:

@@ -15,12 +15,19 @@
 
 using namespace stc;
 
-// Autotuning of batches (group load factor, which also decides which groups get a warp of
-// their own): per size bucket, each candidate is timed once with CUDA events around the
-// accumulation kernels, read back without a sync on a later call of the same bucket; then
-// the fastest is kept.
-constexpr double kTuneAlpha[] = {0.5, 0.75, 0.9};
-constexpr int kTuneCand = 3;
+// Autotuning of batches: per size bucket, each candidate is timed once with CUDA events around
+// the accumulation kernels, read back without a sync on a later call of the same bucket; then
+// the fastest is kept. A candidate sets three things: the group load factor (table sizes), the
+// largest table a group may get in a warp of its own (group-per-warp granularity: groups above
+// it take a CTA), and the expansion split of the CTA tables (products per lane per round).
+struct TuneChoice {
+  double alpha;
+  int warp_max;  // slots of the largest warp-sized table used (256 or 1024)
+  int depth;     // 0: the default expansion split, 1: half as many products per lane per round
+};
+constexpr TuneChoice kTune[] = {{0.5, 1024, 0}, {0.75, 1024, 0}, {0.9, 1024, 0}, {0.75, 256, 0}, {0.75, 1024, 1}};
+constexpr int kTuneCand = 5;
+constexpr TuneChoice kTuneDefault = {0.75, 1024, 0};
 struct TuneEntry {
   int best = -1;
   float ms[kTuneCand] = {};
@@ -43,11 +50,11 @@ struct stc_ctx {
 
 namespace {
 // Picks the load factor for a batch of this bucket; *measure is the candidate to time (or -1).
-double tune_pick(stc_ctx* ctx, int bucket, int* measure) {
+TuneChoice tune_pick(stc_ctx* ctx, int bucket, int* measure) {
   std::lock_guard<std::mutex> lk(ctx->tune_mu);
   TuneEntry& te = ctx->tune[bucket];
   *measure = -1;
-  if (te.best >= 0) return kTuneAlpha[te.best];
+  if (te.best >= 0) return kTune[te.best];
   // Only candidates whose batch has recorded both events are read: a batch of another thread
   // may still be between picking a candidate and recording its events (an event never
   // recorded reads as complete). A failed read is cleared so that it cannot surface as the
@@ -74,7 +81,7 @@ double tune_pick(stc_ctx* ctx, int bucket, int* measure) {
   }
   if (all) {
     te.best = best;
-    return kTuneAlpha[best];
+    return kTune[best];
   }
   for (int c = 0; c < kTuneCand; c++) {
     if (!te.done[c] && !te.pending[c]) {
@@ -83,7 +90,7 @@ double tune_pick(stc_ctx* ctx, int bucket, int* measure) {
         if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
           cudaGetLastError();
           if (a) cudaEventDestroy(a);
-          return 0.75;  // untimed; the default
+          return kTuneDefault;  // untimed
         }
         te.ev0[c] = a;
         te.ev1[c] = b;
@@ -91,10 +98,10 @@ double tune_pick(stc_ctx* ctx, int bucket, int* measure) {
       *measure = c;
       te.pending[c] = true;
       te.recorded[c] = false;
-      return kTuneAlpha[c];
+      return kTune[c];
     }
   }
-  return 0.75;  // every remaining candidate is still being timed
+  return kTuneDefault;  // every remaining candidate is still being timed
 }
 void tune_mark(stc_ctx* ctx, int bucket, int cand, bool end, cudaStream_t s) {
   if (cand < 0) return;
@@ -229,6 +236,8 @@ bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
 // Output key spaces up to this size take the one-global-table strategy without a host read
 // between the survey and the expansion: table and output sized from F (16 MB of table at most).
 constexpr uint64_t kGlobalFromF = 1ull << 18;
+// Lanes that probe the one global table together when stc_opts.probe is 0.
+constexpr int kDefaultProbe = 1;
 
 // Moves the listed blocks from an arena into a shared block that results can own.
 std::shared_ptr<DeviceBlock> adopt(Arena& ar, stc_ctx* ctx, cudaStream_t s, std::initializer_list<void*> ptrs) {
@@ -515,7 +524,9 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
 
   // Y: count per contract key, exclusive scan, scatter (Section 4.1.1 counting sort).
   uint32_t *ycnt = nullptr, *ycur = nullptr, *scr = nullptr;
-  STC_TRY(ar.alloc(&ycnt, bins));
+  // The Y counts and, past them, the bitmap of contract keys with entries (one clearing).
+  const uint64_t ne_words = (mode != Survey::kDenseGroups && pl.K <= kNonemptyMaxKeys) ? (pl.K + 31) / 32 : 0;
+  STC_TRY(ar.alloc(&ycnt, bins + ne_words));
   STC_TRY(ar.alloc(&pr.yoff, bins + 1));
   STC_TRY(ar.alloc(&ycur, bins));
   STC_TRY(ar.alloc(&scr, (size_t)scan_scratch_elems((int64_t)bins)));
@@ -542,10 +553,10 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
     STC_TRY(ar.alloc(&pr.sv.ystart, (size_t)nX));
     STC_TRY(ar.alloc(&pr.sv.w, (size_t)nX));
     STC_TRY(ar.alloc(&pr.sv.v, (size_t)nX));
-    if (pl.K <= kNonemptyMaxKeys) STC_TRY(ar.alloc(&nonempty, (size_t)((pl.K + 31) / 32)));
+    if (ne_words) nonempty = ycnt + bins;
   }
-  STC_CUDA(cudaMemsetAsync(ycnt, 0, bins * sizeof(uint32_t), s));
-  STC_CUDA(launch_y_count(Y->coords, nY, pl.ky, ycnt, status, ctx->sms, s));
+  STC_CUDA(cudaMemsetAsync(ycnt, 0, (bins + ne_words) * sizeof(uint32_t), s));
+  STC_CUDA(launch_y_count(Y->coords, nY, pl.ky, ycnt, status, ctx->sms, s, nonempty));
   STC_CUDA(scan_u32(ycnt, pr.yoff, (int64_t)bins, scr, s));
   STC_CUDA(cudaMemcpyAsync(ycur, pr.yoff, bins * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   STC_CUDA(launch_y_scatter(Y->coords, Y->vals, nY, pl.ky, ycur, pr.yfk, pr.key32, pr.yv, ctx->sms, s));
@@ -557,7 +568,7 @@ stc_status prepare(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc_coo* Y, 
     STC_CUDA(launch_x_count(X->coords, nX, pl.kx, pr.yoff, &pr.ctr->P, pr.gcnt, status, ctx->sms, s));
   } else {
     STC_CUDA(launch_x_survey(X->coords, X->vals, nX, pl.kx, pr.yoff, pl.K, pr.sv, &pr.ctr->P, pr.gcnt, status,
-                             nonempty, ctx->sms, s));
+                             nonempty, ctx->sms, s, nonempty != nullptr));
   }
   tm.mark(1);
   return STC_OK;
@@ -915,6 +926,7 @@ struct BatchDev {
   u64* offs = nullptr;         // [2n + 2] value and coordinate offsets of a captured run
   BatchLayoutArgs* dargs = nullptr;
   bool wide = false;
+  int depth = 0;  // expansion split of the CTA tables (TuneChoice::depth)
   int64_t total_x = 0, total_y = 0;
   int tune_bucket = 0;
 };
@@ -1054,11 +1066,14 @@ stc_status batch_setup(stc_ctx* ctx, int32_t n, const stc_problem* problems, Are
   return STC_OK;
 }
 
-// Class thresholds of a group load factor: a group of bound t goes to the first class with
-// t <= ga * slots.
-void batch_set_load_factor(BatchDev& bd, double ga) {
+// Class thresholds of a tuning choice: a group of bound t goes to the first class with
+// t <= alpha * slots; with warp_max 256 the 1024-slot warp class takes no groups (its groups go
+// to the CTA classes). depth selects the expansion split of the CTA tables.
+void batch_set_choice(BatchDev& bd, const TuneChoice& ch) {
   const ClassShape* shapes = bd.wide ? kClassShapes64 : kClassShapes32;
-  for (int c = 0; c < bd.b.nclasses; c++) bd.b.tmax[c] = (u64)(ga * shapes[c].slots);
+  for (int c = 0; c < bd.b.nclasses; c++) bd.b.tmax[c] = (u64)(ch.alpha * shapes[c].slots);
+  if (ch.warp_max < 1024) bd.b.tmax[1] = bd.b.tmax[0];
+  bd.depth = ch.depth;
 }
 
 // The batch up to its per-group bins: counters cleared, Y grouped, X surveyed, grouped by
@@ -1184,7 +1199,7 @@ stc_status batch_finish_eager(stc_ctx* ctx, BatchDev& bd, const stc_opts& o, Are
   if (h.P > 0) {
     const bool direct = !bd.wide && sz.maxcap < 0xffffffffull && o.accumulator != STC_ACC_HASH_SCAN;
     tune_mark(ctx, bd.tune_bucket, tune_cand, false, s);
-    STC_CUDA(launch_group_classes(a, bd.wide, direct, bd.b, hg.count, ctx->sms, s));
+    STC_CUDA(launch_group_classes(a, bd.wide, direct, bd.b, hg.count, ctx->sms, s, bd.depth));
     STC_CUDA(launch_group_huge(a, hh, bd.wide, ctx->sms, s));
     tune_mark(ctx, bd.tune_bucket, tune_cand, true, s);
     if (timed) *timed = true;
@@ -1216,7 +1231,7 @@ struct stc_batch_plan {
   std::unique_ptr<Arena> scratch;
   BatchDev bd;
   BatchSizes sizes{};
-  double ga = 0.0;
+  TuneChoice choice{0.0, 1024, 0};  // the settled choice the graph was captured with (alpha 0: none)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned graph_launches = 0;
@@ -1252,7 +1267,7 @@ stc_status plan_capture(stc_batch_plan* pl) {
   pl->h_args->huge_keys = pl->huge_keys;
   pl->h_args->huge_vals = pl->huge_vals;
   pl->h_args->huge_cap = pl->huge_cap;
-  batch_set_load_factor(bd, pl->ga);
+  batch_set_choice(bd, pl->choice);
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->graph) cudaGraphDestroy(pl->graph);
   pl->exec = nullptr;
@@ -1269,7 +1284,7 @@ stc_status plan_capture(stc_batch_plan* pl) {
     const GroupArgs a = batch_group_args(bd);
     const bool direct =
         !bd.wide && pl->sizes.maxcap < 0x7fffffffull && pl->opts.accumulator != STC_ACC_HASH_SCAN;
-    STC_CUDA(launch_group_classes(a, bd.wide, direct, bd.b, nullptr, ctx->sms, ps));
+    STC_CUDA(launch_group_classes(a, bd.wide, direct, bd.b, nullptr, ctx->sms, ps, bd.depth));
     HugeGroups hh{};
     hh.count = kCountOnDevice;
     hh.countp = bd.gc->count + kMaxClasses;
@@ -1308,7 +1323,8 @@ stc_status plan_run_eager(stc_batch_plan* pl, cudaStream_t s, stc_result** outs)
   stc_ctx* ctx = pl->ctx;
   int tune_cand = -1;
   const bool given = pl->opts.group_load_factor > 0.0;
-  const double ga = given ? pl->opts.group_load_factor : tune_pick(ctx, bd.tune_bucket, &tune_cand);
+  const TuneChoice ch =
+      given ? TuneChoice{pl->opts.group_load_factor, 1024, 0} : tune_pick(ctx, bd.tune_bucket, &tune_cand);
   struct TuneGuard {
     stc_ctx* c;
     int b, k;
@@ -1317,7 +1333,7 @@ stc_status plan_run_eager(stc_batch_plan* pl, cudaStream_t s, stc_result** outs)
       if (armed) tune_abort(c, b, k);
     }
   } tune_guard{ctx, bd.tune_bucket, tune_cand};
-  batch_set_load_factor(bd, ga);
+  batch_set_choice(bd, ch);
   Arena run(ctx, s);
   StageTimer tm;
   tm.start(pl->opts.record_times != 0, s);
@@ -1337,16 +1353,20 @@ stc_status plan_run_eager(stc_batch_plan* pl, cudaStream_t s, stc_result** outs)
   common.accumulator = STC_ACC_HASH;
   auto blk = adopt(run, ctx, s, {vals, coords});
   batch_results(ctx, s, bd, blk, vals, coords, voff.data(), coff.data(), hper.data(), common, outs);
-  // Capture once the load factor is settled (given, or the tuner's pick for this bucket).
-  double settled = given ? ga : 0.0;
-  if (!given) {
+  // Capture once the choice is settled (given, or the tuner's pick for this bucket).
+  TuneChoice settled{0.0, 1024, 0};
+  if (given) {
+    settled = ch;
+  } else {
     int probe = -1;
-    const double pick = tune_pick(ctx, bd.tune_bucket, &probe);
+    const TuneChoice pick = tune_pick(ctx, bd.tune_bucket, &probe);
     if (probe < 0) settled = pick;
     else tune_abort(ctx, bd.tune_bucket, probe);
   }
-  if (settled > 0.0 && (!pl->exec || settled != pl->ga || pl->sizes.huge > pl->huge_cap)) {
-    pl->ga = settled;
+  const bool changed = settled.alpha != pl->choice.alpha || settled.warp_max != pl->choice.warp_max ||
+                       settled.depth != pl->choice.depth;
+  if (settled.alpha > 0.0 && (!pl->exec || changed || pl->sizes.huge > pl->huge_cap)) {
+    pl->choice = settled;
     const stc_status st = plan_capture(pl);
     if (st != STC_OK) {
       // The results of this run stand; the plan keeps running with the host in the loop.
@@ -1466,6 +1486,9 @@ stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32
     return fail(STC_ERR_INVALID_ARG, "unknown operands %d", o.operands);
   if (o.table_shrink < 0 || o.table_shrink > 30)
     return fail(STC_ERR_INVALID_ARG, "table_shrink %d outside 0..30", o.table_shrink);
+  if (o.probe != 0 && o.probe != 1 && o.probe != 4 && o.probe != 8)
+    return fail(STC_ERR_INVALID_ARG, "probe %d is none of 0, 1, 4, 8", o.probe);
+  const int probe = o.probe ? o.probe : kDefaultProbe;
   // A swap permutes the output modes back, so outputs in key form keep the operands as given.
   if (!xfree && (o.operands == STC_OPERANDS_SWAPPED ||
                  (o.operands == STC_OPERANDS_AUTO && !o.output_keys && (uint64_t)Y->nnz > 4 * (uint64_t)X->nnz))) {
@@ -1559,7 +1582,7 @@ stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32
       STC_CUDA(scan_u32_u64_dev(pr.sv.w, wpre, nX, &pr.ctr->ns, wscr, s));
       tm.mark(3);
       STC_CUDA(launch_expand_global_dev(wpre, &pr.ctr->ns, &pr.ctr->P, pr.sv, static_cast<const u64*>(pr.yfk), pr.yv,
-                                        pl.FY, t, &pr.ctr->status, ctx->sms, s));
+                                        pl.FY, t, &pr.ctr->status, ctx->sms, s, probe));
       tm.mark(4);
       STC_CUDA(launch_compact_global(t, pl.op, r->coords, r->vals, out_cap, &pr.ctr->nz, &pr.ctr->status, ctx->sms,
                                      s));
@@ -1623,7 +1646,7 @@ stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32
         STC_CUDA(cudaMemsetAsync(t.keys, 0xff, c * sizeof(u64), s));
         STC_CUDA(cudaMemsetAsync(t.vals, 0, c * sizeof(double), s));
         STC_CUDA(launch_expand_global(wpre, (int64_t)h.ns, h.P, pr.sv, static_cast<const u64*>(pr.yfk), pr.yv,
-                                      pl.FY, t, &pr.ctr->status, ctx->sms, s));
+                                      pl.FY, t, &pr.ctr->status, ctx->sms, s, probe));
         tm.mark(4);
         STC_CUDA(launch_compact_global(t, pl.op, r->coords, r->vals, out_cap, &pr.ctr->nz, &pr.ctr->status,
                                        ctx->sms, s));
@@ -1682,7 +1705,8 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
   STC_TRY(batch_setup(ctx, n, problems, ar, s, bd));
   // Load factor: given, or picked by the autotuner for this size bucket (entries, problems).
   int tune_cand = -1;
-  const double ga = o.group_load_factor > 0.0 ? o.group_load_factor : tune_pick(ctx, bd.tune_bucket, &tune_cand);
+  const TuneChoice ch =
+      o.group_load_factor > 0.0 ? TuneChoice{o.group_load_factor, 1024, 0} : tune_pick(ctx, bd.tune_bucket, &tune_cand);
   struct TuneGuard {  // gives a picked candidate back if the batch fails before it is timed
     stc_ctx* c;
     int b, k;
@@ -1691,7 +1715,7 @@ stc_status stc_contract_batch(stc_ctx* ctx, int32_t n, const stc_problem* proble
       if (armed) tune_abort(c, b, k);
     }
   } tune_guard{ctx, bd.tune_bucket, tune_cand};
-  batch_set_load_factor(bd, ga);
+  batch_set_choice(bd, ch);
   StageTimer tm;
   tm.start(o.record_times != 0, s);
   take_launches();
@@ -1814,11 +1838,13 @@ stc_status stc_batch_plan_run(stc_batch_plan* pl, void* stream, stc_result** out
 }
 
 stc_status stc_batch_plan_stats(const stc_batch_plan* pl, int64_t* runs, int64_t* graph_runs,
-                                double* group_load_factor) {
+                                double* group_load_factor, int32_t* warp_table_max, int32_t* expansion_depth) {
   if (!pl) return fail(STC_ERR_INVALID_ARG, "plan is NULL");
   if (runs) *runs = pl->runs;
   if (graph_runs) *graph_runs = pl->graph_runs;
-  if (group_load_factor) *group_load_factor = pl->exec ? pl->ga : 0.0;
+  if (group_load_factor) *group_load_factor = pl->exec ? pl->choice.alpha : 0.0;
+  if (warp_table_max) *warp_table_max = pl->exec ? pl->choice.warp_max : 0;
+  if (expansion_depth) *expansion_depth = pl->exec ? pl->choice.depth : 0;
   return STC_OK;
 }
 

@@ -2000,7 +2000,7 @@ cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, 
 }
 
 cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct, const Bins& b,
-                                 const uint32_t* counts, int sms, cudaStream_t s) {
+                                 const uint32_t* counts, int sms, cudaStream_t s, int depth) {
   cudaError_t e = cudaSuccess;
   // Host counts size the grids (a class without groups is not launched); without them
   // (counts == nullptr) each class kernel runs a full persistent grid and reads its count.
@@ -2010,9 +2010,16 @@ cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct
   if (!wide_keys && direct) {
     if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], d + 0, h[0], sms, s))) return e;
     if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], d + 1, h[1], sms, s))) return e;
-    if ((e = launch_direct_class<4096, 256, 6, 4>(a, b.list[2], d + 2, h[2], sms, s))) return e;
-    if ((e = launch_direct_class<8192, 512, 6, 2>(a, b.list[3], d + 3, h[3], sms, s))) return e;
-    if ((e = launch_direct_class<16384, 1024, 4, 1>(a, b.list[4], d + 4, h[4], sms, s))) return e;
+    // The expansion split: products each lane forms per round before the claims of the round.
+    if (depth == 0) {
+      if ((e = launch_direct_class<4096, 256, 6, 4>(a, b.list[2], d + 2, h[2], sms, s))) return e;
+      if ((e = launch_direct_class<8192, 512, 6, 2>(a, b.list[3], d + 3, h[3], sms, s))) return e;
+      if ((e = launch_direct_class<16384, 1024, 4, 1>(a, b.list[4], d + 4, h[4], sms, s))) return e;
+    } else {
+      if ((e = launch_direct_class<4096, 256, 3, 4>(a, b.list[2], d + 2, h[2], sms, s))) return e;
+      if ((e = launch_direct_class<8192, 512, 3, 2>(a, b.list[3], d + 3, h[3], sms, s))) return e;
+      if ((e = launch_direct_class<16384, 1024, 2, 1>(a, b.list[4], d + 4, h[4], sms, s))) return e;
+    }
   } else if (!wide_keys) {
     if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], d + 0, h[0], sms, s))) return e;
     if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], d + 1, h[1], sms, s))) return e;

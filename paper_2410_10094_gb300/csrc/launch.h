@@ -37,8 +37,10 @@ cudaError_t launch_key_scatter(const u64* keys, int64_t n, u64 k, uint32_t* curs
 
 // Group Y by contract key (Section 4.2): histogram of ckey, then (after a scan) a scatter
 // of each entry's free key and value into its key's run.
+// nonempty (may be null): K/32 words, zeroed by the caller, receive the bitmap of the contract
+// keys that have at least one Y entry.
 cudaError_t launch_y_count(const int32_t* coords, int64_t n, const KeyPlan& p, uint32_t* cnt,
-                           uint32_t* status, int sms, cudaStream_t s);
+                           uint32_t* status, int sms, cudaStream_t s, uint32_t* nonempty = nullptr);
 // yfk receives 32-bit free keys when key32 is set (F_Y < 2^32), 64-bit ones otherwise.
 cudaError_t launch_y_scatter(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
                              uint32_t* cursor, void* yfk, bool key32, double* yv, int sms, cudaStream_t s);
@@ -56,11 +58,12 @@ struct Survivors {
 // With gcnt non-null, also counts survivors per X free key.
 // `nonempty` (K / 32 words of scratch, may be null) is used when K <= kNonemptyMaxKeys: a
 // bitmap of the contract keys that have a Y run, held in shared memory by the survey so that
-// rows without a run skip the lookup.
+// rows without a run skip the lookup; built here from the runs unless nonempty_built (then
+// launch_y_count built it).
 constexpr u64 kNonemptyMaxKeys = 1ull << 18;
 cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
                             const uint32_t* yoff, u64 K, Survivors sv, u64* P, uint32_t* gcnt, uint32_t* status,
-                            uint32_t* nonempty, int sms, cudaStream_t s);
+                            uint32_t* nonempty, int sms, cudaStream_t s, bool nonempty_built = false);
 
 // Dense X (Y runs exist for most contract keys): count entries with a run per X free key
 // and the products, then place them in group order straight from the input, without an
@@ -117,15 +120,17 @@ struct GlobalTable {
   u64 mask;     // cap - 1, cap a power of two
 };
 // Expansion with a merge-path split over the survivors' product prefix `wpre` (ns+1
-// entries, wpre[ns] = P): every CTA takes an equal share of the P products.
+// entries, wpre[ns] = P): every CTA takes an equal share of the P products. probe: lanes that
+// probe the table together (1: each lane alone over slots; 4 or 8: tiles over buckets of that
+// many slots).
 cudaError_t launch_expand_global(const u64* wpre, int64_t ns, u64 P, Survivors sv, const u64* yfk,
                                  const double* yv, u64 FY, GlobalTable t, uint32_t* status, int sms,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int probe);
 // The same with P and the survivor count read on the device (no host read between the survey
 // and the expansion).
 cudaError_t launch_expand_global_dev(const u64* wpre, const unsigned* dns, const u64* dP, Survivors sv, const u64* yfk,
                                      const double* yv, u64 FY, GlobalTable t, uint32_t* status, int sms,
-                                     cudaStream_t s);
+                                     cudaStream_t s, int probe);
 // Occupied slots -> COO output (coordinates decoded from the key).
 cudaError_t launch_compact_global(GlobalTable t, const OutPlan& op, int32_t* coords, double* vals,
                                   u64 out_cap, u64* nz, uint32_t* status, int sms, cudaStream_t s);
@@ -234,9 +239,11 @@ cudaError_t launch_bin_groups(u64 FX, const uint32_t* goff, const uint32_t* gw, 
                               cudaStream_t s);
 // direct: the shared-memory classes may write outputs as keys are first claimed (needs 32-bit
 // keys and output positions below 2^32 in every problem). counts: host copies of the class
-// counts (b.count), used to size the grids, or null when only the device knows them.
+// counts (b.count), used to size the grids, or null when only the device knows them. depth:
+// 0 the default expansion split of the direct CTA tables, 1 half as many products per lane
+// per round.
 cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct, const Bins& b,
-                                 const uint32_t* counts, int sms, cudaStream_t s);
+                                 const uint32_t* counts, int sms, cudaStream_t s, int depth = 0);
 cudaError_t launch_group_huge(const GroupArgs& a, const HugeGroups& h, bool wide_keys, int sms, cudaStream_t s);
 
 // ------------------------------------------------------------------ batches (batch.cu)

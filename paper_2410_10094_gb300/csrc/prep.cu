@@ -71,8 +71,11 @@ constexpr int kXMinBlocks = STC_X_MIN_BLOCKS;
 constexpr bool kStageRows = STC_STAGE_ROWS != 0;
 
 template <int ORDER, bool VEC>
+// With `nonempty` non-null, also sets bit c of it for every contract key c that has an entry
+// (when the first entry of one of its bins is counted): the survey's bitmap of keys with a run.
 __global__ void __launch_bounds__(kThreads) y_count_kernel(const int32_t* __restrict__ coords, int64_t n, KeyPlan p,
-                                                           uint32_t* __restrict__ cnt, uint32_t* status) {
+                                                           uint32_t* __restrict__ cnt, uint32_t* status,
+                                                           uint32_t* __restrict__ nonempty) {
   const int64_t step = (int64_t)gridDim.x * kThreads * kRows;
   for (int64_t base = (int64_t)blockIdx.x * kThreads * kRows + threadIdx.x; base < n; base += step) {
     uint64_t ck[kRows], fk[kRows];
@@ -85,8 +88,16 @@ __global__ void __launch_bounds__(kThreads) y_count_kernel(const int32_t* __rest
     }
 #pragma unroll
     for (int r = 0; r < kRows; r++) {
-      if (!ok[r]) atomicOr(status, kStatCoordRange);
-      else if (ck[r] != kEmpty64) atomicAdd(cnt + ck[r] * p.nseg + (p.nseg > 1 ? (fk[r] >> p.seg_shift) : 0), 1u);
+      if (!ok[r]) {
+        atomicOr(status, kStatCoordRange);
+      } else if (ck[r] != kEmpty64) {
+        uint32_t* const bin = cnt + ck[r] * p.nseg + (p.nseg > 1 ? (fk[r] >> p.seg_shift) : 0);
+        if (nonempty) {
+          if (atomicAdd(bin, 1u) == 0u) atomicOr(nonempty + (ck[r] >> 5), 1u << (ck[r] & 31));
+        } else {
+          atomicAdd(bin, 1u);
+        }
+      }
     }
   }
 }
@@ -448,7 +459,6 @@ __global__ void __launch_bounds__(kThreads, kXMinBlocks) x_scatter_dense_kernel(
   }
 }
 
-// Runs `body.template operator()<ORDER, VEC>()` for the runtime order and alignment.
 // ---- the survey with X's coordinates streamed through shared memory by bulk copies: one
 // persistent CTA per SM, a ring of kSvStages chunks of coordinate rows filled by one producer
 // thread (cp.async.bulk, completion counted on the stage's mbarrier) and consumed by
@@ -478,7 +488,9 @@ __host__ __device__ constexpr size_t sv_ring_bytes() {
   return (size_t)kSvStages * sv_rows<ORDER>() * ORDER * 4;
 }
 
-template <int ORDER, bool GROUPS>
+// KEY32: contract keys below 2^32, formed in 32-bit arithmetic; the free key (64-bit) is formed
+// only for the rows that survive.
+template <int ORDER, bool GROUPS, bool KEY32>
 __global__ void __launch_bounds__(kSvThreads, 1) x_survey_bulk_kernel(const int32_t* __restrict__ coords,
                                                                      const double* __restrict__ vals, int64_t n,
                                                                      KeyPlan p, const uint32_t* __restrict__ yoff,
@@ -564,14 +576,36 @@ __global__ void __launch_bounds__(kSvThreads, 1) x_survey_bulk_kernel(const int3
     __syncwarp();
     held = 0;
   };
+  uint32_t cs32[ORDER > 0 ? ORDER : 1], sz32[ORDER > 0 ? ORDER : 1];
+#pragma unroll
+  for (int j = 0; j < ORDER; j++) {
+    cs32[j] = (uint32_t)p.cstride[j];
+    sz32[j] = (uint32_t)p.size[j];
+  }
   // One row per lane: keys, the range check, the bitmap test, and the append of survivors.
   auto take = [&](const int32_t* c, int64_t row, bool in) {
     uint64_t ck = 0, fk = 0;
     bool live = false;
     if (in) {
-      const bool ok = keys_of<ORDER>(c, p, ck, fk);
+      bool ok;
+      if constexpr (KEY32) {
+        uint32_t k = 0;
+        ok = true;
+#pragma unroll
+        for (int j = 0; j < ORDER; j++) {
+          ok &= (uint32_t)c[j] < sz32[j];
+          k += (uint32_t)c[j] * cs32[j];
+        }
+        ck = k;
+      } else {
+        ok = keys_of<ORDER>(c, p, ck, fk);
+      }
       if (!ok) atomicOr(status, kStatCoordRange);
       live = ok && ((ne[ck >> 5] >> (ck & 31)) & 1u);
+      if (KEY32 && live) {
+#pragma unroll
+        for (int j = 0; j < ORDER; j++) fk += (uint64_t)(uint32_t)c[j] * p.fstride[j];
+      }
     }
     const unsigned m = __ballot_sync(0xffffffffu, live);
     if (live) {
@@ -664,6 +698,7 @@ __global__ void __launch_bounds__(kThreads) keyed_split_kernel(const u64* __rest
   }
 }
 
+// Runs `body.template operator()<ORDER, VEC>()` for the runtime order and alignment.
 template <typename F>
 cudaError_t dispatch_order(int order, bool vec, F&& body) {
   switch (order) {
@@ -716,11 +751,11 @@ cudaError_t launch_key_scatter(const u64* keys, int64_t n, u64 k, uint32_t* curs
 }
 
 cudaError_t launch_y_count(const int32_t* coords, int64_t n, const KeyPlan& p, uint32_t* cnt, uint32_t* status,
-                           int sms, cudaStream_t s) {
+                           int sms, cudaStream_t s, uint32_t* nonempty) {
   if (n <= 0) return cudaSuccess;
   const unsigned g = grid_for((n + kRows - 1) / kRows, sms);
   return dispatch_order(p.order, vec_ok(coords, p.order), [&]<int O, bool V>() {
-    y_count_kernel<O, V><<<g, kThreads, 0, s>>>(coords, n, p, cnt, status);
+    y_count_kernel<O, V><<<g, kThreads, 0, s>>>(coords, n, p, cnt, status, nonempty);
     note_launch();
     return cudaGetLastError();
   });
@@ -743,12 +778,12 @@ cudaError_t launch_y_scatter(const int32_t* coords, const double* vals, int64_t 
 
 cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n, const KeyPlan& p,
                             const uint32_t* yoff, u64 K, Survivors sv, u64* P, uint32_t* gcnt, uint32_t* status,
-                            uint32_t* nonempty, int sms, cudaStream_t s) {
+                            uint32_t* nonempty, int sms, cudaStream_t s, bool nonempty_built) {
   if (n <= 0) return cudaSuccess;
   const unsigned g = grid_for((n + kRows - 1) / kRows, sms);
   const bool groups = gcnt != nullptr;
   const uint32_t ne_words = (nonempty && K <= kNonemptyMaxKeys) ? (uint32_t)((K + 31) / 32) : 0u;
-  if (ne_words) {
+  if (ne_words && !nonempty_built) {
     const unsigned gw = (unsigned)std::min<u64>((ne_words + kThreads - 1) / kThreads, (u64)sms * 8);
     nonempty_kernel<<<gw, kThreads, 0, s>>>(yoff, K, p.nseg, nonempty);
     note_launch();
@@ -760,7 +795,10 @@ cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n
       if constexpr (O == 0) {
         return cudaErrorInvalidValue;
       } else {
-        auto kern = groups ? x_survey_bulk_kernel<O, true> : x_survey_bulk_kernel<O, false>;
+        // 32-bit contract keys when every contract stride and key fits (K <= 2^18 here).
+        const bool k32 = K <= 0xffffffffull;
+        auto kern = groups ? (k32 ? x_survey_bulk_kernel<O, true, true> : x_survey_bulk_kernel<O, true, false>)
+                           : (k32 ? x_survey_bulk_kernel<O, false, true> : x_survey_bulk_kernel<O, false, false>);
         const size_t bytes = sv_ring_bytes<O>() + smem;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;

@@ -48,6 +48,10 @@ __global__ void __launch_bounds__(kThreads) tile_sums_kernel(const TI* __restric
   if (dn && (int64_t)*dn < n) n = (int64_t)*dn;
   __shared__ TO warp_sums[kWarps];
   const int64_t base = (int64_t)blockIdx.x * kTile;
+  if (base >= n) {  // a tile past the end (device-side length): its sum is zero
+    if (threadIdx.x == 0) sums[blockIdx.x] = TO(0);
+    return;
+  }
   TO acc = 0;
 #pragma unroll
   for (int k = 0; k < kItems; k++) {
@@ -69,6 +73,8 @@ __global__ void __launch_bounds__(kThreads) tile_scan_kernel(const TI* __restric
   __shared__ TO warp_sums[kWarps];
   auto at = [](int e) { return e + (e >> 5); };
   const int64_t base = (int64_t)blockIdx.x * kTile;
+  // A tile past the end writes nothing (the tile starting exactly at the end writes the total).
+  if (base > n) return;
 #pragma unroll
   for (int k = 0; k < kItems; k++) {
     const int e = k * kThreads + threadIdx.x;

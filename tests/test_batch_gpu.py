@@ -127,8 +127,9 @@ def test_batched_workload_full():
 
 
 def test_batch_autotuned_calls_agree():
-    """Repeated calls on one size bucket: the autotuner tries each load factor once and then
-    keeps the fastest; every call's results match the oracle."""
+    """Repeated calls on one size bucket: the autotuner tries each of its five candidates once
+    (load factor, largest warp table, expansion split) and then keeps the fastest; every call's
+    results match the oracle."""
     rng = W.rng_for(8400)
     probs = [W.small_pair(rng, nnz_hi=2e3) for _ in range(48)]
     refs = [oracle.contract(p.X, p.Y, p.cx, p.cy) for p in probs]
@@ -136,7 +137,7 @@ def test_batch_autotuned_calls_agree():
 
     ctx = stc.Context(0)
     bp = stc.BatchProblems([(to_dev(p.X), to_dev(p.Y), p.cx, p.cy, p.out_order) for p in probs])
-    for _ in range(5):
+    for _ in range(8):
         res = stc.contract_batch(bp, ctx=ctx)
         for ref, r in zip(refs, res):
             c, v = host(r)

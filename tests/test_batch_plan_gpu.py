@@ -49,8 +49,8 @@ def run_and_check(plan, probs, refs, runs):
 
 @pytest.mark.parametrize("ga", [0.75, 0.0])
 def test_plan_runs_replay_and_match_oracle(ga):
-    """Given load factor: the first run captures; tuned (0): the first three runs time the
-    candidates, then the graph is captured. Every run of either plan matches the oracle."""
+    """Given load factor: the first run captures; tuned (0): the first five runs time the
+    candidates (load factor, warp-table size, expansion split), then the graph is captured. Every run of either plan matches the oracle."""
     import gc
 
     import paper_2410_10094_gb300 as stc
@@ -61,12 +61,13 @@ def test_plan_runs_replay_and_match_oracle(ga):
     plan = stc.BatchPlan([(to_dev(p.X), to_dev(p.Y), p.cx, p.cy, p.out_order) for p in probs],
                          group_load_factor=ga, ctx=ctx)
     try:
-        runs = 6
+        runs = 7
         run_and_check(plan, probs, refs, runs)
-        n_runs, graph_runs, ga_used = plan.stats()
+        n_runs, graph_runs, ga_used, warp_max, depth = plan.stats()
         assert n_runs == runs
-        assert graph_runs >= (runs - 1 if ga else runs - 4)
-        assert ga_used > 0
+        # tuned: one ordinary run per candidate (five), then the capture
+        assert graph_runs >= (runs - 1 if ga else runs - 5)
+        assert ga_used > 0 and warp_max in (256, 1024) and depth in (0, 1)
     finally:
         plan.close()
         gc.collect()
@@ -120,7 +121,7 @@ def test_plan_batched_workload():
     bp = stc.BatchProblems([(to_dev(p.X), to_dev(p.Y), p.cx, p.cy, p.out_order) for p in probs])
     plan = stc.BatchPlan(bp)
     try:
-        for _ in range(5):
+        for _ in range(6):  # five tuning runs (one per candidate), then replays
             res = plan.run()
             del res
         res = plan.run()

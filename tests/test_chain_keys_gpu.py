@@ -106,3 +106,32 @@ def test_key_form_edges():
     # an empty operand
     e = stc.contract_keyed((X.shape, keys[:0], xv[:0]), to_dev(W.uniform_coo(rng, (5, 3), 40)), (2,), (0,))
     assert e.nnz == 0
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_key_form_above_2_32(mode):
+    """Output keys above 2^32 (a 3000 x 2000 x 1000 x 900 output, 5.4e12 keys), written as two
+    32-bit halves, then handed to a contraction over the last two modes (a contract block of
+    9e5 keys split off by one division)."""
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(9720)
+    X = W.uniform_coo(rng, (3000, 2000, 40), 6_000)
+    Y = W.uniform_coo(rng, (40, 1000, 900), 5_000)
+    Wt = W.uniform_coo(rng, (1000, 900, 7), 200_000)
+    z1 = stc.contract(to_dev(X), to_dev(Y), (2,), (0,), output_keys=True, operands=stc.OPERANDS_AS_GIVEN, **mode)
+    assert z1.shape == (3000, 2000, 1000, 900)
+    r1 = oracle.contract(X, Y, (2,), (0,))
+    k1 = np.sort(z1.keys.cpu().numpy().view(np.uint64))
+    assert int(k1[-1]) >= 1 << 32
+    np.testing.assert_array_equal(decode(k1, z1.shape), r1.coords)
+    z2 = stc.contract_keyed(z1.tensor, to_dev(Wt), (2, 3), (0, 1), **mode)  # (3000, 2000, 7)
+    r2 = oracle.contract(coo_of(r1), Wt, (2, 3), (0, 1))
+    a1 = oracle.contract(abs_coo(X), abs_coo(Y), (2,), (0,))
+    a2 = oracle.contract(W.COO(a1.shape, a1.coords, a1.vals), abs_coo(Wt), (2, 3), (0, 1))
+    c, v = result_host(z2)
+    order = np.lexsort(c.T[::-1])
+    c, v = c[order], v[order]
+    assert z2.shape == r2.shape and r2.nnz > 100
+    np.testing.assert_array_equal(c, r2.coords)
+    assert np.all(np.abs(v - r2.vals) <= 3e-12 * a2.vals)

@@ -34,14 +34,15 @@ def _lib():
     stc.load()
 
 
+@pytest.mark.parametrize("probe", [1, 4, 8])
 @pytest.mark.parametrize("shrink", [0, 8])
-def test_undersized_global_table_is_retried(shrink):
+def test_undersized_global_table_is_retried(shrink, probe):
     rng = W.rng_for(9500)
     X = W.uniform_coo(rng, (30, 20, 40), 60_000)
     Y = W.uniform_coo(rng, (40, 25), 3_000)
     p = W.Problem(X, Y, (2,), (0,))
     ref = oracle.contract(p.X, p.Y, p.cx, p.cy)
-    res = gpu_contract(p, strategy=1, table_shrink=shrink)
+    res = gpu_contract(p, strategy=1, table_shrink=shrink, probe=probe)
     c, v = result_host(res)
     assert_matches_oracle(c, v, ref)
     # A table with fewer slots than distinct output keys must overflow and be retried once (a

@@ -11,11 +11,14 @@ from helpers import REL_TOL
 
 pytestmark = pytest.mark.gpu
 
-# one global table; per-X-free-group hash tables (direct output, table scan); bitmap rows for
+# per-X-free-group hash tables (direct output, table scan); bitmap rows for
 # every group; AUTO (bitmap rows for the large groups, hash tables for the small ones)
-MODES = [dict(strategy=1), dict(strategy=2, accumulator=1), dict(strategy=2, accumulator=3),
+# one global table probed lane by lane, and by tiles of 4 and 8 lanes over buckets;
+MODES = [dict(strategy=1, probe=1), dict(strategy=1, probe=4), dict(strategy=1, probe=8),
+         dict(strategy=2, accumulator=1), dict(strategy=2, accumulator=3),
          dict(strategy=2, accumulator=2), dict(strategy=2, accumulator=0)]
-MODE_IDS = ["global", "grouped-hash", "grouped-hash-scan", "grouped-dense", "grouped-auto"]
+MODE_IDS = ["global", "global-coop4", "global-coop8", "grouped-hash", "grouped-hash-scan", "grouped-dense",
+            "grouped-auto"]
 STRATEGIES = [1, 2]
 
 
@@ -167,6 +170,31 @@ def test_grouped_wide_local_keys():
     Y = W.uniform_coo(rng, (7, 70_000, 70_000), 30_000)
     res, ref = check(W.Problem(X, Y, (1,), (0,)))
     assert res.stats.strategy == 2
+
+
+_DENSE_TABLE = {}
+
+
+@pytest.mark.parametrize("probe", [1, 4, 8])
+@pytest.mark.parametrize("lf", [0.25, 0.9])
+def test_global_probe_load_factors(probe, lf):
+    """The one global table sized for load factor 0.25 and 0.9 of its bound P = 1.87e6, with
+    1.37e6 distinct keys: at 0.9 the 2^21 slots end 65% full, so most keys meet
+    occupied slots (or buckets) before their own. Probed lane by lane and by tiles of 4 and 8."""
+    if not _DENSE_TABLE:
+        rng = W.rng_for(6010)
+        X = W.uniform_coo(rng, (2000, 32), 7_735)
+        Y = W.uniform_coo(rng, (32, 2000), 7_735)
+        p = W.Problem(X, Y, (1,), (0,))
+        _DENSE_TABLE["p"] = p
+        _DENSE_TABLE["ref"] = oracle.contract(p.X, p.Y, p.cx, p.cy)
+    p, ref = _DENSE_TABLE["p"], _DENSE_TABLE["ref"]
+    res = gpu_contract(p, strategy=1, probe=probe, load_factor=lf)
+    c, v = result_host(res)
+    assert_matches_oracle(c, v, ref)
+    assert res.stats.strategy == 1 and res.stats.retries == 0
+    assert res.stats.table_slots == (1 << 21 if lf == 0.9 else 1 << 23)
+    assert ref.nnz > 0.6 * (1 << 21)
 
 
 def test_grouped_load_factors_agree():
