@@ -1280,7 +1280,7 @@ stc_status plan_capture(stc_batch_plan* pl) {
     STC_CUDA(cudaMemcpyAsync(bd.dargs, pl->h_args, sizeof(BatchLayoutArgs), cudaMemcpyHostToDevice, ps));
     STC_TRY(batch_front(ctx, bd, ps, tm));
     STC_CUDA(launch_batch_layout(n, bd.per + n, bd.doz, bd.dbo, bd.dargs, bd.offs, &bd.gc->huge_slots,
-                                 bd.gc->count + kMaxClasses, &bd.ctr->status, ps));
+                                 bd.gc->count + kMaxClasses, &bd.ctr->status, ctx->sms, ps));
     const GroupArgs a = batch_group_args(bd);
     const bool direct =
         !bd.wide && pl->sizes.maxcap < 0x7fffffffull && pl->opts.accumulator != STC_ACC_HASH_SCAN;

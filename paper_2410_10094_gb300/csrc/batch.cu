@@ -337,13 +337,20 @@ __global__ void __launch_bounds__(kLayoutThreads) batch_layout_kernel(int n, con
       *huge_count = 0;
     }
   }
-  // Clear the overflow groups' table.
-  if (fits) {
-    const u64 hs = *huge_slots;
-    for (u64 k = threadIdx.x; k < hs; k += kLayoutThreads) {
-      args->huge_keys[k] = kEmpty64;
-      args->huge_vals[k] = 0.0;
-    }
+}
+
+// Clears the slots the overflow groups' table uses in this run (after batch_layout_kernel,
+// which leaves no overflow groups when the run's layout did not fit).
+__global__ void __launch_bounds__(kThreads) batch_clear_huge_kernel(const BatchLayoutArgs* __restrict__ args,
+                                                                    const u64* huge_slots,
+                                                                    const uint32_t* huge_count) {
+  if (*huge_count == 0) return;
+  const u64 hs = *huge_slots < args->huge_cap ? *huge_slots : args->huge_cap;
+  u64* const keys = args->huge_keys;
+  double* const vals = args->huge_vals;
+  for (u64 k = (u64)blockIdx.x * kThreads + threadIdx.x; k < hs; k += (u64)gridDim.x * kThreads) {
+    keys[k] = kEmpty64;
+    vals[k] = 0.0;
   }
 }
 
@@ -399,11 +406,12 @@ cudaError_t launch_batch_group(const BatchArgs& ba, GroupedX gx, const Bins& b, 
 }
 
 cudaError_t launch_batch_layout(int n, const u64* pcap, const int32_t* oz, BatchOut* bo, const BatchLayoutArgs* args,
-                                u64* offs, const u64* huge_slots, uint32_t* huge_count, uint32_t* status,
+                                u64* offs, const u64* huge_slots, uint32_t* huge_count, uint32_t* status, int sms,
                                 cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   batch_layout_kernel<<<1, kLayoutThreads, 0, s>>>(n, pcap, oz, bo, args, offs, huge_slots, huge_count, status);
-  note_launch();
+  batch_clear_huge_kernel<<<(unsigned)sms * 8, kThreads, 0, s>>>(args, huge_slots, huge_count);
+  note_launch(2);
   return cudaGetLastError();
 }
 

@@ -1823,8 +1823,9 @@ cudaError_t launch_warp_class(const GroupArgs& a, const uint32_t* list, const ui
 // (warp-aggregated); after the round's claims are counted, one atomic per round reserves the
 // output positions, and claimers store their entry at base + rank (consecutive lanes,
 // consecutive positions). Products whose key was already present add their value to that
-// entry in global memory after a device-scope fence and a barrier, when the claiming store
-// is visible. No values are kept in shared memory and no table scan writes the output.
+// entry in global memory after a block barrier, which makes the claiming stores of the
+// block's threads visible to the block's later atomics (only this block touches the group's
+// entries). No values are kept in shared memory and no table scan writes the output.
 template <int SLOTS, int THREADS, int D, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) group_direct_kernel(GroupArgs a, const uint32_t* __restrict__ list,
                                                                      const uint32_t* __restrict__ countp) {
@@ -1920,7 +1921,6 @@ __global__ void __launch_bounds__(THREADS, MINB) group_direct_kernel(GroupArgs a
               atomicOr(a.status, kStatOutOverflow);
           }
         }
-        __threadfence();
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < D; u++) {

@@ -303,10 +303,11 @@ struct BatchLayoutArgs {
   u64 huge_cap;        // its slots
 };
 // Places every problem's output region in the run's block from the exact bounds pcap[n]
-// (offs: [n + 1] value offsets, then [n + 1] coordinate offsets, in elements) and clears the
-// overflow table; flags kStatOutOverflow (and places nothing) when the block is too small.
+// (offs: [n + 1] value offsets, then [n + 1] coordinate offsets, in elements), then clears
+// the slots of the overflow table this run uses (a grid of its own); flags kStatOutOverflow
+// (and places nothing) when the block is too small.
 cudaError_t launch_batch_layout(int n, const u64* pcap, const int32_t* oz, BatchOut* bo, const BatchLayoutArgs* args,
-                                u64* offs, const u64* huge_slots, uint32_t* huge_count, uint32_t* status,
+                                u64* offs, const u64* huge_slots, uint32_t* huge_count, uint32_t* status, int sms,
                                 cudaStream_t s);
 cudaError_t launch_batch_group(const BatchArgs& ba, GroupedX gx, const Bins& b, uint32_t* gprob, u64* gfk, int sms,
                                cudaStream_t s);

@@ -488,6 +488,10 @@ __host__ __device__ constexpr size_t sv_ring_bytes() {
   return (size_t)kSvStages * sv_rows<ORDER>() * ORDER * 4;
 }
 
+static_assert(sv_ring_bytes<4>() + kNonemptyMaxKeys / 8 <= 227 * 1024 &&
+                  sv_ring_bytes<8>() + kNonemptyMaxKeys / 8 <= 227 * 1024,
+              "the survey's ring and key bitmap fit one CTA's shared memory");
+
 // KEY32: contract keys below 2^32, formed in 32-bit arithmetic; the free key (64-bit) is formed
 // only for the rows that survive.
 template <int ORDER, bool GROUPS, bool KEY32>
@@ -800,7 +804,12 @@ cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n
         auto kern = groups ? (k32 ? x_survey_bulk_kernel<O, true, true> : x_survey_bulk_kernel<O, true, false>)
                            : (k32 ? x_survey_bulk_kernel<O, false, true> : x_survey_bulk_kernel<O, false, false>);
         const size_t bytes = sv_ring_bytes<O>() + smem;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        // The limit is a property of the kernel, shared by every thread that launches it, so it
+        // is set to the largest size any launch uses (the bitmap of kNonemptyMaxKeys keys), not
+        // to this launch's: threads of a server launching with different key spaces at once
+        // would otherwise lower it under one another's launches.
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sv_ring_bytes<O>() + kNonemptyMaxKeys / 8));
         if (e != cudaSuccess) return e;
         const int64_t nchunks = n / sv_rows<O>();
         const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, nchunks));
@@ -812,8 +821,9 @@ cudaError_t launch_x_survey(const int32_t* coords, const double* vals, int64_t n
   }
   return dispatch_order(p.order, vec_ok(coords, p.order), [&]<int O, bool V>() {
     auto kern = groups ? x_survey_kernel<O, V, true> : x_survey_kernel<O, V, false>;
-    if (smem) {
-      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem) {  // the largest size any launch uses, as above
+      const cudaError_t e =
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kNonemptyMaxKeys / 8));
       if (e != cudaSuccess) return e;
     }
     kern<<<g, kThreads, smem, s>>>(coords, vals, n, p, yoff, sv, P, gcnt, status, nonempty, ne_words);
