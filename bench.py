@@ -836,20 +836,25 @@ def main(argv=None):
 
 def secondary_workloads():
     """The other configurations' lines, measured in this run (each in a process of its own):
-    the imbalanced contraction (config 3) and the batched workload replayed as one captured
-    graph per step, with the 2,048 sequential calls beside it (config 4)."""
+    the imbalanced contraction (config 3), the batched workload replayed as one captured graph
+    per step with the 2,048 sequential calls beside it (config 4), and a short served trace
+    (config 5: 2,000 requests at the plain server's own rate; the full 20,000-request sweep over
+    six rates is `--workload served --requests 20000`)."""
     out = {}
-    for wl, steps in (("imbalanced", 20), ("batched", 10)):
+    for wl, steps in (("imbalanced", 20), ("batched", 10), ("served", 0)):
         cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", wl, "--steps", str(steps), "--warmup", "4",
                "--no-e2e", "--no-cpu-baseline", "--no-secondary"]
+        if wl == "served":
+            cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "served", "--requests", "2000",
+                   "--rates", "1.0", "--warmup", "3", "--no-secondary"]
         try:
             r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
             ln = [x for x in r.stdout.splitlines() if x.startswith("{")]
             d = json.loads(ln[-1]) if ln else {"error": (r.stderr or "")[-300:]}
         except Exception as e:  # reported, never fatal to the main line
             d = {"error": repr(e)}
-        keep = ("value", "unit", "ms_per_step", "stage_ms", "roofline", "sequential_calls", "batch_plan", "clocks",
-                "config", "error")
+        keep = ("metric", "value", "unit", "ms_per_step", "stage_ms", "roofline", "sequential_calls", "batch_plan",
+                "rates", "clocks", "config", "error")
         out[wl] = {k: d.get(k) for k in keep if k in d}
     return out
 

@@ -349,8 +349,10 @@ stc_status stc_dense_ids(stc_ctx* ctx, const uint64_t* keys, int64_t n, uint32_t
  *   - Limit: k <= 262144 (2^18) and n <= STC_MAX_NNZ; a larger k returns
  *     STC_ERR_INVALID_ARG with a message naming the limit.
  *   - It runs on the caller's current device. The first call on a device looks up the
- *     array's device address (set-up); make that first call before capturing any stream.
- *     If the look-up fails the call returns STC_ERR_CUDA and the next call tries again.
+ *     array's device address (set-up). If the look-up fails the call returns STC_ERR_CUDA
+ *     and the next call tries again.
+ *   - No call can be captured into a CUDA graph: every call reads its status word back to
+ *     the host and waits for its stream (below).
  *   - All calls on a device share the one array. The call clears what must start at zero,
  *     but calls whose work overlaps on the GPU (other streams, other host threads) race on
  *     it: serialise them.

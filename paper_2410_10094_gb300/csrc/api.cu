@@ -1022,6 +1022,7 @@ stc_status batch_setup(stc_ctx* ctx, int32_t n, const stc_problem* problems, Are
     uint32_t* k = nullptr;
     STC_TRY(ar.alloc(&k, (size_t)total_y));
     ba.yfk = k;
+    STC_TRY(ar.alloc(&ba.yuniq, (size_t)std::max<int64_t>(total_y, 1)));
   } else {
     u64* k = nullptr;
     STC_TRY(ar.alloc(&k, (size_t)total_y));
@@ -1107,6 +1108,7 @@ GroupArgs batch_group_args(const BatchDev& bd) {
   a.bnz = bd.per + 2 * bd.n;
   a.gprob = bd.gprob;
   a.gfk = bd.gfk;
+  a.yuniq = bd.ba.yuniq;
   return a;
 }
 

@@ -86,6 +86,55 @@ __global__ void __launch_bounds__(kThreads) y_scatter_batch_kernel(const BatchPr
   }
 }
 
+// Marks the Y runs (the entries of one contract-key bin) whose free keys are all different:
+// yuniq[first entry of the run] = 1, else 0. One warp per run, with a table of kUniqSlots keys
+// in shared memory (linear probing, one compare-and-swap per entry); runs longer than half the
+// table are left at 0 and keep the table path. The table is cleared after every run.
+constexpr int kUniqWarps = 8;
+constexpr uint32_t kUniqSlots = 1024;
+__global__ void __launch_bounds__(kUniqWarps * 32) run_unique_kernel(const uint32_t* __restrict__ yoff, u64 bins,
+                                                                    const uint32_t* __restrict__ yfk,
+                                                                    uint8_t* __restrict__ yuniq) {
+  __shared__ __align__(16) uint32_t tab[kUniqWarps][kUniqSlots];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  uint32_t* const t = tab[warp];
+  for (uint32_t i = lane; i < kUniqSlots / 4; i += 32)
+    reinterpret_cast<uint4*>(t)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+  __syncwarp();
+  for (u64 b = (u64)blockIdx.x * kUniqWarps + warp; b < bins; b += (u64)gridDim.x * kUniqWarps) {
+    const uint32_t s0 = yoff[b], len = yoff[b + 1] - s0;
+    if (len <= 1) {
+      if (len == 1 && lane == 0) yuniq[s0] = 1;
+      continue;
+    }
+    if (len > kUniqSlots / 2) {
+      if (lane == 0) yuniq[s0] = 0;
+      continue;
+    }
+    bool dup = false;
+    for (uint32_t j = lane; j < len; j += 32) {
+      const uint32_t key = yfk[s0 + j];
+      uint32_t h = (key * 0x9E3779B1u) >> 22;  // 10 bits: kUniqSlots slots
+      for (uint32_t probe = 0; probe < kUniqSlots; probe++) {
+        const uint32_t prev = atomicCAS(t + h, kEmpty32, key);
+        if (prev == kEmpty32) break;
+        if (prev == key) {
+          dup = true;
+          break;
+        }
+        h = (h + 1) & (kUniqSlots - 1);
+      }
+    }
+    const bool any = __any_sync(0xffffffffu, dup);
+    if (lane == 0) yuniq[s0] = any ? 0 : 1;
+    __syncwarp();
+    for (uint32_t i = lane; i < kUniqSlots / 4; i += 32)
+      reinterpret_cast<uint4*>(t)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+    __syncwarp();
+  }
+}
+static_assert(kUniqSlots == 1024, "the hash above takes 10 bits");
+
 // Survivors of all problems: their combined group key fxoff[p] + fX, Y run, value; the
 // product count per problem and in total.
 __global__ void __launch_bounds__(kThreads) x_survey_batch_kernel(const BatchProb* __restrict__ pb,
@@ -371,10 +420,16 @@ cudaError_t launch_batch_prepare(const BatchArgs& ba, int sms, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   if (ba.total_y > 0) {
-    if (ba.key32)
+    if (ba.key32) {
       y_scatter_batch_kernel<uint32_t><<<grid_for(ba.total_y, sms), kThreads, 0, s>>>(
           ba.pb, ba.yrow, ba.n, ba.total_y, ba.ycur, static_cast<uint32_t*>(ba.yfk), ba.yv);
-    else
+      if (ba.yuniq && ba.bins) {
+        const u64 want = (ba.bins + kUniqWarps - 1) / kUniqWarps, cap = (u64)sms * 8;
+        run_unique_kernel<<<(unsigned)(want < cap ? want : cap), kUniqWarps * 32, 0, s>>>(
+            ba.yoff, ba.bins, static_cast<const uint32_t*>(ba.yfk), ba.yuniq);
+        note_launch();
+      }
+    } else
       y_scatter_batch_kernel<u64><<<grid_for(ba.total_y, sms), kThreads, 0, s>>>(
           ba.pb, ba.yrow, ba.n, ba.total_y, ba.ycur, static_cast<u64*>(ba.yfk), ba.yv);
     note_launch();

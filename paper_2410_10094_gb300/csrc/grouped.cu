@@ -1683,6 +1683,29 @@ __global__ void __launch_bounds__(WARPS * 32) group_warp_kernel(GroupArgs a, con
   for (uint32_t k = blockIdx.x * WARPS + warp; k < count; k += gridDim.x * WARPS) {
     const uint32_t g = list[k];
     const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
+    if (a.yuniq != nullptr && x1 - x0 == 1 && a.yuniq[a.gx.ystart[x0]]) {
+      // One X entry over a run of all-different free keys: every product is an output of its
+      // own, written as the run scaled by x, without the table.
+      const uint32_t ys = a.gx.ystart[x0], len = a.gx.w[x0];
+      const double xv = a.gx.v[x0];
+      if (lane == 0) resolve_target(a, g, len, ws.tg);
+      __syncwarp();
+      for (uint32_t j = lane; j < len; j += 32) {
+        u64 key;
+        if constexpr (sizeof(KT) == 4)
+          key = ld_keep_u32(static_cast<const uint32_t*>(a.yfk) + ys + j, keep);
+        else
+          key = ld_keep_u64(static_cast<const uint64_t*>(a.yfk) + ys + j, keep);
+        const double prod = __dmul_rn(xv, ld_keep_f64(a.yv + ys + j, keep));
+        const u64 pos = ws.tg.base + j;
+        if (pos < ws.tg.cap)
+          store_output(ws.tg.coords, ws.tg.vals, pos, ws.tg.zrow + key, prod, ws.tg.op, pol);
+        else
+          atomicOr(a.status, kStatOutOverflow);
+      }
+      __syncwarp();  // ws.tg is rewritten for the next group
+      continue;
+    }
     unsigned claims = 0;
     for (uint32_t c0 = x0; c0 < x1; c0 += 32) {
       const uint32_t n = (x1 - c0 < 32u) ? x1 - c0 : 32u;
@@ -1817,6 +1840,168 @@ cudaError_t launch_warp_class(const GroupArgs& a, const uint32_t* list, const ui
   return cudaGetLastError();
 }
 
+
+// ---- small groups with direct output: one warp per group, each warp with its own table of
+// 32-bit keys and output positions (no values in shared memory). A product that claims a new
+// key writes its output entry at once: the round's claims are counted with ballots, one
+// atomic on the problem's output counter reserves their positions, and consecutive claimers
+// store at consecutive positions. Products whose key is already claimed add their value to
+// that entry in global memory after the warp synchronises, which makes the claiming stores of
+// the warp's lanes visible to its later atomics (only this warp touches the group's entries).
+// Afterwards the table is cleared with vector stores: no scan of its slots writes the output.
+template <int SLOTS>
+struct alignas(16) WarpDirectSlice {
+  uint32_t keys[SLOTS];
+  uint32_t spos[SLOTS];  // output position of the key in the slot (within its problem's output)
+  u64 pre[33];
+  uint32_t ystart[32];
+  double v[32];
+  OutTarget tg;
+};
+
+template <int SLOTS, int WARPS, int D>
+__global__ void __launch_bounds__(WARPS * 32) group_warp_direct_kernel(GroupArgs a,
+                                                                       const uint32_t* __restrict__ list,
+                                                                       const uint32_t* __restrict__ countp) {
+  const uint32_t count = *countp;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t lt = lanemask_lt();
+  WarpDirectSlice<SLOTS>& ws = reinterpret_cast<WarpDirectSlice<SLOTS>*>(smem)[warp];
+  for (uint32_t i = lane; i < SLOTS / 4; i += 32)
+    reinterpret_cast<uint4*>(ws.keys)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+  __syncwarp();
+  const uint64_t keep = policy_evict_last();
+  const uint64_t pol = policy_evict_first();
+  const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
+  for (uint32_t k = blockIdx.x * WARPS + warp; k < count; k += gridDim.x * WARPS) {
+    const uint32_t g = list[k];
+    const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
+    // One X entry over a run of all-different free keys: the run scaled by x, no table.
+    const bool single = a.yuniq != nullptr && x1 - x0 == 1 && a.yuniq[a.gx.ystart[x0]];
+    if (lane == 0) resolve_target(a, g, single ? a.gx.w[x0] : 0u, ws.tg);
+    __syncwarp();
+    const u64 cap = ws.tg.cap;
+    if (single) {
+      const uint32_t ys = a.gx.ystart[x0], len = a.gx.w[x0];
+      const double xv = a.gx.v[x0];
+      for (uint32_t j = lane; j < len; j += 32) {
+        const uint32_t key = ld_keep_u32(yfk + ys + j, keep);
+        const double prod = __dmul_rn(xv, ld_keep_f64(a.yv + ys + j, keep));
+        const u64 pos = ws.tg.base + j;
+        if (pos < cap)
+          store_output(ws.tg.coords, ws.tg.vals, pos, ws.tg.zrow + (u64)key, prod, ws.tg.op, pol);
+        else
+          atomicOr(a.status, kStatOutOverflow);
+      }
+      __syncwarp();  // ws.tg is rewritten for the next group
+      continue;
+    }
+    for (uint32_t c0 = x0; c0 < x1; c0 += 32) {
+      const uint32_t n = (x1 - c0 < 32u) ? x1 - c0 : 32u;
+      u64 w = 0;
+      if (lane < n) {
+        w = a.gx.w[c0 + lane];
+        ws.ystart[lane] = a.gx.ystart[c0 + lane];
+        ws.v[lane] = a.gx.v[c0 + lane];
+      }
+      u64 incl = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      ws.pre[lane] = incl - w;
+      const u64 total = __shfl_sync(0xffffffffu, incl, 31);
+      if (lane == 0) ws.pre[32] = total;
+      __syncwarp();
+      // Entries at or past n have w = 0, so pre[n..32] = total bounds the walk.
+      uint32_t own = 0;
+      for (u64 base = 0; base < total; base += 32 * D) {
+        uint32_t key[D];
+        double prod[D];
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          const u64 p = base + (u64)u * 32 + lane;
+          uint32_t kk = own;
+          key[u] = kEmpty32;
+          if (p < total) {
+            while (ws.pre[kk + 1] <= p) kk++;
+            const u64 j = (u64)ws.ystart[kk] + (p - ws.pre[kk]);
+            key[u] = ld_keep_u32(yfk + j, keep);
+            prod[u] = __dmul_rn(ws.v[kk], ld_keep_f64(a.yv + j, keep));
+          }
+          own = __shfl_sync(0xffffffffu, kk, 31);
+        }
+        int slot[D];
+        bool mine[D];
+        uint32_t m[D];
+        uint32_t nclaim = 0;
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          slot[u] = -1;
+          mine[u] = false;
+          if (key[u] != kEmpty32) {
+            slot[u] = bucket_claim<uint32_t, SLOTS>(ws.keys, key[u], &mine[u]);
+            if (slot[u] < 0) atomicOr(a.status, kStatTableFull);
+          }
+          m[u] = __ballot_sync(0xffffffffu, mine[u]);
+          nclaim += __popc(m[u]);
+        }
+        u64 rb = 0;
+        if (nclaim) {
+          if (lane == 0) rb = atomicAdd(ws.tg.counter, (u64)nclaim);
+          rb = __shfl_sync(0xffffffffu, rb, 0);
+        }
+        uint32_t off = 0;
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          if (mine[u]) {
+            const u64 pos = rb + off + __popc(m[u] & lt);
+            ws.spos[slot[u]] = (uint32_t)pos;
+            if (pos < cap)
+              store_output(ws.tg.coords, ws.tg.vals, pos, ws.tg.zrow + (u64)key[u], prod[u], ws.tg.op, pol);
+            else
+              atomicOr(a.status, kStatOutOverflow);
+          }
+          off += __popc(m[u]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < D; u++) {
+          if (slot[u] >= 0 && !mine[u]) {
+            const u64 pos = ws.spos[slot[u]];
+            if (pos < cap) atomicAdd(ws.tg.vals + pos, prod[u]);
+          }
+        }
+      }
+      __syncwarp();  // the chunk's staging is rewritten by the next chunk
+    }
+    for (uint32_t i = lane; i < SLOTS / 4; i += 32)
+      reinterpret_cast<uint4*>(ws.keys)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+    __syncwarp();
+  }
+}
+
+template <int SLOTS, int D>
+cudaError_t launch_warp_direct_class(const GroupArgs& a, const uint32_t* list, const uint32_t* countp, uint32_t count,
+                                     int sms, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  constexpr int WARPS = 8;
+  const size_t smem = WARPS * sizeof(WarpDirectSlice<SLOTS>);
+  auto kern = group_warp_direct_kernel<SLOTS, WARPS, D>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const uint32_t need = count == kCountOnDevice ? count : (count + WARPS - 1) / WARPS;
+  const uint32_t cap = (uint32_t)(sms * per_sm);
+  kern<<<need < cap ? need : cap, WARPS * 32, smem, s>>>(a, list, countp);
+  note_launch();
+  return cudaGetLastError();
+}
 
 // ---- direct output: a product that claims a new key writes its output entry at once.
 // The table holds keys and output positions only. A claimer takes a rank inside its round
@@ -2008,9 +2193,14 @@ cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct
   for (int c = 0; c < kMaxClasses; c++) h[c] = counts ? counts[c] : kCountOnDevice;
   const uint32_t* d = b.count;
   if (!wide_keys && direct) {
-    if ((e = launch_warp_class<256, uint32_t>(a, b.list[0], d + 0, h[0], sms, s))) return e;
-    if ((e = launch_warp_class<1024, uint32_t>(a, b.list[1], d + 1, h[1], sms, s))) return e;
     // The expansion split: products each lane forms per round before the claims of the round.
+    if (depth == 0) {
+      if ((e = launch_warp_direct_class<256, 4>(a, b.list[0], d + 0, h[0], sms, s))) return e;
+      if ((e = launch_warp_direct_class<1024, 4>(a, b.list[1], d + 1, h[1], sms, s))) return e;
+    } else {
+      if ((e = launch_warp_direct_class<256, 2>(a, b.list[0], d + 0, h[0], sms, s))) return e;
+      if ((e = launch_warp_direct_class<1024, 2>(a, b.list[1], d + 1, h[1], sms, s))) return e;
+    }
     if (depth == 0) {
       if ((e = launch_direct_class<4096, 256, 6, 4>(a, b.list[2], d + 2, h[2], sms, s))) return e;
       if ((e = launch_direct_class<8192, 512, 6, 2>(a, b.list[3], d + 3, h[3], sms, s))) return e;

@@ -206,6 +206,10 @@ struct GroupArgs {
   u64* bnz;
   const uint32_t* gprob;
   const u64* gfk;
+  // Non-null: yuniq[r] = 1 at the first entry r of every Y run whose free keys are all
+  // different (run_unique_kernel). A group of one X entry over such a run has one product per
+  // output, and the warp kernels write it as a scaled copy of the run without a table.
+  const uint8_t* yuniq;
 };
 
 // Where one group's outputs go, resolved once per group.
@@ -290,6 +294,7 @@ struct BatchArgs {
   u64* pcap;            // [n] output bound per problem
   uint32_t* scan_scratch32;
   uint32_t* status;
+  uint8_t* yuniq;       // [total_y] or null: runs with all-different free keys (32-bit keys only)
 };
 
 cudaError_t launch_batch_prepare(const BatchArgs& ba, int sms, cudaStream_t s);

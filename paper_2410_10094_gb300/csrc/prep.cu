@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, kXMinBlocks) x_scatter_dense_kernel(
 #define SV_CONSUMERS 24
 #endif
 #ifndef SV_STAGES
-#define SV_STAGES 4
+#define SV_STAGES 6
 #endif
 #ifndef SV_ROWS
 #define SV_ROWS 1536
@@ -488,9 +488,13 @@ __host__ __device__ constexpr size_t sv_ring_bytes() {
   return (size_t)kSvStages * sv_rows<ORDER>() * ORDER * 4;
 }
 
-static_assert(sv_ring_bytes<4>() + kNonemptyMaxKeys / 8 <= 227 * 1024 &&
-                  sv_ring_bytes<8>() + kNonemptyMaxKeys / 8 <= 227 * 1024,
-              "the survey's ring and key bitmap fit one CTA's shared memory");
+// Static shared memory of x_survey_bulk_kernel: the consumers' survivor buffers (free key,
+// contract key, row), their product sums, the ring's mbarriers, the abort flag.
+constexpr size_t kSvStatic = (size_t)kSvConsumers * 64 * (8 + 4 + 8) + (size_t)kSvConsumers * 8 +
+                             (size_t)kSvStages * 16 + 256;  // + alignment
+static_assert(sv_ring_bytes<4>() + kNonemptyMaxKeys / 8 + kSvStatic <= 227 * 1024 &&
+                  sv_ring_bytes<8>() + kNonemptyMaxKeys / 8 + kSvStatic <= 227 * 1024,
+              "the survey's ring, key bitmap and buffers fit one CTA's shared memory");
 
 // KEY32: contract keys below 2^32, formed in 32-bit arithmetic; the free key (64-bit) is formed
 // only for the rows that survive.

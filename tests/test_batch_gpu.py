@@ -168,3 +168,39 @@ def test_batch_overflow_groups_twice_in_a_row():
 
         gc.collect()
         ctx.close()
+
+
+def test_batch_single_entry_groups_and_repeated_y_keys():
+    """Groups of one X entry (most X free keys hold a single entry here) over Y runs with and
+    without repeated free keys: runs whose free keys are all different take the scaled-copy
+    path, runs with a repeated (contract, free) coordinate must still sum the repeats. Both
+    against the oracle, in an ordinary batch and in a replayed plan."""
+    import numpy as np
+
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(8500)
+    probs = []
+    for i in range(12):
+        X = W.uniform_coo(rng, (400, 300, 24), 2_500)
+        Y = W.uniform_coo(rng, (24, 40, 30), 3_000)
+        if i % 2:  # repeat some of Y's coordinates with new values
+            k = 200
+            Y = W.COO(Y.shape, np.concatenate([Y.coords, Y.coords[:k]]), np.concatenate([Y.vals, W.nonzero_values(rng, k)]))
+        probs.append(W.Problem(X, Y, (2,), (0,)))
+    refs = [oracle.contract(p.X, p.Y, p.cx, p.cy) for p in probs]
+    dev = [(to_dev(p.X), to_dev(p.Y), p.cx, p.cy) for p in probs]
+    for ref, r in zip(refs, stc.contract_batch(dev)):
+        c, v = host(r)
+        assert_matches_oracle(c, v, ref)
+    plan = stc.BatchPlan(dev, group_load_factor=0.75)
+    try:
+        for _ in range(3):
+            res = plan.run()
+            for ref, r in zip(refs, res):
+                c, v = host(r)
+                assert_matches_oracle(c, v, ref)
+            del res
+        assert plan.stats()[1] >= 2
+    finally:
+        plan.close()
