@@ -211,10 +211,13 @@ def source_sha(kernel):
     return h.hexdigest()
 
 
-def ncu_traffic(workload):
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+
+def ncu_traffic(workload, path=None):
     """(kernel, bytes per launch) of the workload's capture when it matches today's sources."""
     try:
-        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        with open(path or TRAFFIC_FILE) as f:
             entry = json.load(f).get(workload)
     except (OSError, ValueError):
         return None
@@ -223,8 +226,8 @@ def ncu_traffic(workload):
     return entry["kernel"], float(entry["bytes_per_launch"])
 
 
-def record_traffic(workload, kernel, csv_path):
-    """Adds one capture to profiles/ncu_traffic.json: the mean dram__bytes_read.sum +
+def record_traffic(workload, kernel, csv_path, path=None):
+    """Adds one capture to profiles/ncu_traffic.json (or `path`): the mean dram__bytes_read.sum +
     dram__bytes_write.sum per launch of `kernel` in an ncu --csv log, with today's source hash."""
     import csv
 
@@ -240,7 +243,7 @@ def record_traffic(workload, kernel, csv_path):
             per[r[ii]] = per.get(r[ii], 0.0) + float(r[vi].replace(",", "")) * scale
     if not per:
         raise SystemExit(f"no DRAM counters of {kernel} in {csv_path}")
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    path = path or TRAFFIC_FILE
     try:
         with open(path) as f:
             data = json.load(f)
