@@ -118,6 +118,38 @@ __device__ __forceinline__ void resolve_target(const GroupArgs& a, u64 g, unsign
   for (unsigned i = 0; i < sizeof(OutPlan) / sizeof(u64); i++) dst[i] = src[i];
 }
 
+// resolve_target by the 32 lanes of one warp (every lane calls it): the output plan is copied a
+// word per lane rather than word by word, and only when the group's problem differs from the
+// previous group's (a single contraction copies it once), so a group's set-up costs at most one
+// round of loads. t.prob must hold kNoProb before the warp's first call.
+__device__ __forceinline__ void resolve_target_warp(const GroupArgs& a, u64 g, unsigned n, OutTarget& t) {
+  const unsigned lane = lane_id();
+  uint32_t p = 0;
+  if (lane == 0 && a.gprob) p = a.gprob[g];
+  p = __shfl_sync(0xffffffffu, p, 0);
+  const bool fresh = t.prob != p;
+  __syncwarp();  // every lane has read t.prob before lane 0 rewrites it
+  const BatchOut* bo = a.bout + p;
+  if (fresh) {
+    const u64* src = reinterpret_cast<const u64*>(&bo->op);
+    u64* dst = reinterpret_cast<u64*>(&t.op);
+    constexpr unsigned kWords = sizeof(OutPlan) / sizeof(u64);
+    for (unsigned i = lane; i < kWords; i += 32) dst[i] = src[i];
+  }
+  if (lane == 0) {
+    t.prob = p;
+    const u64 FY = bo->FY;
+    t.FY = FY;
+    t.zrow = (a.gfk ? a.gfk[g] : g) * FY;
+    t.counter = a.bnz + p;
+    t.base = n ? atomicAdd(a.bnz + p, (u64)n) : 0;
+    t.cap = bo->out_cap;
+    t.coords = bo->coords;
+    t.vals = bo->vals;
+  }
+  __syncwarp();
+}
+
 // Shared-memory staging of one chunk of a group's X entries: the exclusive prefix of their
 // run lengths (products), the first slot of each run, and the X values.
 template <int THREADS>
@@ -732,10 +764,14 @@ __global__ void __launch_bounds__(THREADS, 2) group_bitmap_kernel(GroupArgs a, c
     }
   };
   prefetch(blockIdx.x);
+  if (threadIdx.x < 32) {  // warp 0 resolves the targets: no plan cached yet
+    if (threadIdx.x == 0) tg.prob = kNoProb;
+    __syncwarp();
+  }
   for (uint32_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
     const uint32_t g = pf_g, x0 = pf_x0, x1 = pf_x1;
     const bool one_chunk = x1 - x0 <= (uint32_t)THREADS;
-    if (threadIdx.x == 0) resolve_target(a, g, 0, tg);
+    if ((threadIdx.x >> 5) == 0) resolve_target_warp(a, g, 0, tg);  // warp 0; published by later barriers
     if (one_chunk && threadIdx.x < x1 - x0) {
       st.ck[threadIdx.x] = pf_ck;
       st.v[threadIdx.x] = pf_v;
@@ -1126,10 +1162,14 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
     }
   };
   prefetch(blockIdx.x);
+  if (threadIdx.x < 32) {  // warp 0 resolves the targets: no plan cached yet
+    if (threadIdx.x == 0) tg.prob = kNoProb;
+    __syncwarp();
+  }
   for (uint32_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
     const uint32_t g = pf_g, x0 = pf_x0, x1 = pf_x1;
     const bool one_chunk = x1 - x0 <= (uint32_t)T;
-    if (threadIdx.x == 0) resolve_target(a, g, 0, tg);
+    if ((threadIdx.x >> 5) == 0) resolve_target_warp(a, g, 0, tg);  // warp 0; published by later barriers
     const uint32_t my_ck = pf_ck, my_ys = pf_ys, my_ye = pf_ye;
     const double my_v = pf_v;
     prefetch(gi + gridDim.x);
@@ -1382,10 +1422,14 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
     }
   };
   prefetch(blockIdx.x);
+  if (threadIdx.x < 32) {  // warp 0 resolves the targets: no plan cached yet
+    if (threadIdx.x == 0) tg.prob = kNoProb;
+    __syncwarp();
+  }
   for (uint32_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
     const uint32_t g = pf_g, x0 = pf_x0, x1 = pf_x1;
     const bool one_chunk = x1 - x0 <= CH;
-    if (threadIdx.x == 0) resolve_target(a, g, 0, tg);
+    if ((threadIdx.x >> 5) == 0) resolve_target_warp(a, g, 0, tg);  // warp 0; published by later barriers
     const uint32_t my_ck = pf_ck, my_ys = pf_ys, my_ye = pf_ye;
     const double my_v = pf_v;
     prefetch(gi + gridDim.x);
@@ -1677,6 +1721,7 @@ __global__ void __launch_bounds__(WARPS * 32) group_warp_kernel(GroupArgs a, con
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   WarpSlice<SLOTS, KT>& ws = reinterpret_cast<WarpSlice<SLOTS, KT>*>(smem)[warp];
   for (uint32_t i = lane; i < SLOTS; i += 32) ws.keys[i] = empty_key<KT>();
+  if (lane == 0) ws.tg.prob = kNoProb;
   __syncwarp();
   const uint64_t keep = policy_evict_last();
   const uint64_t pol = policy_evict_first();
@@ -1688,8 +1733,7 @@ __global__ void __launch_bounds__(WARPS * 32) group_warp_kernel(GroupArgs a, con
       // own, written as the run scaled by x, without the table.
       const uint32_t ys = a.gx.ystart[x0], len = a.gx.w[x0];
       const double xv = a.gx.v[x0];
-      if (lane == 0) resolve_target(a, g, len, ws.tg);
-      __syncwarp();
+      resolve_target_warp(a, g, len, ws.tg);
       for (uint32_t j = lane; j < len; j += 32) {
         u64 key;
         if constexpr (sizeof(KT) == 4)
@@ -1767,8 +1811,7 @@ __global__ void __launch_bounds__(WARPS * 32) group_warp_kernel(GroupArgs a, con
       }
     }
     // Write the group's occupied slots, consecutive lanes storing consecutive outputs.
-    if (lane == 0) resolve_target(a, g, claims, ws.tg);
-    __syncwarp();
+    resolve_target_warp(a, g, claims, ws.tg);
     unsigned off = 0;
     for (uint32_t b0 = 0; b0 < NB; b0 += 32) {
       const uint32_t b = b0 + lane;
@@ -1870,6 +1913,7 @@ __global__ void __launch_bounds__(WARPS * 32) group_warp_direct_kernel(GroupArgs
   WarpDirectSlice<SLOTS>& ws = reinterpret_cast<WarpDirectSlice<SLOTS>*>(smem)[warp];
   for (uint32_t i = lane; i < SLOTS / 4; i += 32)
     reinterpret_cast<uint4*>(ws.keys)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+  if (lane == 0) ws.tg.prob = kNoProb;
   __syncwarp();
   const uint64_t keep = policy_evict_last();
   const uint64_t pol = policy_evict_first();
@@ -1879,8 +1923,7 @@ __global__ void __launch_bounds__(WARPS * 32) group_warp_direct_kernel(GroupArgs
     const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
     // One X entry over a run of all-different free keys: the run scaled by x, no table.
     const bool single = a.yuniq != nullptr && x1 - x0 == 1 && a.yuniq[a.gx.ystart[x0]];
-    if (lane == 0) resolve_target(a, g, single ? a.gx.w[x0] : 0u, ws.tg);
-    __syncwarp();
+    resolve_target_warp(a, g, single ? a.gx.w[x0] : 0u, ws.tg);
     const u64 cap = ws.tg.cap;
     if (single) {
       const uint32_t ys = a.gx.ystart[x0], len = a.gx.w[x0];
@@ -2030,9 +2073,13 @@ __global__ void __launch_bounds__(THREADS, MINB) group_direct_kernel(GroupArgs a
   if (threadIdx.x == 0) round_claims = 0;
   const uint64_t keep = policy_evict_last();
   const uint64_t pol = policy_evict_first();
+  if (threadIdx.x < 32) {  // warp 0 resolves the targets: no plan cached yet
+    if (threadIdx.x == 0) tg.prob = kNoProb;
+    __syncwarp();
+  }
   for (uint32_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
     const uint32_t g = list[gi];
-    if (threadIdx.x == 0) resolve_target(a, g, 0, tg);
+    if (warp == 0) resolve_target_warp(a, g, 0, tg);  // published by load_chunk's barriers
     const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
     for (uint32_t c0 = x0; c0 < x1; c0 += THREADS) {
       const uint32_t n = (x1 - c0 < (uint32_t)THREADS) ? x1 - c0 : (uint32_t)THREADS;

@@ -221,8 +221,10 @@ struct OutTarget {
   int32_t* coords;
   double* vals;
   u64* counter;  // the problem's output counter (positions are reserved from it)
+  uint32_t prob; // problem whose output plan `op` holds (kNoProb before the first group)
   OutPlan op;
 };
+constexpr uint32_t kNoProb = 0xffffffffu;
 
 // A count only the device knows (launchers then run a full persistent grid).
 constexpr uint32_t kCountOnDevice = 0xffffffffu;
