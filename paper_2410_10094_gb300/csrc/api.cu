@@ -611,7 +611,7 @@ uint64_t grouped_bytes(const Plan& pl, int64_t nX, int64_t nY, uint64_t P) {
 // Counters of the grouping and binning passes, read back with the first host sync.
 struct GroupCounters {
   uint32_t count[kMaxClasses + 4];
-  unsigned stream_nrec;  // streamed segments with repeats
+  unsigned stream_nrec;  // streamed (group, segment) records
   u64 huge_slots;
   u64 out_cap;
   u64 stream_holes;      // positions of streamed reservations that hold no output

@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(kThreads) y_scatter_batch_kernel(const BatchPr
 // Marks the Y runs (the entries of one contract-key bin) whose free keys are all different:
 // yuniq[first entry of the run] = 1, else 0. One warp per run, with a table of kUniqSlots keys
 // in shared memory (linear probing, one compare-and-swap per entry); runs longer than half the
-// table are left at 0 and keep the table path. The table is cleared after every run.
+// table are set to 0 here and decided by run_unique_long_kernel up to kUniqLongMax entries (the
+// longer ones keep the table path). The table is cleared after every run.
 constexpr int kUniqWarps = 8;
 constexpr uint32_t kUniqSlots = 1024;
 __global__ void __launch_bounds__(kUniqWarps * 32) run_unique_kernel(const uint32_t* __restrict__ yoff, u64 bins,
@@ -134,6 +135,48 @@ __global__ void __launch_bounds__(kUniqWarps * 32) run_unique_kernel(const uint3
   }
 }
 static_assert(kUniqSlots == 1024, "the hash above takes 10 bits");
+
+// The same for the runs run_unique_kernel leaves unmarked (kUniqSlots / 2 < length <=
+// kUniqLongMax): one CTA per run with a table of 2 * kUniqLongMax keys in shared memory.
+constexpr int kUniqLongThreads = 256;
+constexpr uint32_t kUniqLongMax = 4096;
+constexpr uint32_t kUniqLongSlots = 2 * kUniqLongMax;
+__global__ void __launch_bounds__(kUniqLongThreads) run_unique_long_kernel(const uint32_t* __restrict__ yoff, u64 bins,
+                                                                          const uint32_t* __restrict__ yfk,
+                                                                          uint8_t* __restrict__ yuniq) {
+  __shared__ __align__(16) uint32_t t[kUniqLongSlots];
+  __shared__ int s_dup;
+  for (uint32_t i = threadIdx.x; i < kUniqLongSlots / 4; i += kUniqLongThreads)
+    reinterpret_cast<uint4*>(t)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+  if (threadIdx.x == 0) s_dup = 0;
+  __syncthreads();
+  for (u64 b = blockIdx.x; b < bins; b += gridDim.x) {
+    const uint32_t s0 = yoff[b], len = yoff[b + 1] - s0;
+    if (len <= kUniqSlots / 2 || len > kUniqLongMax) continue;  // uniform over the CTA
+    for (uint32_t j = threadIdx.x; j < len; j += kUniqLongThreads) {
+      const uint32_t key = yfk[s0 + j];
+      uint32_t h = (key * 0x9E3779B1u) >> 19;  // 13 bits: kUniqLongSlots slots
+      for (uint32_t probe = 0; probe < kUniqLongSlots; probe++) {
+        const uint32_t prev = atomicCAS(t + h, kEmpty32, key);
+        if (prev == kEmpty32) break;
+        if (prev == key) {
+          s_dup = 1;
+          break;
+        }
+        h = (h + 1) & (kUniqLongSlots - 1);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      yuniq[s0] = s_dup ? 0 : 1;
+      s_dup = 0;
+    }
+    for (uint32_t i = threadIdx.x; i < kUniqLongSlots / 4; i += kUniqLongThreads)
+      reinterpret_cast<uint4*>(t)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+    __syncthreads();
+  }
+}
+static_assert(kUniqLongSlots == 8192, "the hash above takes 13 bits");
 
 // Survivors of all problems: their combined group key fxoff[p] + fX, Y run, value; the
 // product count per problem and in total.
@@ -427,7 +470,10 @@ cudaError_t launch_batch_prepare(const BatchArgs& ba, int sms, cudaStream_t s) {
         const u64 want = (ba.bins + kUniqWarps - 1) / kUniqWarps, cap = (u64)sms * 8;
         run_unique_kernel<<<(unsigned)(want < cap ? want : cap), kUniqWarps * 32, 0, s>>>(
             ba.yoff, ba.bins, static_cast<const uint32_t*>(ba.yfk), ba.yuniq);
-        note_launch();
+        const u64 lcap = (u64)sms * 4;
+        run_unique_long_kernel<<<(unsigned)(ba.bins < lcap ? ba.bins : lcap), kUniqLongThreads, 0, s>>>(
+            ba.yoff, ba.bins, static_cast<const uint32_t*>(ba.yfk), ba.yuniq);
+        note_launch(2);
       }
     } else
       y_scatter_batch_kernel<u64><<<grid_for(ba.total_y, sms), kThreads, 0, s>>>(

@@ -1404,6 +1404,7 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
   const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
   for (uint32_t i = threadIdx.x; i < 2 * kBitmapWords; i += T) bits[i] = 0;
   if (threadIdx.x == 0) s_cnt = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sa.nrec = count * nseg;  // one record per (group, segment)
   // Prefetched staging of the next group (when it fits one chunk).
   uint32_t pf_g = 0, pf_x0 = 0, pf_x1 = 0, pf_ck = 0, pf_ys = 0, pf_ye = 0;
   double pf_v = 0.0;
@@ -1464,7 +1465,10 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
           block_exscan_u32<T>(len, &tot, warp_tot);
           Pq += tot;
         }
-        if (Pq == 0) continue;
+        if (Pq == 0) {
+          if (threadIdx.x == 0) sa.rec[(u64)gi * nseg + q] = StreamRec{0, 0, 0};
+          continue;
+        }
         if (threadIdx.x == 0) s_gbase = atomicAdd(tg.counter, (u64)Pq);
       }
       // ---- pass 1, one chunk of X entries at a time.
@@ -1589,7 +1593,10 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
         }
         if (!one_chunk) __syncthreads();
       }
-      if (Pq == 0) continue;
+      if (Pq == 0) {
+        if (threadIdx.x == 0) sa.rec[(u64)gi * nseg + q] = StreamRec{0, 0, 0};
+        continue;
+      }
       // The block barrier orders every thread's earlier global stores (first products, repeats'
       // records) before the later reads and atomics of the block's threads, which are the only
       // ones that touch this group's reservation; no device-wide fence is needed.
@@ -1625,9 +1632,10 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
         if (threadIdx.x == 0) atomicAdd(sa.holes, (u64)reps);
         __syncthreads();  // the lookups above read the bitmaps cleared below
       }
-      // Every streamed segment is recorded: those whose outputs end above the final count are
-      // the sources of the hole filling, whatever their repeats.
-      if (threadIdx.x == 0) sa.rec[atomicAdd(sa.nrec, 1u)] = StreamRec{s_gbase, nkeys, Pq};
+      // Every streamed segment is recorded, at its own index (list position, segment): those
+      // whose outputs end above the final count are the sources of the hole filling, whatever
+      // their repeats.
+      if (threadIdx.x == 0) sa.rec[(u64)gi * nseg + q] = StreamRec{s_gbase, nkeys, Pq};
       // ---- clear the bitmaps for the next segment or group.
       for (uint32_t i = threadIdx.x; i < nwords / 4; i += T) {
         reinterpret_cast<uint4*>(bits)[i] = make_uint4(0, 0, 0, 0);
@@ -2079,8 +2087,26 @@ __global__ void __launch_bounds__(THREADS, MINB) group_direct_kernel(GroupArgs a
   }
   for (uint32_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
     const uint32_t g = list[gi];
-    if (warp == 0) resolve_target_warp(a, g, 0, tg);  // published by load_chunk's barriers
     const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
+    // One X entry over a run of all-different free keys: the run scaled by x, no table.
+    const bool single = a.yuniq != nullptr && x1 - x0 == 1 && a.yuniq[a.gx.ystart[x0]];
+    if (warp == 0) resolve_target_warp(a, g, single ? a.gx.w[x0] : 0u, tg);  // published by the next barrier
+    if (single) {
+      __syncthreads();
+      const uint32_t ys = a.gx.ystart[x0], len = a.gx.w[x0];
+      const double xv = a.gx.v[x0];
+      for (uint32_t j = threadIdx.x; j < len; j += THREADS) {
+        const uint32_t key = ld_keep_u32(static_cast<const uint32_t*>(a.yfk) + ys + j, keep);
+        const double prod = __dmul_rn(xv, ld_keep_f64(a.yv + ys + j, keep));
+        const u64 pos = tg.base + j;
+        if (pos < tg.cap)
+          store_output(tg.coords, tg.vals, pos, tg.zrow + (u64)key, prod, tg.op, pol);
+        else
+          atomicOr(a.status, kStatOutOverflow);
+      }
+      __syncthreads();  // tg is rewritten for the next group
+      continue;
+    }
     for (uint32_t c0 = x0; c0 < x1; c0 += THREADS) {
       const uint32_t n = (x1 - c0 < (uint32_t)THREADS) ? x1 - c0 : (uint32_t)THREADS;
       load_chunk<THREADS>(a, c, warp_tot, c0, n);  // its barriers also publish tg

@@ -337,7 +337,7 @@ struct StreamRec {
 };
 struct StreamArgs {
   StreamRec* rec;
-  unsigned* nrec;  // segments recorded
+  unsigned* nrec;  // records: one per (streamed group, segment), [list position * nseg + segment]
   u64* holes;      // total repeats (positions that hold no output at the end)
 };
 uint32_t dense_stream_cap();

@@ -204,3 +204,29 @@ def test_batch_single_entry_groups_and_repeated_y_keys():
         assert plan.stats()[1] >= 2
     finally:
         plan.close()
+
+
+def test_batch_single_entry_groups_over_long_runs():
+    """One-entry groups over Y runs of 1,500 entries (the CTA table classes, and the per-run
+    uniqueness check for long runs): runs with all-different free keys are written as scaled
+    copies, runs with a repeated coordinate keep the table path. Against the oracle."""
+    import numpy as np
+
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(8510)
+    probs = []
+    for i in range(4):
+        X = W.uniform_coo(rng, (500, 400, 8), 3_000)
+        cells = [rng.choice(60 * 60, size=1_500, replace=False) for _ in range(8)]
+        yc = np.concatenate([np.stack([np.full(1_500, k), c // 60, c % 60], axis=1) for k, c in enumerate(cells)])
+        yv = W.nonzero_values(rng, yc.shape[0])
+        if i % 2:  # a repeated coordinate in some runs
+            yc = np.concatenate([yc, yc[::997]])
+            yv = np.concatenate([yv, W.nonzero_values(rng, yc.shape[0] - yv.shape[0])])
+        probs.append(W.Problem(X, W.COO((8, 60, 60), yc, yv), (2,), (0,)))
+    refs = [oracle.contract(p.X, p.Y, p.cx, p.cy) for p in probs]
+    dev = [(to_dev(p.X), to_dev(p.Y), p.cx, p.cy) for p in probs]
+    for ref, r in zip(refs, stc.contract_batch(dev)):
+        c, v = host(r)
+        assert_matches_oracle(c, v, ref)
