@@ -202,12 +202,17 @@ KERNEL_SOURCES = {"group_stream_kernel": ["grouped.cu", "common.cuh", "launch.h"
 
 
 def source_sha(kernel):
+    """Hash of the code (comments and blank lines left out) of the sources that define `kernel`."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for f in KERNEL_SOURCES.get(kernel, []):
-        with open(os.path.join(ROOT, "paper_2410_10094_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2410_10094_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip()).encode())
     return h.hexdigest()
 
 

@@ -1351,9 +1351,9 @@ __global__ void __launch_bounds__(kStashThreads, 2) group_stash_kernel(GroupArgs
 // first product of a key (the one that finds its bit clear) writes its output entry at once,
 // at the next place from the front of the reservation. A repeat writes its key and value as
 // a temporary record at the next place from the back and marks its key in a second bitmap.
-// After a device-scope fence and a barrier the repeated keys are ranked, their first
-// products' places looked up, and every repeat adds its value to that entry with an L2
-// atomic. The back of the reservation (the repeats' records) becomes a hole; after all
+// After a block barrier (which orders the block's own stores before its later reads and
+// atomics) the repeated keys are ranked, their first products' places looked up, and every
+// repeat adds its value to that entry with an L2 atomic. The back of the reservation (the repeats' records) becomes a hole; after all
 // groups, holes below the final output count are filled with the entries above it.
 
 #ifndef STREAM_U

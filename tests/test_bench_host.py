@@ -42,3 +42,17 @@ def test_oracle_parts_make_the_whole_sample():
     prods, seconds, desc = bench.run_oracle_parallel(p, "plain_small", 3, 4)
     assert prods == whole and whole > 0 and seconds >= 0
     assert "4 parts" in desc
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    d = tmp_path / "paper_2410_10094_gb300" / "csrc"
+    d.mkdir(parents=True)
+    f = d / "k.cu"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", {"k": ["k.cu"]})
+    f.write_text("// a kernel\n__global__ void k(int* p) { p[0] = 1; }\n")
+    h0 = bench.source_sha("k")
+    f.write_text("/* reworded\n   comment */\n__global__ void k(int* p) { p[0] = 1; }  // trailing\n\n")
+    assert bench.source_sha("k") == h0
+    f.write_text("// a kernel\n__global__ void k(int* p) { p[0] = 2; }\n")
+    assert bench.source_sha("k") != h0
