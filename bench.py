@@ -688,9 +688,11 @@ def main(argv=None):
     # ---- per-stage times: K more steps with the library's stage events on (they wait for
     # the last event of each call, so they run outside the timed region above)
     stage = np.zeros(8)
+    acc_used = None
     for _ in range(args.steps):
         r = step(record=True)
         stage[: len(r.stats.stage_ms)] += np.asarray(r.stats.stage_ms)
+        acc_used = getattr(r.stats, "accumulator", None)
         del r
     torch.cuda.synchronize()
     clk.stop()
@@ -790,17 +792,25 @@ def main(argv=None):
                 "traffic_kernel": traffic[0] if traffic else None, "peak_kind": peak_kind,
                 "kernel_ms": dom_ms, "alg_bytes": kernel_bytes}
     if args.workload == "imbalanced_both":
-        # Products fall on at most 262,144 outputs: the one-global-table expansion issues one FP64
-        # multiply and one FP64 atomic add in L2 per product, so its bounds are those two rates,
-        # measured here (stc_measure_peaks), not HBM bandwidth.
+        # Products fall on at most 262,144 outputs, so the bounds are not HBM bandwidth but the
+        # rates measured here (stc_measure_peaks): the one-global-table expansion issues one FP64
+        # multiply and one FP64 atomic add in L2 per product; the lane-private rows (accumulator
+        # ROWS, which AUTO takes once the shape is known to be rows-heavy) one FP64 multiply and
+        # one FP64 add, so half the FP64 multiply rate bounds them.
         dmul, atom = stc.measure_peaks(torch.cuda.current_device())
         acc_ms = float(per_step[4])
         rate = P / (acc_ms / 1e3) if acc_ms > 0 else None
-        roofline = {"bound": "l2_atomic", "kernel": "accumulate", "achieved": rate and rate / 1e9,
-                    "peak": atom / 1e9, "unit": "G products/s (one L2 FP64 atomic add each)",
-                    "frac": rate and rate / atom, "traffic": None, "peak_kind": "measured in this run",
-                    "kernel_ms": acc_ms, "dmul_peak": dmul / 1e9, "dmul_frac": rate and rate / dmul,
-                    "hbm": roofline}
+        if acc_used == stc.ACC_ROWS:
+            roofline = {"bound": "fp64", "kernel": "accumulate", "achieved": rate and rate / 1e9,
+                        "peak": dmul / 2e9, "unit": "G products/s (one FP64 multiply and one FP64 add each)",
+                        "frac": rate and rate / (dmul / 2), "traffic": None, "peak_kind": "measured in this run",
+                        "kernel_ms": acc_ms, "l2_atomic_peak": atom / 1e9, "accumulator": "rows", "hbm": roofline}
+        else:
+            roofline = {"bound": "l2_atomic", "kernel": "accumulate", "achieved": rate and rate / 1e9,
+                        "peak": atom / 1e9, "unit": "G products/s (one L2 FP64 atomic add each)",
+                        "frac": rate and rate / atom, "traffic": None, "peak_kind": "measured in this run",
+                        "kernel_ms": acc_ms, "dmul_peak": dmul / 1e9, "dmul_frac": rate and rate / dmul,
+                        "hbm": roofline}
     step_alg = alg_bytes(p, nz, oz)
 
     cpu = None

@@ -85,9 +85,14 @@ enum { STC_STRATEGY_AUTO = 0, STC_STRATEGY_GLOBAL = 1, STC_STRATEGY_GROUPED = 2 
  * shared memory and written by a scan of the table after the group. DENSE: the group's output
  * row swept in segments of 2^16 Y free keys; the keys present are found with a bitmap over the
  * segment (no hashing or probing), products are stashed in shared memory and repeated keys
- * folded into their first product (F_Y at most 2^20). AUTO: DENSE for the groups larger than
- * the warp-sized hash tables when F_Y <= 2^20, HASH for the others. */
-enum { STC_ACC_AUTO = 0, STC_ACC_HASH = 1, STC_ACC_DENSE = 2, STC_ACC_HASH_SCAN = 3 };
+ * folded into their first product (F_Y at most 2^20). ROWS: for output rows of at most 64 Y
+ * free keys that receive many products each (both operands' contract keys skewed): one warp
+ * per group, each lane adding its products into a private dense row in shared memory without
+ * atomics, the rows summed in lane order at the end (F_Y at most 64, else
+ * STC_ERR_INVALID_ARG). AUTO: ROWS when F_Y <= 64 and the products average at least 64 per
+ * output cell; otherwise DENSE for the groups larger than the warp-sized hash tables when
+ * F_Y <= 2^20, HASH for the others. */
+enum { STC_ACC_AUTO = 0, STC_ACC_HASH = 1, STC_ACC_DENSE = 2, STC_ACC_HASH_SCAN = 3, STC_ACC_ROWS = 4 };
 
 /* Contract keys (Section 4.1.2). DIRECT: Y is grouped over the K = prod(paired lengths)
  * contract keys themselves (counting sort over K bins). DENSE: the contract keys of Y are
@@ -147,7 +152,8 @@ typedef struct stc_stats {
   int32_t nstages;        /* valid entries of stage_ms when record_times was set */
   uint32_t launches;      /* CUDA kernels this call launched (memsets and copies not counted) */
   int32_t accumulator;    /* GROUPED: STC_ACC_HASH or STC_ACC_DENSE when every group used that
-                             accumulator, STC_ACC_AUTO when both ran */
+                             accumulator, STC_ACC_AUTO when both ran, STC_ACC_ROWS for the
+                             lane-private dense rows */
   float stage_ms[8];      /* 0 group Y, 1 survey X, 2 group X, 3 plan, 4 accumulate, 5 compact/write */
   uint64_t contract_ids;  /* distinct contract keys of Y when the contract keys were renumbered
                              to dense ids (STC_IDS_DENSE), else 0 */

@@ -18,7 +18,7 @@ STATUS_NAMES = {
     8: "STC_ERR_COORD_OUT_OF_RANGE", 9: "STC_ERR_UNSUPPORTED", 10: "STC_ERR_CANCELLED",
 }
 STRATEGY_AUTO, STRATEGY_GLOBAL, STRATEGY_GROUPED = 0, 1, 2
-ACC_AUTO, ACC_HASH, ACC_DENSE, ACC_HASH_SCAN = 0, 1, 2, 3
+ACC_AUTO, ACC_HASH, ACC_DENSE, ACC_HASH_SCAN, ACC_ROWS = 0, 1, 2, 3, 4
 IDS_AUTO, IDS_DIRECT, IDS_DENSE = 0, 1, 2
 OPERANDS_AUTO, OPERANDS_AS_GIVEN, OPERANDS_SWAPPED = 0, 1, 2
 STC_MAX_ORDER = 8

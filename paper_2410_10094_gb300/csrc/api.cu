@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -46,6 +47,12 @@ struct stc_ctx {
   int sms = 0;
   std::mutex tune_mu;
   std::map<int, TuneEntry> tune;
+  // Problem shapes (shape_signature) whose last run here averaged at least kRowsMinPerOutput
+  // products per output cell with output rows of at most kLaneRowMax keys: AUTO then groups X
+  // and takes the lane-private dense rows for them (the product count is only known after the
+  // survey, and the one-global-table path for small output key spaces never waits for it).
+  std::mutex rows_mu;
+  std::set<uint64_t> rows_shapes;
 };
 
 namespace {
@@ -236,6 +243,10 @@ bool is_pow2(uint64_t v) { return v && !(v & (v - 1)); }
 // Output key spaces up to this size take the one-global-table strategy without a host read
 // between the survey and the expansion: table and output sized from F (16 MB of table at most).
 constexpr uint64_t kGlobalFromF = 1ull << 18;
+// Lane-private dense rows (STC_ACC_ROWS): output rows of at most this many free keys, chosen by
+// AUTO when the products average at least kRowsMinPerOutput per output cell.
+constexpr uint64_t kLaneRowMax = 64;
+constexpr uint64_t kRowsMinPerOutput = 64;
 // Lanes that probe the one global table together when stc_opts.probe is 0.
 constexpr int kDefaultProbe = 1;
 
@@ -625,6 +636,9 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
                             const stc_opts& o, cudaStream_t s, StageTimer& tm, stc_result* r) {
   const int64_t nX = X->nnz;
   Plan pl = plan_in;
+  if (o.accumulator == STC_ACC_ROWS && pl.FY > kLaneRowMax)
+    return fail(STC_ERR_INVALID_ARG, "the ROWS accumulator takes at most %llu Y free keys, not %llu",
+                (unsigned long long)kLaneRowMax, (unsigned long long)pl.FY);
   // Bitmap rows: F_Y is swept in segments of `seg` free keys; Y is grouped per (contract key,
   // segment). Used when F_Y <= 2^20: for every group with the bitmap accumulator, for the
   // groups beyond the warp-sized hash classes with AUTO.
@@ -710,10 +724,16 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   r->stats.table_slots = hg.huge_slots;
   r->stats.accumulator = dense_groups == 0 ? STC_ACC_HASH : (dense_groups == groups ? STC_ACC_DENSE : STC_ACC_AUTO);
   if (h.P == 0) return STC_OK;
+  // Lane-private dense rows: asked for, or (AUTO) output rows of at most 64 keys that receive
+  // on average kRowsMinPerOutput products or more per output cell.
+  const bool lane_rows = !wide && pl.FY <= kLaneRowMax &&
+                         (o.accumulator == STC_ACC_ROWS ||
+                          (o.accumulator == STC_ACC_AUTO && h.P >= kRowsMinPerOutput * pl.FX * pl.FY));
+  if (lane_rows) r->stats.accumulator = STC_ACC_ROWS;
 
   const uint64_t out_cap = hg.out_cap;
   HugeGroups hh{};
-  hh.count = hg.count[kMaxClasses];
+  hh.count = lane_rows ? 0u : hg.count[kMaxClasses];
   hh.countp = gc->count + kMaxClasses;
   hh.list = b.huge_list;
   hh.off = b.huge_off;
@@ -749,14 +769,16 @@ stc_status contract_grouped(stc_ctx* ctx, Arena& ar, const stc_coo* X, const stc
   a.status = &pr.ctr->status;
   a.bout = dbo;
   a.bnz = &pr.ctr->nz;
-  {
+  if (lane_rows) {
+    STC_CUDA(launch_group_lanerow(a, pl.FX, (uint32_t)pl.FY, ctx->sms, s));
+  } else {
     const bool direct = !wide && out_cap < 0xffffffffull && o.accumulator != STC_ACC_HASH_SCAN;
     STC_CUDA(launch_group_classes(a, wide, direct, b, hg.count, ctx->sms, s));
     STC_CUDA(launch_group_huge(a, hh, wide, ctx->sms, s));
   }
   StreamArgs sa{};
-  const uint32_t nstream = dense_rows ? hg.count[kMaxClasses + 1] : 0u;
-  if (dense_rows) {
+  const uint32_t nstream = (dense_rows && !lane_rows) ? hg.count[kMaxClasses + 1] : 0u;
+  if (dense_rows && !lane_rows) {
     // Streamed groups go last: every other kernel's outputs then lie below the final count.
     STC_CUDA(launch_group_dense(a, pr.yoff, nseg, seg, b.dense_list[2], hg.count[kMaxClasses + 3], b.dense_list[1],
                                 hg.count[kMaxClasses + 2], ctx->sms, s));
@@ -800,6 +822,47 @@ int pick_strategy(const Plan& pl, const stc_coo* X, const stc_coo* Y, int reques
   if (pl.FX <= 2 * nX + (1ull << 20)) return STC_STRATEGY_GROUPED;
   if (nY >= 16 * pl.K && pl.FX <= 16 * nX + (1ull << 20)) return STC_STRATEGY_GROUPED;
   return STC_STRATEGY_GLOBAL;
+}
+
+// FNV-1a over what fixes a contraction's shape: the operands' shapes and entry counts, the mode
+// lists, the output order and form.
+uint64_t shape_signature(const stc_coo* X, const stc_coo* Y, int32_t m, const int32_t* cx, const int32_t* cy,
+                         const int32_t* out_order, int32_t oz, int32_t keys_out) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  auto mix = [&](uint64_t v) {
+    for (int i = 0; i < 8; i++) {
+      h ^= (v >> (8 * i)) & 0xff;
+      h *= 0x100000001b3ull;
+    }
+  };
+  mix((uint64_t)X->order);
+  for (int j = 0; j < X->order; j++) mix((uint64_t)X->shape[j]);
+  mix((uint64_t)Y->order);
+  for (int j = 0; j < Y->order; j++) mix((uint64_t)Y->shape[j]);
+  mix((uint64_t)X->nnz);
+  mix((uint64_t)Y->nnz);
+  mix((uint64_t)m);
+  for (int i = 0; i < m; i++) mix(((uint64_t)(uint32_t)cx[i] << 32) | (uint32_t)cy[i]);
+  mix(out_order ? 1u : 0u);
+  if (out_order)
+    for (int q = 0; q < oz; q++) mix((uint64_t)(uint32_t)out_order[q]);
+  mix((uint64_t)keys_out);
+  return h;
+}
+
+bool rows_remembered(stc_ctx* ctx, uint64_t sig) {
+  std::lock_guard<std::mutex> lk(ctx->rows_mu);
+  return ctx->rows_shapes.count(sig) != 0;
+}
+
+void rows_note(stc_ctx* ctx, uint64_t sig, bool rows) {
+  std::lock_guard<std::mutex> lk(ctx->rows_mu);
+  if (!rows) {
+    ctx->rows_shapes.erase(sig);
+    return;
+  }
+  if (ctx->rows_shapes.size() >= 4096) ctx->rows_shapes.clear();  // a bound, not an eviction policy
+  ctx->rows_shapes.insert(sig);
 }
 
 // Whether the contract keys are renumbered to dense ids before grouping (Section 4.1.2):
@@ -1478,7 +1541,7 @@ stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32
   if (!(alpha > 0.0 && alpha <= 0.9)) return fail(STC_ERR_INVALID_ARG, "load_factor %g outside (0, 0.9]", alpha);
   if (o.strategy < 0 || o.strategy > STC_STRATEGY_GROUPED)
     return fail(STC_ERR_INVALID_ARG, "unknown strategy %d", o.strategy);
-  if (o.accumulator < 0 || o.accumulator > STC_ACC_HASH_SCAN)
+  if (o.accumulator < 0 || o.accumulator > STC_ACC_ROWS)
     return fail(STC_ERR_INVALID_ARG, "unknown accumulator %d", o.accumulator);
   if (o.group_load_factor < 0.0 || o.group_load_factor > 0.9)
     return fail(STC_ERR_INVALID_ARG, "group_load_factor %g outside (0, 0.9]", o.group_load_factor);
@@ -1521,7 +1584,13 @@ stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32
     rl.tm.collect((*out)->stats);
     return STC_OK;
   }
-  const int strategy = pick_strategy(pl, X, Y, o.strategy);
+  int strategy = pick_strategy(pl, X, Y, o.strategy);
+  // AUTO: a shape whose last run here was rows-heavy is grouped again (lane-private rows).
+  const uint64_t sig = shape_signature(X, Y, m, cx, cy, out_order, pl.oz, o.output_keys);
+  const bool rows_shape = o.strategy == STC_STRATEGY_AUTO && pl.FY <= kLaneRowMax && pl.FX <= kMaxDirectBins &&
+                          (o.accumulator == STC_ACC_AUTO || o.accumulator == STC_ACC_ROWS);
+  const bool by_memory = rows_shape && strategy == STC_STRATEGY_GLOBAL && rows_remembered(ctx, sig);
+  if (by_memory) strategy = STC_STRATEGY_GROUPED;
   if (strategy == STC_STRATEGY_GROUPED && pl.FX > kMaxDirectBins)
     return fail(STC_ERR_UNSUPPORTED, "X free key space %llu exceeds %llu bins", (unsigned long long)pl.FX,
                 (unsigned long long)kMaxDirectBins);
@@ -1547,6 +1616,7 @@ stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32
       delete r;
       return st;
     }
+    if (by_memory && r->stats.accumulator != STC_ACC_ROWS) rows_note(ctx, sig, false);
     tm.collect(r->stats);
     r->stats.launches = take_launches();
     ctx->live_results++;
@@ -1603,6 +1673,7 @@ stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32
       delete r;
       return st;
     }
+    if (rows_shape && r->stats.products >= kRowsMinPerOutput * pl.F) rows_note(ctx, sig, true);
     r->mem = adopt(ar, ctx, s, {r->coords, r->vals});
     tm.collect(r->stats);
     r->stats.launches = take_launches();
@@ -1613,6 +1684,7 @@ stc_status contract_impl(stc_ctx* ctx, const stc_coo* X, const stc_coo* Y, int32
   Counters h{};
   STC_TRY(read_counters(pr, s, h));
   tm.mark(3);
+  if (rows_shape && h.P >= kRowsMinPerOutput * pl.F) rows_note(ctx, sig, true);
 
   stc_result* r = new stc_result;
   r->ctx = ctx;

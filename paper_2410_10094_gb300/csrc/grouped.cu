@@ -2298,6 +2298,125 @@ cudaError_t launch_group_classes(const GroupArgs& a, bool wide_keys, bool direct
   return cudaSuccess;
 }
 
+// ---- lane-private dense rows: output rows of at most kRowMax free keys (F_Y <= 64) that
+// receive many products each (both operands' contract keys skewed). One warp per group (X free
+// key); every lane owns a row of F_Y doubles in shared memory and adds its products into it, a
+// rounded product and then a rounded add as everywhere else, with no atomics; a 64-bit mask per
+// lane records the keys the lane has met. At the end the 32 rows are summed column by column
+// in lane order (a lane that never met a key adds an exact zero, so an output of one or two
+// products is the same sum as in any other accumulator), the masks are combined, and the
+// group's outputs are written in key order after one reservation.
+constexpr uint32_t kRowMax = 64;
+constexpr uint32_t kRowStride = kRowMax + 1;  // odd stride in doubles: a column spreads over banks
+constexpr int kRowWarps = 4;
+constexpr int kRowD = 4;  // products per lane per round, loaded before any of them is added
+constexpr size_t kRowSmem = (size_t)kRowWarps * 32 * kRowStride * sizeof(double);
+
+__global__ void __launch_bounds__(kRowWarps * 32) group_lanerow_kernel(GroupArgs a, u64 ngroups, uint32_t FY) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  double* const rows = reinterpret_cast<double*>(smem) + (size_t)warp * 32 * kRowStride;
+  double* const myrow = rows + (size_t)lane * kRowStride;
+  __shared__ u64 s_pre[kRowWarps][33];
+  __shared__ uint32_t s_ys[kRowWarps][32];
+  __shared__ double s_v[kRowWarps][32];
+  __shared__ OutTarget s_tg[kRowWarps];
+  OutTarget& tg = s_tg[warp];
+  u64* const pre = s_pre[warp];
+  uint32_t* const ysv = s_ys[warp];
+  double* const xv = s_v[warp];
+  for (uint32_t c = 0; c < kRowMax; c++) myrow[c] = 0.0;
+  if (lane == 0) tg.prob = kNoProb;
+  __syncwarp();
+  const uint64_t keep = policy_evict_last();
+  const uint64_t pol = policy_evict_first();
+  const uint32_t* yfk = static_cast<const uint32_t*>(a.yfk);
+  for (u64 g = (u64)blockIdx.x * kRowWarps + warp; g < ngroups; g += (u64)gridDim.x * kRowWarps) {
+    const uint32_t x0 = a.goff[g], x1 = a.goff[g + 1];
+    if (x0 == x1) continue;  // uniform over the warp
+    u64 seen = 0;
+    for (uint32_t c0 = x0; c0 < x1; c0 += 32) {
+      const uint32_t n = (x1 - c0 < 32u) ? x1 - c0 : 32u;
+      u64 w = 0;
+      if (lane < n) {
+        w = a.gx.w[c0 + lane];
+        ysv[lane] = a.gx.ystart[c0 + lane];
+        xv[lane] = a.gx.v[c0 + lane];
+      }
+      u64 incl = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      pre[lane] = incl - w;
+      const u64 total = __shfl_sync(0xffffffffu, incl, 31);
+      if (lane == 0) pre[32] = total;
+      __syncwarp();
+      // Entries at or past n have w = 0, so pre[n..32] = total bounds the walk.
+      uint32_t own = 0;
+      for (u64 base = 0; base < total; base += 32 * kRowD) {
+        uint32_t fk[kRowD];
+        double prod[kRowD];
+#pragma unroll
+        for (int u = 0; u < kRowD; u++) {
+          const u64 p = base + (u64)u * 32 + lane;
+          uint32_t kk = own;
+          fk[u] = kRowMax;  // no product
+          if (p < total) {
+            while (pre[kk + 1] <= p) kk++;
+            const u64 j = (u64)ysv[kk] + (p - pre[kk]);
+            fk[u] = ld_keep_u32(yfk + j, keep);
+            prod[u] = __dmul_rn(xv[kk], ld_keep_f64(a.yv + j, keep));
+          }
+          own = __shfl_sync(0xffffffffu, kk, 31);
+        }
+#pragma unroll
+        for (int u = 0; u < kRowD; u++) {
+          if (fk[u] < FY) {
+            myrow[fk[u]] = __dadd_rn(myrow[fk[u]], prod[u]);
+            seen |= 1ull << fk[u];
+          }
+        }
+      }
+      __syncwarp();  // the chunk's staging is rewritten by the next chunk
+    }
+    const u64 any = (u64)__reduce_or_sync(0xffffffffu, (uint32_t)seen) |
+                    ((u64)__reduce_or_sync(0xffffffffu, (uint32_t)(seen >> 32)) << 32);
+    resolve_target_warp(a, g, (unsigned)__popcll(any), tg);  // also orders the rows' stores
+    for (uint32_t c = lane; c < FY; c += 32) {
+      if ((any >> c) & 1ull) {
+        double sum = 0.0;
+        for (int l = 0; l < 32; l++) sum = __dadd_rn(sum, rows[(size_t)l * kRowStride + c]);
+        const u64 pos = tg.base + (u64)__popcll(any & ((1ull << c) - 1ull));
+        if (pos < tg.cap)
+          store_output(tg.coords, tg.vals, pos, tg.zrow + c, sum, tg.op, pol);
+        else
+          atomicOr(a.status, kStatOutOverflow);
+      }
+    }
+    __syncwarp();  // every column is summed before the rows are cleared
+    for (uint32_t c = 0; c < FY; c++) myrow[c] = 0.0;
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_group_lanerow(const GroupArgs& a, u64 ngroups, uint32_t FY, int sms, cudaStream_t s) {
+  if (ngroups == 0) return cudaSuccess;
+  if (FY == 0 || FY > kRowMax) return cudaErrorInvalidValue;
+  auto kern = group_lanerow_kernel;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowSmem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRowWarps * 32, kRowSmem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const u64 want = (ngroups + kRowWarps - 1) / kRowWarps, cap = (u64)sms * per_sm;
+  kern<<<(unsigned)(want < cap ? want : cap), kRowWarps * 32, kRowSmem, s>>>(a, ngroups, FY);
+  note_launch();
+  return cudaGetLastError();
+}
+
 uint32_t dense_stash_cap() { return kStashCap; }
 uint32_t dense_stream_cap() { return kStreamCap; }
 

@@ -340,6 +340,9 @@ struct StreamArgs {
   unsigned* nrec;  // records: one per (streamed group, segment), [list position * nseg + segment]
   u64* holes;      // total repeats (positions that hold no output at the end)
 };
+// Lane-private dense rows for output rows of at most 64 free keys (FY <= 64, 32-bit Y free
+// keys): one warp per group g in [0, ngroups) (empty groups skipped), outputs in key order.
+cudaError_t launch_group_lanerow(const GroupArgs& a, u64 ngroups, uint32_t FY, int sms, cudaStream_t s);
 uint32_t dense_stream_cap();
 // Streamed groups (B_g <= dense_stream_cap()); launched after every other accumulation kernel.
 // fixed_rows: the output plan has 2..8 modes in concatenation order, not all powers of two.

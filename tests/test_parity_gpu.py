@@ -411,3 +411,80 @@ def test_imbalanced_both_zipf():
     print(f"imbalanced_both sample: {info.products} products into {info.outputs} outputs "
           f"({info.products / max(info.outputs, 1):.0f} per output) against the oracle")
     assert info.products > 50 * info.outputs
+
+
+# ------------------------------------------------------------------ lane-private dense rows
+
+@pytest.mark.parametrize("shape", [((4, 6, 5), (5, 3)), ((40, 30, 7), (7, 64)), ((9, 7), (7, 1)), ((3, 50), (50, 8))])
+def test_lane_rows_against_oracle(shape):
+    """STC_ACC_ROWS (F_Y <= 64): heavy repeats per output, F_Y = 64 and F_Y = 1; outputs of one
+    or two products bit-exact (the rows are summed in a fixed lane order)."""
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(6100 + shape[1][1])
+    X = W.uniform_coo(rng, shape[0], 6_000)
+    Y = W.uniform_coo(rng, shape[1], 3_000)
+    res, ref = check(W.Problem(X, Y, (len(shape[0]) - 1,), (0,)), strategy=2, accumulator=stc.ACC_ROWS)
+    assert res.stats.accumulator == stc.ACC_ROWS
+
+
+def test_lane_rows_rejects_wide_rows():
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(6110)
+    p = W.Problem(W.uniform_coo(rng, (10, 5), 100), W.uniform_coo(rng, (5, 65), 100), (1,), (0,))
+    with pytest.raises(stc.StcError) as e:
+        gpu_contract(p, strategy=2, accumulator=stc.ACC_ROWS)
+    assert e.value.status == 1  # STC_ERR_INVALID_ARG
+
+
+def test_auto_remembers_rows_heavy_shapes():
+    """AUTO on a small output key space takes the one global table; once a run of a shape has
+    averaged 64 or more products per output cell, the next AUTO call of that shape in the same
+    context groups X and takes the lane-private rows, and a later run of the shape that is not
+    rows-heavy sends it back. Every result against the oracle."""
+    import gc
+
+    import numpy as np
+
+    import paper_2410_10094_gb300 as stc
+
+    rng = W.rng_for(6120)
+    X = W.uniform_coo(rng, (512, 8, 8), 50_000)
+    X.coords[:, 1] = X.coords[:, 1] % 2  # X's contract cells on 16 of the 64
+    X.coords[:, 2] = X.coords[:, 2] % 8
+    Y = W.uniform_coo(rng, (8, 8, 16), 2_000)
+    p = W.Problem(X, Y, (1, 2), (0, 1))
+    ref = oracle.contract(p.X, p.Y, p.cx, p.cy)
+    assert ref.products >= 64 * 512 * 16
+    ctx = stc.Context(0)
+    try:
+        def run(prob):
+            r = stc.contract(to_dev(prob.X), to_dev(prob.Y), prob.cx, prob.cy, ctx=ctx,
+                             operands=stc.OPERANDS_AS_GIVEN)
+            return r, (r.stats.strategy, r.stats.accumulator)
+
+        r1, k1 = run(p)
+        r2, k2 = run(p)
+        assert k1[0] == stc.STRATEGY_GLOBAL and k2 == (stc.STRATEGY_GROUPED, stc.ACC_ROWS)
+        for r in (r1, r2):
+            c, v = result_host(r)
+            assert_matches_oracle(c, v, ref)
+        # Same shapes and entry counts, few products: grouped once more, then forgotten. Y's
+        # entries move to contract cells (0..3, *), X's to (7, *) but for one in a hundred.
+        Xs = W.COO(X.shape, X.coords.copy(), X.vals)
+        Xs.coords[:, 1] = np.where(np.arange(X.nnz) % 100 == 0, 0, 7)
+        Ys = W.COO(Y.shape, Y.coords.copy(), Y.vals)
+        Ys.coords[:, 0] = Ys.coords[:, 0] % 4
+        ps = W.Problem(Xs, Ys, (1, 2), (0, 1))
+        refs = oracle.contract(ps.X, ps.Y, ps.cx, ps.cy)
+        r3, k3 = run(ps)
+        r4, k4 = run(ps)
+        assert k3[0] == stc.STRATEGY_GROUPED and k3[1] != stc.ACC_ROWS and k4[0] == stc.STRATEGY_GLOBAL
+        for r in (r3, r4):
+            c, v = result_host(r)
+            assert_matches_oracle(c, v, refs)
+        del r, r1, r2, r3, r4
+    finally:
+        gc.collect()
+        ctx.close()
