@@ -1368,6 +1368,7 @@ constexpr uint32_t kStreamCap = 8192;     // products of one group segment
 constexpr uint32_t kStreamSlots = kStreamCap / 32 + kStreamEntries;
 // Shared memory: key bitmap, repeat bitmap, slot table, X values, first-product keys, and the
 // rank -> place map of the repeated keys.
+static_assert(kStreamCap % 4 == 0, "the fix-up reads the first-product keys four at a time");
 constexpr size_t kStreamSmem = (size_t)kBitmapWords * 8 + (size_t)kStreamSlots * 8 + (size_t)kStreamEntries * 8 +
                                (size_t)kStreamCap * 2 + (size_t)kStreamCap;
 
@@ -1616,9 +1617,17 @@ __global__ void __launch_bounds__(kStreamThreads, STREAM_MINB) group_stream_kern
           r += __popc(rbits[w]);
         }
         __syncthreads();
-        for (uint32_t i = threadIdx.x; i < nkeys; i += T) {
-          const uint32_t fk = pk[i], w = fk >> 5, bit = 1u << (fk & 31), rw = rbits[w];
-          if (rw & bit) map[bits[w] + __popc(rw & (bit - 1))] = (uint16_t)i;
+        // Four first-product keys per 8-byte load (pk holds kStreamCap entries, so reading up
+        // to the next multiple of four stays inside it; entries past nkeys are skipped).
+        for (uint32_t q = threadIdx.x; q < (nkeys + 3) / 4; q += T) {
+          const uint2 four = reinterpret_cast<const uint2*>(pk)[q];
+#pragma unroll
+          for (int t = 0; t < 4; t++) {
+            const uint32_t i = q * 4 + t;
+            const uint32_t fk = ((t < 2 ? four.x : four.y) >> ((t & 1) * 16)) & 0xffffu;
+            const uint32_t w = fk >> 5, bit = 1u << (fk & 31), rw = rbits[w];
+            if (i < nkeys && (rw & bit)) map[bits[w] + __popc(rw & (bit - 1))] = (uint16_t)i;
+          }
         }
         __syncthreads();
         const int oz = tg.op.order;
