@@ -131,3 +131,18 @@ def test_missing_library_fails_loudly():
             "try:\n    B.load()\nexcept ImportError as e:\n    print('raised', e); sys.exit(0)\nsys.exit(1)")
     r = subprocess.run([__import__("sys").executable, "-c", code], capture_output=True, text=True, cwd=ROOT)
     assert r.returncode == 0 and "no CPU fallback" in r.stdout, r.stdout + r.stderr
+
+
+def test_binding_constants_match_the_header():
+    """Every enum value and status code of include/stc.h has the same value in the binding."""
+    import paper_2410_10094_gb300.binding as b
+
+    src = open(os.path.join(ROOT, "include", "stc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    pairs = dict((name, int(v)) for name, v in re.findall(r"\b(STC_[A-Z_0-9]+)\s*=\s*(\d+)", src))
+    assert pairs["STC_ACC_ROWS"] == 4 and pairs["STC_ERR_CANCELLED"] == 10
+    for name, v in pairs.items():
+        if name.startswith("STC_ERR_") or name == "STC_OK":
+            assert b.STATUS_NAMES[v] == name, name
+        else:
+            assert getattr(b, name[len("STC_"):]) == v, name
